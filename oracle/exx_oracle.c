@@ -1,0 +1,497 @@
+/*
+ * exx_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Plain, slow, CPU FP64 reference of the exact-exchange hot path of
+ * "GPU acceleration of hybrid functional calculations in the SPARC electronic
+ * structure code" (arXiv 2501.16572).  Only tests/, the smoke check and the
+ * benchmark's CPU-baseline leg may load this file; the CUDA library never does,
+ * and this file shares no code, header, table or helper with it.
+ *
+ * What it computes, in the paper's order:
+ *   - finite-difference weights of the second derivative (textbook central
+ *     differences; the paper leaves the order open, 12th order is used by the
+ *     workloads),
+ *   - the 1D second-derivative operators along x1, x2, x3 with Dirichlet or
+ *     periodic ends (Sec. II, below Eq. 3),
+ *   - their eigen-decompositions by cyclic Jacobi (Sec. II.A, Eqs. 6-7),
+ *   - f applied to the eigenvalue sums (Eq. 5; screened reading documented below),
+ *   - one Poisson solve per right-hand side with the original, slice-by-slice
+ *     Kronecker formalism of Eq. 8 (forward x,y per frontal slice, forward z,
+ *     Hadamard scaling, inverse x,y per slice, inverse z),
+ *   - the exchange operator of Eq. 1 at the Gamma point, real orbitals:
+ *     (Vx psi_n)(r) = - sum_m f_m psi_m(r) phi_mn(r), phi_mn = f(L)(psi_m psi_n),
+ *     summed over m with Neumaier compensation,
+ *   - the exchange energy in two independent forms,
+ *   - the ACE matrices of Sec. III.A: M = dV Psi^T W, the Cholesky factor of -M,
+ *     xi = W L^{-T}.
+ *
+ * Readings where the paper is garbled or silent (each one is listed in the design
+ * notes of the repository):
+ *   R1  Screened kernel: Eq. 3 / Eq. 5 as printed, -4 pi L^{-1} (I - e^{-L/(16 pi w^2)}),
+ *       grows without bound for L <= 0.  The erfc-screened (HSE) kernel the paper
+ *       cites is used: f(lam) = (4 pi/|lam|) (1 - exp(-|lam|/(4 w^2))), f(0) = pi/w^2.
+ *       The literal magnitude 16 pi w^2 is kept as kernel 2 for comparison only.
+ *   R2  Dirichlet ends are homogeneous: grid values outside [0, n) are zero.
+ *   R3  The occupations f are applied exactly as given (no hidden factor 1/2);
+ *       E_x = 1/4 sum_n f_n dV <psi_n, Vx psi_n>.
+ *   R4  M = dV Psi^T W (orbitals orthonormal with the dV metric).
+ *   R5  ACE: M is negative definite, so its Cholesky factor does not exist as
+ *       printed; -sym(M) = L L^T with L lower triangular (positive diagonal),
+ *       xi = W L^{-T}, and the compressed operator is -dV xi xi^T.
+ *
+ * Every function has a pin in tests/test_oracle_pins.py: closed-form eigenvalues,
+ * stencil residuals, a dense brute-force solve, energy identities and ACE
+ * identities.
+ *
+ * Storage: grid functions are x-fastest, r = ix + n1*(iy + n2*iz); dense matrices
+ * are column-major, A[i + n*j] = A(i, j); orbital blocks are N x n column-major
+ * with leading dimension N.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define EXO_PI 3.14159265358979323846
+
+/* Deliberate-mistake switch used only by tests/test_oracle_pins.py to show that a
+ * pin fails when the oracle is wrong.  0 = normal operation. */
+static int g_mutation = 0;
+void exo_set_mutation(int m) { g_mutation = m; }
+
+int exo_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ---------------------------------------------------------------------------
+ * Finite-difference weights of the 2p-th order central second derivative:
+ *   w_k = 2 (-1)^{k+1} (p!)^2 / (k^2 (p-k)! (p+k)!),  k = 1..p,   w_0 = -2 sum_k w_k.
+ * (textbook closed form; the paper only states that the Laplacian is a
+ * finite-difference one.)  w[0..p].
+ */
+int exo_fd_weights(int p, double *w)
+{
+    if (p < 1 || p > 20) return -1;
+    double s = 0.0;
+    for (int k = 1; k <= p; ++k) {
+        /* (p!)^2 / ((p-k)! (p+k)!) = prod_{i=1..k} (p-k+i)/(p+i) */
+        double r = 1.0;
+        for (int i = 1; i <= k; ++i) r *= (double)(p - k + i) / (double)(p + i);
+        double wk = 2.0 * r / ((double)k * (double)k);
+        if (k % 2 == 0) wk = -wk;
+        w[k] = wk;
+        s += wk;
+    }
+    w[0] = -2.0 * s;
+    return 0;
+}
+
+/* 1D second-derivative operator D (n x n, column-major) with spacing h.
+ * bc = 0: Dirichlet, entries that would fall outside [0, n) are dropped.
+ * bc = 1: periodic, w_k added at (i, (i +- k) mod n) (folds onto itself when k >= n).
+ */
+int exo_second_derivative_1d(int n, double h, int bc, int p, double *D)
+{
+    double w[32];
+    if (n < 1 || exo_fd_weights(p, w)) return -1;
+    memset(D, 0, sizeof(double) * (size_t)n * n);
+    double ih2 = 1.0 / (h * h);
+    for (int i = 0; i < n; ++i) {
+        D[i + (size_t)n * i] += w[0] * ih2;
+        for (int k = 1; k <= p; ++k) {
+            int jp = i + k, jm = i - k;
+            if (bc == 1) {
+                jp = ((jp % n) + n) % n;
+                jm = ((jm % n) + n) % n;
+                D[i + (size_t)n * jp] += w[k] * ih2;
+                D[i + (size_t)n * jm] += w[k] * ih2;
+            } else {
+                if (jp < n) D[i + (size_t)n * jp] += w[k] * ih2;
+                if (jm >= 0) D[i + (size_t)n * jm] += w[k] * ih2;
+            }
+        }
+    }
+    return 0;
+}
+
+/* Cyclic Jacobi eigen-decomposition of the symmetric n x n matrix A:
+ * A = V diag(lam) V^T, eigenvalues ascending, eigenvectors in the columns of V. */
+int exo_jacobi_eigh(int n, const double *Ain, double *V, double *lam)
+{
+    double *A = (double *)malloc(sizeof(double) * (size_t)n * n);
+    if (!A) return -1;
+    memcpy(A, Ain, sizeof(double) * (size_t)n * n);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) V[i + (size_t)n * j] = (i == j) ? 1.0 : 0.0;
+    double fro = 0.0;
+    for (size_t i = 0; i < (size_t)n * n; ++i) fro += A[i] * A[i];
+    fro = sqrt(fro);
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int q = 1; q < n; ++q)
+            for (int pp = 0; pp < q; ++pp) off += A[pp + (size_t)n * q] * A[pp + (size_t)n * q];
+        if (sqrt(2.0 * off) <= 1e-17 * fro) break;
+        for (int pp = 0; pp < n - 1; ++pp) {
+            for (int q = pp + 1; q < n; ++q) {
+                double apq = A[pp + (size_t)n * q];
+                if (apq == 0.0) continue;
+                double app = A[pp + (size_t)n * pp], aqq = A[q + (size_t)n * q];
+                double theta = (aqq - app) / (2.0 * apq);
+                double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                /* A <- J^T A J with J the rotation in the (pp, q) plane */
+                for (int k = 0; k < n; ++k) {
+                    double akp = A[k + (size_t)n * pp], akq = A[k + (size_t)n * q];
+                    A[k + (size_t)n * pp] = c * akp - s * akq;
+                    A[k + (size_t)n * q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double apk = A[pp + (size_t)n * k], aqk = A[q + (size_t)n * k];
+                    A[pp + (size_t)n * k] = c * apk - s * aqk;
+                    A[q + (size_t)n * k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double vkp = V[k + (size_t)n * pp], vkq = V[k + (size_t)n * q];
+                    V[k + (size_t)n * pp] = c * vkp - s * vkq;
+                    V[k + (size_t)n * q] = s * vkp + c * vkq;
+                }
+            }
+        }
+    }
+    for (int i = 0; i < n; ++i) lam[i] = A[i + (size_t)n * i];
+    /* selection sort ascending, moving eigenvectors along */
+    for (int i = 0; i < n; ++i) {
+        int best = i;
+        for (int j = i + 1; j < n; ++j) if (lam[j] < lam[best]) best = j;
+        if (best != i) {
+            double t = lam[i]; lam[i] = lam[best]; lam[best] = t;
+            for (int k = 0; k < n; ++k) {
+                double v = V[k + (size_t)n * i];
+                V[k + (size_t)n * i] = V[k + (size_t)n * best];
+                V[k + (size_t)n * best] = v;
+            }
+        }
+    }
+    free(A);
+    return 0;
+}
+
+/* f applied to one eigenvalue sum lam (<= 0), Eq. 5 with reading R1. */
+double exo_kernel_value(double lam, int kernel, double omega)
+{
+    double x = -lam; /* = |k|^2 in the continuum limit */
+    if (kernel == 0) {
+        if (g_mutation == 3) return 4.0 * EXO_PI / lam;   /* planted sign error */
+        return -4.0 * EXO_PI / lam;
+    }
+    double a = (kernel == 2) ? 16.0 * EXO_PI * omega * omega : 4.0 * omega * omega;
+    if (x == 0.0) return 4.0 * EXO_PI / a;
+    return (4.0 * EXO_PI / x) * (-expm1(-x / a));
+}
+
+/* ---------------------------------------------------------------------------
+ * Plan: the three 1D eigenbases and f(Lambda~) (Eqs. 6-7).
+ */
+typedef struct {
+    int n[3];
+    double h, omega, dV;
+    int bc[3], p, kernel;
+    double *V[3];   /* n_d x n_d column-major: V[d][i + n_d*a] = component i of mode a */
+    double *lam[3];
+    double *F;      /* N values, index a + n1*(b + n2*c) */
+} exo_plan;
+
+void exo_plan_free(exo_plan *P)
+{
+    if (!P) return;
+    for (int d = 0; d < 3; ++d) { free(P->V[d]); free(P->lam[d]); }
+    free(P->F);
+    free(P);
+}
+
+exo_plan *exo_plan_new(int n1, int n2, int n3, double h, const int *bc, int fd_order,
+                       int kernel, double omega)
+{
+    if (fd_order < 2 || fd_order % 2) return NULL;
+    exo_plan *P = (exo_plan *)calloc(1, sizeof(exo_plan));
+    if (!P) return NULL;
+    P->n[0] = n1; P->n[1] = n2; P->n[2] = n3;
+    P->h = h; P->omega = omega; P->dV = h * h * h;
+    P->p = fd_order / 2; P->kernel = kernel;
+    for (int d = 0; d < 3; ++d) {
+        int nd = P->n[d];
+        P->bc[d] = bc[d];
+        double *D = (double *)malloc(sizeof(double) * (size_t)nd * nd);
+        P->V[d] = (double *)malloc(sizeof(double) * (size_t)nd * nd);
+        P->lam[d] = (double *)malloc(sizeof(double) * (size_t)nd);
+        if (!D || !P->V[d] || !P->lam[d] || exo_second_derivative_1d(nd, h, bc[d], P->p, D) ||
+            exo_jacobi_eigh(nd, D, P->V[d], P->lam[d])) {
+            free(D); exo_plan_free(P); return NULL;
+        }
+        free(D);
+    }
+    size_t N = (size_t)n1 * n2 * n3;
+    P->F = (double *)malloc(sizeof(double) * N);
+    if (!P->F) { exo_plan_free(P); return NULL; }
+    for (int c = 0; c < n3; ++c)
+        for (int b = 0; b < n2; ++b)
+            for (int a = 0; a < n1; ++a) {
+                double lam = P->lam[0][a] + P->lam[1][b] + P->lam[2][c];
+                P->F[a + (size_t)n1 * (b + (size_t)n2 * c)] = exo_kernel_value(lam, kernel, omega);
+            }
+    return P;
+}
+
+int exo_plan_dims(const exo_plan *P, int *n3out) { n3out[0] = P->n[0]; n3out[1] = P->n[1]; n3out[2] = P->n[2]; return 0; }
+const double *exo_plan_eigvecs(const exo_plan *P, int d) { return P->V[d]; }
+const double *exo_plan_eigvals(const exo_plan *P, int d) { return P->lam[d]; }
+const double *exo_plan_F(const exo_plan *P) { return P->F; }
+
+/* ---------------------------------------------------------------------------
+ * One Poisson solve X = f(L) B by the original Kronecker formalism (Eq. 8):
+ *   S_k = V1^T B_k V2 for every frontal slice k,
+ *   R   = [vec S_1 ... vec S_n3] V3,           Xt = F (.) R,
+ *   U_c = V1 Xt_c V2^T for every slice c,
+ *   X   = [vec U_1 ... vec U_n3] V3^T.
+ * Real eigenvectors, so the conjugates of Eq. 8 are no-ops.
+ */
+int exo_solve(const exo_plan *P, const double *B, double *X)
+{
+    const int n1 = P->n[0], n2 = P->n[1], n3 = P->n[2];
+    const size_t n12 = (size_t)n1 * n2, N = n12 * n3;
+    const double *V1 = P->V[0], *V2 = P->V[1], *V3 = P->V[2];
+    double *S = (double *)malloc(sizeof(double) * N);
+    double *R = (double *)malloc(sizeof(double) * N);
+    if (!S || !R) { free(S); free(R); return -1; }
+
+    /* forward x, y per frontal slice */
+    #pragma omp parallel for schedule(static)
+    for (int k = 0; k < n3; ++k) {
+        double *T = (double *)malloc(sizeof(double) * n12);
+        const double *Bk = B + n12 * k;
+        for (int j = 0; j < n2; ++j)              /* T = V1^T B_k */
+            for (int a = 0; a < n1; ++a) {
+                double s = 0.0;
+                for (int i = 0; i < n1; ++i) s += V1[i + (size_t)n1 * a] * Bk[i + (size_t)n1 * j];
+                T[a + (size_t)n1 * j] = s;
+            }
+        for (int b = 0; b < n2; ++b)              /* S_k = T V2 */
+            for (int a = 0; a < n1; ++a) {
+                double s = 0.0;
+                for (int j = 0; j < n2; ++j) s += T[a + (size_t)n1 * j] * V2[j + (size_t)n2 * b];
+                S[a + (size_t)n1 * b + n12 * k] = s;
+            }
+        free(T);
+    }
+    /* forward z: R(:, c) = sum_k S(:, k) V3(k, c); then the Hadamard scaling */
+    #pragma omp parallel for schedule(static)
+    for (int c = 0; c < n3; ++c) {
+        double *Rc = R + n12 * c;
+        for (size_t q = 0; q < n12; ++q) Rc[q] = 0.0;
+        for (int k = 0; k < n3; ++k) {
+            double v = V3[k + (size_t)n3 * c];
+            if (g_mutation == 1) v = V3[c + (size_t)n3 * k];     /* planted transpose */
+            const double *Sk = S + n12 * k;
+            for (size_t q = 0; q < n12; ++q) Rc[q] += v * Sk[q];
+        }
+        const double *Fc = P->F + n12 * c;
+        if (g_mutation != 2)                                     /* 2 = planted: drop F */
+            for (size_t q = 0; q < n12; ++q) Rc[q] *= Fc[q];
+    }
+    /* inverse x, y per slice: U_c = V1 Xt_c V2^T (stored back into S) */
+    #pragma omp parallel for schedule(static)
+    for (int c = 0; c < n3; ++c) {
+        double *T = (double *)malloc(sizeof(double) * n12);
+        const double *Xc = R + n12 * c;
+        for (int b = 0; b < n2; ++b)              /* T = V1 Xt_c */
+            for (int i = 0; i < n1; ++i) {
+                double s = 0.0;
+                for (int a = 0; a < n1; ++a) s += V1[i + (size_t)n1 * a] * Xc[a + (size_t)n1 * b];
+                T[i + (size_t)n1 * b] = s;
+            }
+        for (int j = 0; j < n2; ++j)              /* U_c = T V2^T */
+            for (int i = 0; i < n1; ++i) {
+                double s = 0.0;
+                for (int b = 0; b < n2; ++b) s += T[i + (size_t)n1 * b] * V2[j + (size_t)n2 * b];
+                S[i + (size_t)n1 * j + n12 * c] = s;
+            }
+        free(T);
+    }
+    /* inverse z: X(:, k) = sum_c U(:, c) V3(k, c) */
+    #pragma omp parallel for schedule(static)
+    for (int k = 0; k < n3; ++k) {
+        double *Xk = X + n12 * k;
+        for (size_t q = 0; q < n12; ++q) Xk[q] = 0.0;
+        for (int c = 0; c < n3; ++c) {
+            double v = V3[k + (size_t)n3 * c];
+            const double *Uc = S + n12 * c;
+            for (size_t q = 0; q < n12; ++q) Xk[q] += v * Uc[q];
+        }
+    }
+    free(S); free(R);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * Exchange operator, Eq. 1 (Gamma point, one spin, real orbitals, weights f):
+ *   out_n(r) = - sum_{m < n_occ} f_m psi_m(r) phi_mn(r),  phi_mn = f(L)(psi_m psi_n).
+ * Computed for the output columns listed in cols[0..ncols) (all when cols == NULL,
+ * ncols = n_in); out has ncols columns of length N.  The sum over m runs in order
+ * m = 0, 1, ... with Neumaier compensation.
+ */
+int exo_exx_apply(const exo_plan *P, const double *psi_occ, int n_occ, const double *f,
+                  const double *psi_in, int n_in, const int *cols, int ncols, double *out)
+{
+    const size_t N = (size_t)P->n[0] * P->n[1] * P->n[2];
+    double *rho = (double *)malloc(sizeof(double) * N);
+    double *phi = (double *)malloc(sizeof(double) * N);
+    double *comp = (double *)malloc(sizeof(double) * N);
+    if (!rho || !phi || !comp) { free(rho); free(phi); free(comp); return -1; }
+    if (!cols) ncols = n_in;
+    for (int t = 0; t < ncols; ++t) {
+        int n = cols ? cols[t] : t;
+        if (n < 0 || n >= n_in) { free(rho); free(phi); free(comp); return -2; }
+        const double *pn = psi_in + N * (size_t)n;
+        double *o = out + N * (size_t)t;
+        for (size_t r = 0; r < N; ++r) { o[r] = 0.0; comp[r] = 0.0; }
+        for (int m = 0; m < n_occ; ++m) {
+            const double *pm = psi_occ + N * (size_t)m;
+            for (size_t r = 0; r < N; ++r) rho[r] = pm[r] * pn[r];
+            if (exo_solve(P, rho, phi)) { free(rho); free(phi); free(comp); return -1; }
+            double fm = f[m];
+            for (size_t r = 0; r < N; ++r) {
+                double term = -fm * pm[r] * phi[r];
+                double s = o[r] + term;       /* Neumaier two-sum */
+                if (fabs(o[r]) >= fabs(term)) comp[r] += (o[r] - s) + term;
+                else comp[r] += (term - s) + o[r];
+                o[r] = s;
+            }
+        }
+        for (size_t r = 0; r < N; ++r) o[r] += comp[r];
+    }
+    free(rho); free(phi); free(comp);
+    return 0;
+}
+
+/* Neumaier-compensated sum helper state */
+typedef struct { double s, c; } exo_ksum;
+static void ks_add(exo_ksum *k, double x)
+{
+    double t = k->s + x;
+    if (fabs(k->s) >= fabs(x)) k->c += (k->s - t) + x;
+    else k->c += (x - t) + k->s;
+    k->s = t;
+}
+
+/* E_x, first form: 1/4 sum_n f_n dV <psi_n, (Vx psi)_n> over the n_occ occupied
+ * orbitals (reading R3). */
+double exo_energy(const exo_plan *P, const double *psi_occ, int n_occ, const double *f,
+                  const double *vx, long ld_v)
+{
+    const size_t N = (size_t)P->n[0] * P->n[1] * P->n[2];
+    exo_ksum acc = {0.0, 0.0};
+    for (int n = 0; n < n_occ; ++n) {
+        exo_ksum dot = {0.0, 0.0};
+        const double *pn = psi_occ + N * (size_t)n, *vn = vx + (size_t)ld_v * n;
+        for (size_t r = 0; r < N; ++r) ks_add(&dot, pn[r] * vn[r]);
+        ks_add(&acc, 0.25 * f[n] * P->dV * (dot.s + dot.c));
+    }
+    return acc.s + acc.c;
+}
+
+/* E_x, second form, straight from the pair solves:
+ *   E_x = -1/4 sum_{m,n} f_m f_n dV sum_r rho_mn(r) phi_mn(r)
+ * with every unordered pair solved once (phi_mn = phi_nm). */
+double exo_energy_pairs(const exo_plan *P, const double *psi_occ, int n_occ, const double *f)
+{
+    const size_t N = (size_t)P->n[0] * P->n[1] * P->n[2];
+    double *rho = (double *)malloc(sizeof(double) * N);
+    double *phi = (double *)malloc(sizeof(double) * N);
+    exo_ksum acc = {0.0, 0.0};
+    for (int m = 0; m < n_occ; ++m)
+        for (int n = m; n < n_occ; ++n) {
+            const double *pm = psi_occ + N * (size_t)m, *pn = psi_occ + N * (size_t)n;
+            for (size_t r = 0; r < N; ++r) rho[r] = pm[r] * pn[r];
+            exo_solve(P, rho, phi);
+            exo_ksum dot = {0.0, 0.0};
+            for (size_t r = 0; r < N; ++r) ks_add(&dot, rho[r] * phi[r]);
+            double mult = (m == n) ? 1.0 : 2.0;
+            ks_add(&acc, -0.25 * mult * f[m] * f[n] * P->dV * (dot.s + dot.c));
+        }
+    free(rho); free(phi);
+    return acc.s + acc.c;
+}
+
+/* ---------------------------------------------------------------------------
+ * ACE construction, Sec. III.A with readings R4, R5.
+ *   M   = dV Psi^T W            (n x n)
+ *   Ms  = (M + M^T)/2,  -Ms = L L^T   (plain Cholesky, column by column)
+ *   xi  = W L^{-T}              (N x n), row by row forward substitution
+ * Psi, W, xi: N x n column-major (ld = N).  M and L: n x n column-major; L is
+ * lower triangular with the strict upper part zero.  Returns 0, or 1 + the
+ * failing pivot when -Ms is not positive definite.
+ */
+int exo_ace(int N, int n, double dV, const double *Psi, const double *W, double *M,
+            double *L, double *xi)
+{
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+            exo_ksum s = {0.0, 0.0};
+            const double *pi = Psi + (size_t)N * i, *wj = W + (size_t)N * j;
+            for (int r = 0; r < N; ++r) ks_add(&s, pi[r] * wj[r]);
+            M[i + (size_t)n * j] = dV * (s.s + s.c);
+        }
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i)
+            L[i + (size_t)n * j] = (i >= j) ? -0.5 * (M[i + (size_t)n * j] + M[j + (size_t)n * i]) : 0.0;
+    for (int j = 0; j < n; ++j) {
+        double d = L[j + (size_t)n * j];
+        for (int k = 0; k < j; ++k) d -= L[j + (size_t)n * k] * L[j + (size_t)n * k];
+        if (!(d > 0.0)) return 1 + j;
+        d = sqrt(d);
+        L[j + (size_t)n * j] = d;
+        for (int i = j + 1; i < n; ++i) {
+            double s = L[i + (size_t)n * j];
+            for (int k = 0; k < j; ++k) s -= L[i + (size_t)n * k] * L[j + (size_t)n * k];
+            L[i + (size_t)n * j] = s / d;
+        }
+    }
+    /* xi L^T = W, one grid row r at a time: xi(r, j) = (W(r, j) - sum_{k<j} xi(r, k) L(j, k)) / L(j, j) */
+    #pragma omp parallel for schedule(static)
+    for (int r = 0; r < N; ++r)
+        for (int j = 0; j < n; ++j) {
+            double s = W[r + (size_t)N * j];
+            for (int k = 0; k < j; ++k) s -= xi[r + (size_t)N * k] * L[j + (size_t)n * k];
+            xi[r + (size_t)N * j] = s / L[j + (size_t)n * j];
+        }
+    return 0;
+}
+
+/* Apply the compressed operator: out = -dV xi (xi^T Phi), Phi N x nphi. */
+int exo_ace_apply(int N, int n, double dV, const double *xi, const double *Phi, int nphi, double *out)
+{
+    double *chi = (double *)malloc(sizeof(double) * (size_t)n * nphi);
+    if (!chi) return -1;
+    for (int q = 0; q < nphi; ++q)
+        for (int j = 0; j < n; ++j) {
+            exo_ksum s = {0.0, 0.0};
+            for (int r = 0; r < N; ++r) ks_add(&s, xi[r + (size_t)N * j] * Phi[r + (size_t)N * q]);
+            chi[j + (size_t)n * q] = s.s + s.c;
+        }
+    #pragma omp parallel for schedule(static)
+    for (int r = 0; r < N; ++r)
+        for (int q = 0; q < nphi; ++q) {
+            double s = 0.0;
+            for (int j = 0; j < n; ++j) s += xi[r + (size_t)N * j] * chi[j + (size_t)n * q];
+            out[r + (size_t)N * q] = -dV * s;
+        }
+    free(chi);
+    return 0;
+}
