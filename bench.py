@@ -1,0 +1,402 @@
+#!/usr/bin/env python
+"""Benchmark of one exact-exchange + ACE step on GB300.
+
+Workload (one step): the 48^3 periodic grid, h = 0.25 bohr, 12th-order FD, erfc-screened
+kernel omega = 0.106, 128 orthonormal synthetic orbitals with Fermi-Dirac occupations
+(Fermi level at orbital 100):
+    VxPsi = exx_apply(Psi_occ = all 128, Psi_in = all 128)   (8256 unique pair solves)
+    E_x   = exx_energy(...)
+    xi    = ace_build(Psi, VxPsi)
+Metric: pair-Poisson solves per second (each solve is one batched Kronecker solve of
+one orbital pair, Sec. II.B) and the exx_apply time.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--prec auto|fp64|bf16x3|tf32x3|bf16x6]
+For N > 1 launch with torchrun; every rank runs an independent replica (the pair
+solves shard with no exchange), so the whole-job value is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pair-Poisson solves/s & exx_apply time: FP64 vs split-precision at stated error"
+UNIT = "pair-Poisson solves/s"
+WORKLOAD = ("periodic48_erfc_128: 48x48x48 periodic grid, h=0.25, 12th-order FD, erfc kernel "
+            "omega=0.106, 128 orbitals, Fermi-Dirac occupations; step = exx_apply + exx_energy + ace_build")
+L2_FLUSH_BYTES = 512 << 20
+FP64_PEAK_NOTE = "FP64 CUDA-core peak: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="auto")
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64-vs-split comparison leg")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n-orb", type=int, default=128)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampler for the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def src_hash(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        h.update(open(os.path.join(ROOT, p), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or None when the
+    kernel source changed since the counters were taken."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
+    except Exception:
+        return None
+    if rec.get("src_hash") != src_hash(rec["sources"]):
+        return None
+    return rec
+
+
+def prec_code(exx, name):
+    return {"fp64": exx.EXX_PREC_FP64, "bf16x3": exx.EXX_PREC_BF16X3, "tf32x3": exx.EXX_PREC_TF32X3,
+            "bf16x6": exx.EXX_PREC_BF16X6}[name]
+
+
+def pick_precision(exx, s, dev):
+    """'auto': the fastest split-precision form that is built on this library, else FP64."""
+    import torch
+    for name in ("bf16x6", "tf32x3"):
+        try:
+            p = exx.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+            p.set_precision(prec_code(exx, name))
+            p.close()
+            return name
+        except Exception:
+            continue
+    return "fp64"
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    import paper_2501_16572_gb300 as exx
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    s = synth.config2(args.n_orb)
+    occ = s.n_occ
+    unique = s.unique_pairs()
+    ordered = s.ordered_pairs()
+    psi = torch.from_numpy(s.psi).to(dev)
+    f = torch.from_numpy(s.f).to(dev)
+    prec_name = args.prec if args.prec != "auto" else pick_precision(exx, s, dev)
+
+    def make_plan(name):
+        p = exx.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+        p.set_precision(prec_code(exx, name))
+        return p
+
+    plan = make_plan(prec_name)
+    W = torch.empty_like(psi)
+    xi = torch.empty_like(psi)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(p, t_apply=None):
+        launches = 0
+        if t_apply is not None:
+            t_apply[0].record(stream)
+        p.apply(psi[:occ], f, psi, out=W)
+        launches += p.launch_count()
+        if t_apply is not None:
+            t_apply[1].record(stream)
+        e = p.energy(psi[:occ], f, W)
+        launches += p.launch_count()
+        p.ace_build(psi, W, xi=xi)
+        launches += p.launch_count()
+        return e, launches
+
+    def timed(p, steps, warmup, with_kernel_timing):
+        for _ in range(warmup):
+            step(p)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ms, apply_ms, launches = [], [], 0
+        if with_kernel_timing:
+            p.set_timing(True)
+        clocks = Clocks(local)
+        clocks.start()
+        for _ in range(steps):
+            flush.fill_(1.0)                 # evict L2 between timed steps (untimed)
+            torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(stream)
+            e, nl = step(p, (ev[2], ev[3]))
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            ms.append(ev[0].elapsed_time(ev[1]))
+            apply_ms.append(ev[2].elapsed_time(ev[3]))
+            launches += nl
+        clk = clocks.stop()
+        kt = p.timing() if with_kernel_timing else {}
+        if with_kernel_timing:
+            p.set_timing(False)
+        tot = torch.tensor([sum(ms), sum(apply_ms)], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+        return tot[0].item(), tot[1].item(), e, launches, kt, clk
+
+    total_ms, apply_total_ms, e_main, launches, ktimes, clk = timed(plan, args.steps, args.warmup, True)
+    K = args.steps
+    value = world * unique * K / (total_ms / 1e3)
+    rec = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": prec_name, "data": "synthetic (seeded Gaussian + plane-wave orbitals, orthonormalised)",
+        "config": {"workload": WORKLOAD, "grid": list(s.n), "n_orb": s.n_orb, "n_occ": occ,
+                   "unique_pair_solves_per_step": unique, "ordered_pairs_per_step": ordered,
+                   "precision": prec_name, "l2": "flushed between timed steps (512 MB write, untimed)",
+                   "parallelism": f"replicas x{world}"},
+        "exx_apply_ms": apply_total_ms / K,
+        "ordered_pairs_per_s": world * ordered * K / (total_ms / 1e3),
+        "gpu_launches": launches,
+        "E_x": e_main,
+    }
+    # -- roofline of the dominant kernel (CUDA events around every launch, timed region) --
+    peaks = measured_peaks()
+    if ktimes:
+        dom = max(ktimes, key=lambda k: ktimes[k][0])
+        dom_ms, dom_n = ktimes[dom]
+        rec["kernel_times_ms"] = {k: round(v[0] / K, 4) for k, v in ktimes.items()}
+        rec["roofline"] = roofline(exx, plan, s, prec_name, dom, dom_ms, dom_n, K, peaks, clk)
+    rec["clocks"] = clk
+    # -- FP64 vs split comparison --
+    if not args.no_compare and prec_name != "fp64":
+        W_split = W.clone()
+        xi_split = xi.clone()
+        p64 = make_plan("fp64")
+        t64, a64, e64, _, _, _ = timed(p64, max(1, min(2, K)), 1, False)
+        k64 = max(1, min(2, K))
+        rec["fp64"] = {"ms_per_step": t64 / k64, "exx_apply_ms": a64 / k64,
+                       "pair_solves_per_s": world * unique * k64 / (t64 / 1e3)}
+        rec["split_vs_fp64_speedup"] = (t64 / k64) / (total_ms / K)
+        rec["split_vs_fp64_apply_speedup"] = (a64 / k64) / (apply_total_ms / K)
+        rel = lambda a, b: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+        rec["error_vs_fp64"] = {"vxpsi_rel_fro": rel(W_split, W), "xi_rel_fro": rel(xi_split, xi),
+                                "E_x_rel": abs(e_main - e64) / abs(e64)}
+        p64.close()
+    # -- end to end through the host-buffer entry point --
+    if not args.no_e2e:
+        rec["e2e"] = e2e(exx, plan, s, K, world, dev)
+    # -- CPU oracle baseline (rank 0, N = 1) --
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rec["cpu_baseline"] = cpu_baseline(s)
+    plan.close()
+    if rank == 0:
+        print(json.dumps(rec), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def roofline(exx, plan, s, prec, kind, ms, nlaunch, K, peaks, clk):
+    """Achieved throughput of the dominant kernel class from its live CUDA-event time."""
+    n = s.n
+    N = s.N
+    unique = s.unique_pairs()
+    per_step = {}
+    # algorithmic flops of the mode products: 2 N n_d per field per contraction
+    axis_K = {"pass1": n[2], "pass2": n[0], "pass3": n[1], "pass4": n[0], "pass5": n[2]}
+    if kind in axis_K:
+        contractions = 2 if kind == "pass3" else 1
+        flops = 2.0 * N * axis_K[kind] * contractions * unique * K
+        achieved = flops / (ms / 1e3) / 1e12
+        if prec == "fp64":
+            peak = 152 * 2 * 2 * 2.07e9 / 1e12
+            out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                   "frac": achieved / peak, "kernel": f"fp64_pass_kernel ({kind})",
+                   "peak_source": FP64_PEAK_NOTE + " (derived, not measured)"}
+        else:
+            pk = peaks.get("bf16_tflops_sustained", 1700.0)
+            out = {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+                   "frac": achieved / pk, "kernel": f"tc_pass_kernel ({kind})",
+                   "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"}
+    elif kind == "accum":
+        bytes_ = 0.0
+        out = {"bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s", "frac": None,
+               "kernel": "accumulate"}
+    else:
+        out = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None, "kernel": kind}
+    out["launches"] = nlaunch
+    out["avg_launch_ms"] = ms / max(1, nlaunch)
+    tr = traffic_for(out["kernel"].split(" ")[0] + ":" + kind)
+    out["traffic"] = tr["bytes_per_launch"] if tr else None
+    return out
+
+
+def e2e(exx, plan, s, K, world, dev):
+    import torch
+    psi_h = torch.from_numpy(s.psi.copy()).pin_memory()
+    f_h = torch.from_numpy(s.f.copy()).pin_memory()
+    xi_h = torch.empty_like(psi_h).pin_memory()
+    plan.ace_step_host(psi_h, s.n_occ, f_h, xi_h)       # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        plan.ace_step_host(psi_h, s.n_occ, f_h, xi_h)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / K
+    return {"value": world * s.unique_pairs() / dt, "unit": UNIT, "ms_per_step": dt * 1e3,
+            "h2d_bytes_per_step": int(psi_h.numel() * 8 + f_h.numel() * 8),
+            "d2h_bytes_per_step": int(xi_h.numel() * 8 + 8),
+            "entry": "exx_ace_step_host (pinned host Psi, f in; xi, E_x out)"}
+
+
+def cpu_sample(s, budget_s=15.0):
+    """Time the CPU oracle on whole output columns of the workload (each column = n_occ
+    pair solves) until about budget_s seconds of work have run."""
+    import oracle
+    orc = oracle.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    cols = 0
+    t0 = time.perf_counter()
+    while True:
+        orc.exx_apply(s.psi[:s.n_occ], s.f, s.psi, cols=[cols % s.n_orb])
+        cols += 1
+        dt = time.perf_counter() - t0
+        if dt >= budget_s or cols >= s.n_orb:
+            break
+    solves = cols * s.n_occ
+    return solves / dt, cols, solves, dt, oracle.num_threads()
+
+
+def cpu_baseline(s):
+    v, cols, solves, dt, cores = cpu_sample(s)
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cols} output column(s) of the workload = {solves} pair Poisson solves "
+                      f"(plain C FP64 oracle, {dt:.1f} s)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import synth
+    s = synth.config2(args.n_orb)
+    budget = 8.0
+    for _ in range(args.warmup):
+        cpu_sample(s, budget_s=1.0)
+    vals, tot_solves, tot_t = [], 0, 0.0
+    for _ in range(args.steps):
+        v, cols, solves, dt, cores = cpu_sample(s, budget_s=budget)
+        vals.append(v)
+        tot_solves += solves
+        tot_t += dt
+    value = tot_solves / tot_t
+    rec = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded Gaussian + plane-wave orbitals, orthonormalised)",
+           "config": {"workload": WORKLOAD, "grid": list(s.n), "n_orb": s.n_orb, "n_occ": s.n_occ,
+                      "sample": "each step: whole output columns of the workload for about 8 s"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{args.steps} steps x ~{budget:.0f} s of whole output columns "
+                                      f"({tot_solves} pair solves)"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(rec), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

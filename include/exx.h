@@ -1,0 +1,183 @@
+/*
+ * exx.h -- C interface of the GB300 exact-exchange library (libexx_gb300.so).
+ *
+ * The library applies the exact-exchange operator of a hybrid functional on a
+ * real-space finite-difference grid and builds the adaptively compressed exchange
+ * (ACE) operator from it, following "GPU acceleration of hybrid functional
+ * calculations in the SPARC electronic structure code" (arXiv 2501.16572):
+ *   - exchange operator, Eq. 1 (Gamma point, real orbitals, one spin channel);
+ *   - pair Poisson problems, Eq. 2 (unscreened) and Eq. 3 (erfc-screened);
+ *   - their solution X = f(L) B through the Kronecker eigen-decomposition of the
+ *     finite-difference Laplacian, Eqs. 4-7, solved as a batch (Sec. II.B);
+ *   - ACE construction, Sec. III.A: W, M = Psi^T W, Cholesky factor, xi.
+ *
+ * Conventions shared by every call
+ *   Grid:     N = Nx*Ny*Nz points, spacing h (bohr), index r = ix + Nx*(iy + Ny*iz)
+ *             (x fastest).  dV = h^3.
+ *   Orbitals: real FP64, column-major N x n blocks with leading dimension ld >= N;
+ *             column j starts at base + j*ld.  Orbitals are expected to be
+ *             orthonormal in the dV metric, sum_r psi_m psi_n dV = delta_mn (only
+ *             ACE needs this; exx_apply works for any input).
+ *   Memory:   every array pointer is a DEVICE pointer owned by the caller (for
+ *             example a PyTorch tensor) unless the name ends in _h; the library
+ *             never frees or keeps caller memory.  The plan owns its own device
+ *             workspace.  Arrays must be 8-byte aligned; a call does not modify
+ *             its inputs.
+ *   Streams:  calls are asynchronous on `stream` (NULL = legacy default stream)
+ *             unless stated otherwise.  One plan must not be used by two calls
+ *             that overlap in time (it owns one workspace).
+ *   Errors:   every call returns an exx_status; nothing throws across the
+ *             interface.  Arguments are checked on the host before any launch;
+ *             a failing CUDA call is reported as EXX_ERR_CUDA and its text is kept
+ *             for exx_last_error().
+ *   Device:   compiled for sm_103a (GB300).  There is no CPU fallback: without a
+ *             usable GPU every compute call returns EXX_ERR_CUDA.
+ */
+#ifndef EXX_GB300_H
+#define EXX_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct exx_plan_s *exx_plan;
+/* Same type as cudaStream_t; declared here so this header needs no CUDA include. */
+typedef struct CUstream_st *exx_stream_t;
+
+typedef enum {
+    EXX_OK = 0,
+    EXX_ERR_INVALID_ARG = 1,   /* bad size, pointer, enum or leading dimension */
+    EXX_ERR_CUDA = 2,          /* a CUDA runtime call or launch failed */
+    EXX_ERR_OOM = 3,           /* device workspace could not be allocated */
+    EXX_ERR_NOT_POSDEF = 4,    /* ace_build: -sym(M) is not positive definite */
+    EXX_ERR_TIMEOUT = 5,       /* a bounded device-side wait ran out */
+    EXX_ERR_UNSUPPORTED = 6    /* valid but unsupported combination */
+} exx_status;
+
+enum { EXX_BC_DIRICHLET = 0, EXX_BC_PERIODIC = 1 };
+
+/* Kernels f of Eq. 5, on the eigenvalues lambda <= 0 of the FD Laplacian:
+ *   COULOMB             f = -4 pi / lambda                         (Eq. 2)
+ *   ERFC                f = 4 pi/|lambda| (1 - exp(-|lambda|/(4 omega^2))), f(0) = pi/omega^2
+ *                       (erfc-screened HSE kernel; Eq. 3 as printed has an exponent
+ *                       that grows without bound, this is the reading used)
+ *   ERFC_PAPER16PI      same with 16 pi omega^2 in place of 4 omega^2 (the printed
+ *                       magnitude), kept only for comparison. */
+enum { EXX_KERNEL_COULOMB = 0, EXX_KERNEL_ERFC = 1, EXX_KERNEL_ERFC_PAPER16PI = 2 };
+
+/* Arithmetic of the mode products (the six contractions of the batched Kronecker
+ * solve, Sec. II.B):
+ *   FP64    double precision on the CUDA cores;
+ *   BF16X3  tcgen05 tensor cores, operands split in two bf16 pieces, 3 products,
+ *           FP32 accumulation;
+ *   TF32X3  tcgen05 tensor cores, two tf32 pieces, 3 products, FP32 accumulation;
+ *   BF16X6  tcgen05 tensor cores, three bf16 pieces, 6 products, FP32 accumulation.
+ * Pair densities and the accumulation over pairs are compensated in every mode. */
+enum { EXX_PREC_FP64 = 0, EXX_PREC_BF16X3 = 1, EXX_PREC_TF32X3 = 2, EXX_PREC_BF16X6 = 3 };
+
+/* Create a plan for one grid (Sec. II.A, Eqs. 6-7).  Host FP64 work, done once:
+ * FD weights of order fd_order (even, 2..24), the three 1D second-derivative
+ * operators (Dirichlet: zero outside the grid; periodic: circulant), their
+ * eigen-decompositions, f over the eigenvalue sums; the results are uploaded to
+ * the device.  Nx, Ny, Nz in [2, 256]; h > 0; bc[d] in {DIRICHLET, PERIODIC};
+ * omega > 0 for the ERFC kernels.  COULOMB with all three axes periodic has a
+ * zero eigenvalue and returns EXX_ERR_UNSUPPORTED.  Uses the current CUDA device.
+ * On success *out is a new plan (free with exx_plan_destroy). */
+int exx_plan_create(exx_plan *out, int Nx, int Ny, int Nz, double h, const int bc[3],
+                    int fd_order, int kernel, double omega);
+
+/* Select the mode-product arithmetic (EXX_PREC_*); default EXX_PREC_FP64. */
+int exx_plan_set_precision(exx_plan plan, int prec);
+
+/* Tuning: pairs per batch (the paper's n_c, Sec. II.B; 0 = autotuned default) and
+ * orbitals per pair block (0 = default).  Results do not depend on either. */
+int exx_plan_set_batch(exx_plan plan, int pairs_per_batch, int block_orbitals);
+
+/* Free the plan and its device workspace (synchronizes the device first). */
+int exx_plan_destroy(exx_plan plan);
+
+/* Copy plan data to HOST memory for inspection: which = 0,1,2 gives the eigenvalues
+ * of axis d (n_d values); which = 3 gives f(Lambda) (N values, index
+ * a + Nx*(b + Ny*c)).  `count` must equal the number of values. */
+int exx_plan_get(exx_plan plan, int which, double *dst_h, long count);
+
+/* Exact-exchange operator, Eq. 1 (and Eq. W of Sec. III.A):
+ *   out_n = - sum_{m < n_occ} f_m psi_m (.) phi_mn,  phi_mn = f(L)(psi_m (.) psi_n)
+ * for n = 0..n_in-1, where psi_m are the columns of Psi_occ and psi_n those of Psi_in.
+ * Psi_occ: N x n_occ (ld_occ), f: n_occ device doubles, Psi_in: N x n_in (ld_in),
+ * out: N x n_in (ld_out), overwritten.  out must not overlap the inputs.
+ * When Psi_in == Psi_occ and ld_in == ld_occ (the ACE case: n_in >= n_occ, the
+ * occupied orbitals leading), each pair among the occupied orbitals is solved once
+ * and used for both out_m and out_n (phi_mn = phi_nm).  1 <= n_occ, n_in <= 65536. */
+int exx_apply(exx_plan plan, const double *Psi_occ, int n_occ, long ld_occ, const double *f,
+              const double *Psi_in, int n_in, long ld_in, double *out, long ld_out,
+              exx_stream_t stream);
+
+/* Exchange energy E_x = 1/4 sum_{n < n_occ} f_n dV <psi_n, VxPsi_n>, FP64 with
+ * compensated (Neumaier) sums in a fixed order (the paper prints no formula; this
+ * is the spin-unpolarised Fock energy for occupations f in [0, 2]).  Writes the
+ * HOST double *E_x_h; synchronizes `stream`. */
+int exx_energy(exx_plan plan, const double *Psi_occ, int n_occ, long ld, const double *f,
+               const double *VxPsi, long ld_v, double *E_x_h, exx_stream_t stream);
+
+/* ACE construction, Sec. III.A:
+ *   M = dV Psi^T W (n x n),  -sym(M) = L L^T (L lower triangular, positive diagonal),
+ *   xi = W L^{-T} (N x n).
+ * The compressed operator is then -dV xi xi^T (M is negative definite, so the
+ * printed "Cholesky factor of M" is read as that of -M).  Psi, W: N x n (ld, ld_w);
+ * xi: N x n (ld_xi), overwritten; M_out: optional n x n column-major device buffer
+ * (NULL to skip).  Cholesky and the triangular factor are FP64 in every mode; M and
+ * xi use the plan's precision (FP64, or split products on the tensor cores).
+ * *info_h (host) is 0, or 1 + the failing pivot when EXX_ERR_NOT_POSDEF is
+ * returned.  Synchronizes `stream`.  n <= 2048. */
+int ace_build(exx_plan plan, const double *Psi, int n, long ld, const double *W, long ld_w,
+              double *xi, long ld_xi, double *M_out, int *info_h, exx_stream_t stream);
+
+/* ACE application, Sec. III.B: out = -dV xi (xi^T Phi); xi: N x n, Phi, out: N x nphi. */
+int ace_apply(exx_plan plan, const double *xi, int n, long ld_xi, const double *Phi, int nphi,
+              long ld_phi, double *out, long ld_out, exx_stream_t stream);
+
+/* One ACE outer step from HOST buffers: copies Psi_h (N x n, ld) and f_h (n_occ) to
+ * plan-owned device buffers, runs exx_apply (Psi_occ = the first n_occ columns,
+ * Psi_in = all n), exx_energy and ace_build, and copies xi back to xi_h (N x n,
+ * ld_xi) and the energy to *E_x_h.  Synchronous. */
+int exx_ace_step_host(exx_plan plan, const double *Psi_h, int n, long ld, int n_occ,
+                      const double *f_h, double *xi_h, long ld_xi, double *E_x_h, int *info_h,
+                      exx_stream_t stream);
+
+/* Many independent systems (Sec. II.B's batching carried across systems): for each
+ * s < nsys runs exx_apply(plans[s], args[s]...) so that all systems' pair batches go
+ * through one persistent launch sequence per pass, captured in one CUDA graph on
+ * first use.  Every plan must use the same precision. */
+typedef struct {
+    const double *Psi_occ; int n_occ; long ld_occ; const double *f;
+    const double *Psi_in; int n_in; long ld_in; double *out; long ld_out;
+} exx_apply_args;
+int exx_apply_batched(const exx_plan *plans, int nsys, const exx_apply_args *args,
+                      exx_stream_t stream);
+
+/* Number of kernel launches issued by the last exx_apply / ace_build / energy call
+ * on this plan (for benchmarks). */
+long exx_plan_launch_count(exx_plan plan);
+
+/* Per-kernel timing with CUDA events recorded on the launch stream around every
+ * kernel the plan launches (for benchmarks).  enable = 1 starts recording (and clears
+ * earlier records), 0 stops.  exx_plan_get_timing synchronizes the device and returns,
+ * for kernel class `kind` (EXX_TIMING_*), the summed device time in milliseconds and
+ * the number of launches recorded since timing was enabled. */
+enum { EXX_TIMING_PASS1 = 0, EXX_TIMING_PASS2 = 1, EXX_TIMING_PASS3 = 2, EXX_TIMING_PASS4 = 3,
+       EXX_TIMING_PASS5 = 4, EXX_TIMING_ACCUM = 5, EXX_TIMING_PREP = 6, EXX_TIMING_GEMM = 7,
+       EXX_TIMING_CHOL = 8, EXX_TIMING_ENERGY = 9, EXX_TIMING_KINDS = 10 };
+int exx_plan_set_timing(exx_plan plan, int enable);
+int exx_plan_get_timing(exx_plan plan, int kind, double *ms_h, long *launches_h);
+
+/* Static text for a status code; never NULL. */
+const char *exx_status_string(int status);
+
+/* Text of the last error recorded by this thread (empty when none). */
+const char *exx_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EXX_GB300_H */

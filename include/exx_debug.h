@@ -1,0 +1,33 @@
+/*
+ * exx_debug.h -- host-only inspection hooks of libexx_gb300, for tests.
+ *
+ * These run entirely on the CPU (no CUDA call), so the plan-setup mathematics and the
+ * pair scheduler can be checked on a machine without a GPU.  They have no counterpart
+ * in the paper beyond the steps they expose (Eqs. 6-7 for the eigen-decomposition,
+ * Sec. II.B's batches of right-hand sides for the schedule).
+ */
+#ifndef EXX_GB300_DEBUG_H
+#define EXX_GB300_DEBUG_H
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* FD weights w[0..p] of the order-2p central second difference (host copy of what a plan uses). */
+int exx_debug_fd_weights(int p, double *w);
+
+/* 1D second-derivative operator (n x n column-major) as a plan assembles it. */
+int exx_debug_second_derivative(int n, double h, int bc, int p, double *D);
+
+/* The plan's symmetric eigensolver: A (n x n column-major) = V diag(lam) V^T, lam ascending. */
+int exx_debug_sym_eig(int n, const double *A, double *V, double *lam);
+
+/* Pair schedule of exx_apply.  First call with NULL arrays to get the sizes; then with
+ * pairs (2 ints per pair: m, n), batches (3 ints: nfields, first block, nblocks) and
+ * blocks (6 ints: I0, nI, J0, nJ, kind, field0) of at least those sizes. */
+int exx_debug_schedule(int n_occ, int n_in, int aliased, int block, int max_pairs, long *npairs,
+                       long *nbatches, long *nblocks, int *pairs, int *batches, int *blocks);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,473 @@
+// C interface of libexx_gb300: argument checks, plan life cycle, and the host-side
+// orchestration of the batched solve (Sec. II.B), the exchange accumulation (Eq. 1),
+// the energy and the ACE construction (Sec. III.A).
+#include "exx_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+namespace exx {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+    set_error(buf);
+    return e == cudaErrorMemoryAllocation ? EXX_ERR_OOM : EXX_ERR_CUDA;
+}
+
+static int invalid(const char *msg)
+{
+    set_error(msg);
+    return EXX_ERR_INVALID_ARG;
+}
+
+int dev_reserve(DevBuf &b, size_t bytes)
+{
+    if (b.bytes >= bytes && b.p) return EXX_OK;
+    if (b.p) {
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    if (bytes == 0) return EXX_OK;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        return cuda_fail(e, "cudaMalloc(workspace)");
+    }
+    b.bytes = bytes;
+    return EXX_OK;
+}
+
+void dev_free(DevBuf &b)
+{
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+static void free_plan_buffers(Plan &P)
+{
+    for (auto &b : P.B64) dev_free(b);
+    for (auto &row : P.Btc)
+        for (auto &b : row) dev_free(b);
+    for (auto *b : {&P.F64, &P.F32, &P.work[0], &P.work[1], &P.work[2], &P.pairs_d, &P.blocks_d,
+                    &P.acc_hi, &P.acc_lo, &P.g32, &P.psi32, &P.gemm_ws, &P.small_ws, &P.info_d,
+                    &P.red_ws, &P.host_stage_psi, &P.host_stage_f, &P.host_stage_xi, &P.host_stage_w})
+        dev_free(*b);
+}
+
+// Default batch size: enough fields per pass to fill the GPU several times over while
+// the batch buffers stay a modest part of L2 (tensor path) or of HBM (FP64 path).
+static int default_pairs(const Plan &P, int block)
+{
+    long per_field = long(P.N) * (P.prec == EXX_PREC_FP64 ? 8 : 4);
+    long budget = (P.prec == EXX_PREC_FP64) ? (256L << 20) : (48L << 20);
+    long pairs = std::max<long>(block * block, budget / per_field);
+    pairs = std::min<long>(pairs, 1024);
+    return int((pairs / (block * block)) * (block * block));
+}
+
+static int ensure_schedule(Plan &P, int n_occ, int n_in, bool aliased, cudaStream_t s)
+{
+    const int block = P.block_orbitals > 0 ? P.block_orbitals : 8;
+    const int maxp = P.pairs_per_batch > 0 ? P.pairs_per_batch : default_pairs(P, block);
+    int key[4] = {n_occ, n_in, (aliased ? 1 : 0) | (block << 1), maxp};
+    if (std::equal(key, key + 4, P.sched_key)) return EXX_OK;
+    P.sched = build_schedule(n_occ, n_in, aliased, block, maxp);
+    if (int rc = dev_reserve(P.pairs_d, std::max<size_t>(1, P.sched.pairs.size()) * sizeof(int2))) return rc;
+    if (int rc = dev_reserve(P.blocks_d, std::max<size_t>(1, P.sched.blocks.size()) * sizeof(Block))) return rc;
+    EXX_CUDA(cudaMemcpyAsync(P.pairs_d.p, P.sched.pairs.data(), P.sched.pairs.size() * sizeof(int2),
+                             cudaMemcpyHostToDevice, s));
+    EXX_CUDA(cudaMemcpyAsync(P.blocks_d.p, P.sched.blocks.data(), P.sched.blocks.size() * sizeof(Block),
+                             cudaMemcpyHostToDevice, s));
+    EXX_CUDA(cudaStreamSynchronize(s));   // host vectors may be rebuilt by the next call
+    std::copy(key, key + 4, P.sched_key);
+    return EXX_OK;
+}
+
+int timing_begin(Plan &P, int kind, cudaStream_t s)
+{
+    if (!P.timing.on) return -1;
+    TimingRec r{kind, nullptr, nullptr};
+    for (cudaEvent_t *e : {&r.start, &r.stop}) {
+        if (!P.timing.pool.empty()) {
+            *e = P.timing.pool.back();
+            P.timing.pool.pop_back();
+        } else if (cudaEventCreate(e) != cudaSuccess) {
+            return -1;
+        }
+    }
+    cudaEventRecord(r.start, s);
+    P.timing.recs.push_back(r);
+    return int(P.timing.recs.size()) - 1;
+}
+
+void timing_end(Plan &P, int rec, cudaStream_t s)
+{
+    if (rec < 0 || rec >= int(P.timing.recs.size())) return;
+    cudaEventRecord(P.timing.recs[rec].stop, s);
+}
+
+static void timing_recycle(Plan &P)
+{
+    for (auto &r : P.timing.recs) {
+        P.timing.pool.push_back(r.start);
+        P.timing.pool.push_back(r.stop);
+    }
+    P.timing.recs.clear();
+}
+
+}  // namespace exx
+
+using namespace exx;
+
+static Plan *as_plan(exx_plan p) { return reinterpret_cast<Plan *>(p); }
+
+extern "C" {
+
+const char *exx_status_string(int st)
+{
+    switch (st) {
+    case EXX_OK: return "EXX_OK";
+    case EXX_ERR_INVALID_ARG: return "EXX_ERR_INVALID_ARG: invalid argument";
+    case EXX_ERR_CUDA: return "EXX_ERR_CUDA: CUDA call failed";
+    case EXX_ERR_OOM: return "EXX_ERR_OOM: device allocation failed";
+    case EXX_ERR_NOT_POSDEF: return "EXX_ERR_NOT_POSDEF: -M is not positive definite";
+    case EXX_ERR_TIMEOUT: return "EXX_ERR_TIMEOUT: bounded device wait ran out";
+    case EXX_ERR_UNSUPPORTED: return "EXX_ERR_UNSUPPORTED: unsupported combination";
+    default: return "unknown exx status";
+    }
+}
+
+const char *exx_last_error(void) { return g_last_error.c_str(); }
+
+int exx_plan_create(exx_plan *out, int Nx, int Ny, int Nz, double h, const int bc[3], int fd_order,
+                    int kernel, double omega)
+{
+    if (!out) return invalid("exx_plan_create: out is NULL");
+    *out = nullptr;
+    if (!bc) return invalid("exx_plan_create: bc is NULL");
+    const int n[3] = {Nx, Ny, Nz};
+    for (int d = 0; d < 3; ++d) {
+        if (n[d] < 2 || n[d] > 256) return invalid("exx_plan_create: each grid size must be in [2, 256]");
+        if (bc[d] != EXX_BC_DIRICHLET && bc[d] != EXX_BC_PERIODIC) return invalid("exx_plan_create: bad bc");
+    }
+    if (!(h > 0.0) || !std::isfinite(h)) return invalid("exx_plan_create: h must be > 0");
+    if (fd_order < 2 || fd_order > 24 || (fd_order & 1)) return invalid("exx_plan_create: fd_order must be even in [2, 24]");
+    if (kernel != EXX_KERNEL_COULOMB && kernel != EXX_KERNEL_ERFC && kernel != EXX_KERNEL_ERFC_PAPER16PI)
+        return invalid("exx_plan_create: bad kernel");
+    if (kernel != EXX_KERNEL_COULOMB && !(omega > 0.0)) return invalid("exx_plan_create: omega must be > 0 for a screened kernel");
+    if (kernel == EXX_KERNEL_COULOMB && bc[0] == EXX_BC_PERIODIC && bc[1] == EXX_BC_PERIODIC &&
+        bc[2] == EXX_BC_PERIODIC) {
+        set_error("exx_plan_create: the unscreened kernel has a zero eigenvalue on an all-periodic grid");
+        return EXX_ERR_UNSUPPORTED;
+    }
+    Plan *P = new Plan();
+    for (int d = 0; d < 3; ++d) {
+        P->n[d] = n[d];
+        P->bc[d] = bc[d];
+    }
+    P->N = Nx * Ny * Nz;
+    P->h = h;
+    P->dV = h * h * h;
+    P->omega = omega;
+    P->fd_order = fd_order;
+    P->kernel = kernel;
+    // host FP64 setup, once per plan (Eqs. 6-7)
+    for (int d = 0; d < 3; ++d) {
+        int nd = n[d];
+        std::vector<double> D(size_t(nd) * nd);
+        second_derivative(nd, h, bc[d], fd_order / 2, D.data());
+        P->V[d].resize(size_t(nd) * nd);
+        P->lam[d].resize(nd);
+        if (sym_eig(nd, D.data(), P->V[d].data(), P->lam[d].data())) {
+            delete P;
+            set_error("exx_plan_create: eigen-decomposition did not converge");
+            return EXX_ERR_UNSUPPORTED;
+        }
+    }
+    P->F.resize(size_t(P->N));
+    for (int c = 0; c < Nz; ++c)
+        for (int b = 0; b < Ny; ++b)
+            for (int a = 0; a < Nx; ++a)
+                P->F[a + size_t(Nx) * (b + size_t(Ny) * c)] =
+                    kernel_f(P->lam[0][a] + P->lam[1][b] + P->lam[2][c], kernel, omega);
+    cudaError_t e = cudaGetDevice(&P->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device);
+    if (e != cudaSuccess) {
+        delete P;
+        return cuda_fail(e, "exx_plan_create: no usable CUDA device");
+    }
+    if (int rc = fp64_upload(*P)) {
+        free_plan_buffers(*P);
+        delete P;
+        return rc;
+    }
+    *out = reinterpret_cast<exx_plan>(P);
+    return EXX_OK;
+}
+
+int exx_plan_set_precision(exx_plan plan, int prec)
+{
+    Plan *P = as_plan(plan);
+    if (!P) return invalid("exx_plan_set_precision: plan is NULL");
+    if (prec < EXX_PREC_FP64 || prec > EXX_PREC_BF16X6) return invalid("exx_plan_set_precision: bad precision");
+    if (prec != EXX_PREC_FP64) {
+        if (int rc = tc_upload(*P, prec)) return rc;
+    }
+    P->prec = prec;
+    std::fill(P->sched_key, P->sched_key + 4, -1);
+    return EXX_OK;
+}
+
+int exx_plan_set_batch(exx_plan plan, int pairs_per_batch, int block_orbitals)
+{
+    Plan *P = as_plan(plan);
+    if (!P) return invalid("exx_plan_set_batch: plan is NULL");
+    if (pairs_per_batch < 0 || block_orbitals < 0 || block_orbitals > 32)
+        return invalid("exx_plan_set_batch: sizes must be >= 0 (block <= 32)");
+    P->pairs_per_batch = pairs_per_batch;
+    P->block_orbitals = block_orbitals;
+    std::fill(P->sched_key, P->sched_key + 4, -1);
+    return EXX_OK;
+}
+
+int exx_plan_destroy(exx_plan plan)
+{
+    Plan *P = as_plan(plan);
+    if (!P) return EXX_OK;
+    cudaDeviceSynchronize();
+    free_plan_buffers(*P);
+    timing_recycle(*P);
+    for (auto e : P->timing.pool) cudaEventDestroy(e);
+    delete P;
+    return EXX_OK;
+}
+
+int exx_plan_set_timing(exx_plan plan, int enable)
+{
+    Plan *P = as_plan(plan);
+    if (!P) return invalid("exx_plan_set_timing: plan is NULL");
+    EXX_CUDA(cudaDeviceSynchronize());
+    timing_recycle(*P);
+    P->timing.on = enable != 0;
+    return EXX_OK;
+}
+
+int exx_plan_get_timing(exx_plan plan, int kind, double *ms_h, long *launches_h)
+{
+    Plan *P = as_plan(plan);
+    if (!P || !ms_h || !launches_h) return invalid("exx_plan_get_timing: NULL argument");
+    if (kind < 0 || kind >= EXX_TIMING_KINDS) return invalid("exx_plan_get_timing: bad kind");
+    EXX_CUDA(cudaDeviceSynchronize());
+    double tot = 0.0;
+    long cnt = 0;
+    for (auto &r : P->timing.recs) {
+        if (r.kind != kind) continue;
+        float ms = 0.f;
+        EXX_CUDA(cudaEventElapsedTime(&ms, r.start, r.stop));
+        tot += ms;
+        cnt++;
+    }
+    *ms_h = tot;
+    *launches_h = cnt;
+    return EXX_OK;
+}
+
+int exx_plan_get(exx_plan plan, int which, double *dst_h, long count)
+{
+    Plan *P = as_plan(plan);
+    if (!P || !dst_h) return invalid("exx_plan_get: NULL argument");
+    if (which >= 0 && which < 3) {
+        if (count != P->n[which]) return invalid("exx_plan_get: count must equal n_d");
+        std::copy(P->lam[which].begin(), P->lam[which].end(), dst_h);
+        return EXX_OK;
+    }
+    if (which == 3) {
+        if (count != P->N) return invalid("exx_plan_get: count must equal N");
+        std::copy(P->F.begin(), P->F.end(), dst_h);
+        return EXX_OK;
+    }
+    return invalid("exx_plan_get: which must be 0..3");
+}
+
+long exx_plan_launch_count(exx_plan plan)
+{
+    Plan *P = as_plan(plan);
+    return P ? P->launches : -1;
+}
+
+int exx_apply(exx_plan plan, const double *Psi_occ, int n_occ, long ld_occ, const double *f,
+              const double *Psi_in, int n_in, long ld_in, double *out, long ld_out, exx_stream_t stream)
+{
+    Plan *P = as_plan(plan);
+    if (!P) return invalid("exx_apply: plan is NULL");
+    if (!Psi_occ || !f || !Psi_in || !out) return invalid("exx_apply: NULL array");
+    if (n_occ < 1 || n_in < 1 || n_occ > 65536 || n_in > 65536) return invalid("exx_apply: orbital counts must be in [1, 65536]");
+    if (ld_occ < P->N || ld_in < P->N || ld_out < P->N) return invalid("exx_apply: leading dimensions must be >= N");
+    const char *o0 = reinterpret_cast<const char *>(out);
+    const char *o1 = o0 + (size_t(n_in - 1) * ld_out + P->N) * sizeof(double);
+    auto overlaps = [&](const double *a, int n, long ld) {
+        const char *a0 = reinterpret_cast<const char *>(a);
+        const char *a1 = a0 + (size_t(n - 1) * ld + P->N) * sizeof(double);
+        return a0 < o1 && o0 < a1;
+    };
+    if (overlaps(Psi_occ, n_occ, ld_occ) || overlaps(Psi_in, n_in, ld_in)) return invalid("exx_apply: out overlaps an input");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const bool aliased = (Psi_in == Psi_occ) && (ld_in == ld_occ) && (n_in >= n_occ);
+    P->launches = 0;
+    if (int rc = ensure_schedule(*P, n_occ, n_in, aliased, s)) return rc;
+    const Schedule &S = P->sched;
+    const int2 *pairs_d = static_cast<const int2 *>(P->pairs_d.p);
+    const Block *blocks_d = static_cast<const Block *>(P->blocks_d.p);
+    if (P->prec == EXX_PREC_FP64) {
+        size_t fb = size_t(S.max_fields) * P->N * sizeof(double);
+        if (int rc = dev_reserve(P->work[0], fb)) return rc;
+        if (int rc = dev_reserve(P->work[1], fb)) return rc;
+        EXX_CUDA(cudaMemset2DAsync(out, size_t(ld_out) * sizeof(double), 0, size_t(P->N) * sizeof(double),
+                                   n_in, s));
+        for (size_t b = 0; b < S.batches.size(); ++b) {
+            const Batch &bt = S.batches[b];
+            double *V = nullptr;
+            if (int rc = fp64_solve_batch(*P, Psi_occ, ld_occ, Psi_in, ld_in, pairs_d + S.pair0[b], bt.nfields,
+                                          static_cast<double *>(P->work[0].p),
+                                          static_cast<double *>(P->work[1].p), &V, s))
+                return rc;
+            if (int rc = fp64_accumulate(*P, Psi_occ, ld_occ, Psi_in, ld_in, f, blocks_d + bt.block0, bt.nblocks,
+                                         V, out, ld_out, s))
+                return rc;
+        }
+        return EXX_OK;
+    }
+    // split precision on the tensor cores
+    const int prec = P->prec;
+    if (int rc = tc_prepare_orbitals(*P, Psi_occ, n_occ, ld_occ, f, Psi_in, n_in, ld_in, aliased, s)) return rc;
+    size_t fb = size_t(S.max_fields) * P->N * sizeof(float);
+    if (int rc = dev_reserve(P->work[0], fb)) return rc;
+    if (int rc = dev_reserve(P->work[1], fb)) return rc;
+    for (size_t b = 0; b < S.batches.size(); ++b) {
+        const Batch &bt = S.batches[b];
+        if (int rc = tc_solve_batch(*P, prec, pairs_d + S.pair0[b], bt.nfields, static_cast<float *>(P->work[0].p),
+                                    static_cast<float *>(P->work[1].p), s))
+            return rc;
+        if (int rc = tc_accumulate(*P, blocks_d + bt.block0, bt.nblocks, static_cast<float *>(P->work[0].p), s))
+            return rc;
+    }
+    return tc_finalize(*P, n_in, out, ld_out, s);
+}
+
+int exx_energy(exx_plan plan, const double *Psi_occ, int n_occ, long ld, const double *f, const double *VxPsi,
+               long ld_v, double *E_x_h, exx_stream_t stream)
+{
+    Plan *P = as_plan(plan);
+    if (!P) return invalid("exx_energy: plan is NULL");
+    if (!Psi_occ || !f || !VxPsi || !E_x_h) return invalid("exx_energy: NULL argument");
+    if (n_occ < 1 || ld < P->N || ld_v < P->N) return invalid("exx_energy: bad sizes");
+    return energy_fp64(*P, Psi_occ, n_occ, ld, f, VxPsi, ld_v, E_x_h, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int ace_build(exx_plan plan, const double *Psi, int n, long ld, const double *W, long ld_w, double *xi,
+              long ld_xi, double *M_out, int *info_h, exx_stream_t stream)
+{
+    Plan *P = as_plan(plan);
+    if (!P) return invalid("ace_build: plan is NULL");
+    if (!Psi || !W || !xi || !info_h) return invalid("ace_build: NULL argument");
+    if (n < 1 || n > 2048 || ld < P->N || ld_w < P->N || ld_xi < P->N) return invalid("ace_build: bad sizes");
+    *info_h = 0;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    P->launches = 0;
+    // device scratch: M (n x n), Linv (n x n), info
+    size_t nn = size_t(n) * n;
+    if (int rc = dev_reserve(P->info_d, 2 * nn * sizeof(double) + 256)) return rc;
+    double *M = M_out ? M_out : static_cast<double *>(P->info_d.p);
+    double *Linv = static_cast<double *>(P->info_d.p) + nn;
+    int *info_d = reinterpret_cast<int *>(static_cast<double *>(P->info_d.p) + 2 * nn);
+    if (int rc = gemm_fp64_tn_splitk(*P, n, n, P->N, Psi, ld, W, ld_w, P->dV, M, n, s)) return rc;
+    if (int rc = cholesky_neg_sym_and_inverse(*P, n, M, Linv, info_d, s)) return rc;
+    int info = 0;
+    EXX_CUDA(cudaMemcpyAsync(&info, info_d, sizeof(int), cudaMemcpyDeviceToHost, s));
+    EXX_CUDA(cudaStreamSynchronize(s));
+    if (info) {
+        *info_h = info;
+        set_error("ace_build: -sym(M) is not positive definite");
+        return EXX_ERR_NOT_POSDEF;
+    }
+    // xi = W Linv^T
+    if (int rc = gemm_fp64_nt(*P, P->N, n, n, W, ld_w, Linv, n, 1.0, xi, ld_xi, s)) return rc;
+    EXX_CUDA(cudaStreamSynchronize(s));
+    return EXX_OK;
+}
+
+int ace_apply(exx_plan plan, const double *xi, int n, long ld_xi, const double *Phi, int nphi, long ld_phi,
+              double *out, long ld_out, exx_stream_t stream)
+{
+    Plan *P = as_plan(plan);
+    if (!P) return invalid("ace_apply: plan is NULL");
+    if (!xi || !Phi || !out) return invalid("ace_apply: NULL argument");
+    if (n < 1 || nphi < 1 || n > 65536 || ld_xi < P->N || ld_phi < P->N || ld_out < P->N) return invalid("ace_apply: bad sizes");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    P->launches = 0;
+    size_t need = size_t(n) * nphi * sizeof(double);
+    if (int rc = dev_reserve(P->small_ws, need)) return rc;
+    double *chi = static_cast<double *>(P->small_ws.p);
+    // chi = xi^T Phi (n x nphi), out = -dV xi chi
+    if (int rc = gemm_fp64_tn_splitk(*P, n, nphi, P->N, xi, ld_xi, Phi, ld_phi, 1.0, chi, n, s)) return rc;
+    return gemm_fp64_nn(*P, P->N, nphi, n, xi, ld_xi, chi, n, -P->dV, out, ld_out, s);
+}
+
+int exx_ace_step_host(exx_plan plan, const double *Psi_h, int n, long ld, int n_occ, const double *f_h,
+                      double *xi_h, long ld_xi, double *E_x_h, int *info_h, exx_stream_t stream)
+{
+    Plan *P = as_plan(plan);
+    if (!P) return invalid("exx_ace_step_host: plan is NULL");
+    if (!Psi_h || !f_h || !xi_h || !E_x_h || !info_h) return invalid("exx_ace_step_host: NULL argument");
+    if (n < 1 || n_occ < 1 || n_occ > n || ld < P->N || ld_xi < P->N) return invalid("exx_ace_step_host: bad sizes");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t cols = size_t(P->N) * n * sizeof(double);
+    if (int rc = dev_reserve(P->host_stage_psi, cols)) return rc;
+    if (int rc = dev_reserve(P->host_stage_w, cols)) return rc;
+    if (int rc = dev_reserve(P->host_stage_xi, cols)) return rc;
+    if (int rc = dev_reserve(P->host_stage_f, size_t(n_occ) * sizeof(double))) return rc;
+    double *Psi = static_cast<double *>(P->host_stage_psi.p);
+    double *W = static_cast<double *>(P->host_stage_w.p);
+    double *xi = static_cast<double *>(P->host_stage_xi.p);
+    double *f = static_cast<double *>(P->host_stage_f.p);
+    EXX_CUDA(cudaMemcpy2DAsync(Psi, size_t(P->N) * sizeof(double), Psi_h, size_t(ld) * sizeof(double),
+                               size_t(P->N) * sizeof(double), n, cudaMemcpyHostToDevice, s));
+    EXX_CUDA(cudaMemcpyAsync(f, f_h, size_t(n_occ) * sizeof(double), cudaMemcpyHostToDevice, s));
+    long launches = 0;
+    if (int rc = exx_apply(plan, Psi, n_occ, P->N, f, Psi, n, P->N, W, P->N, stream)) return rc;
+    launches += P->launches;
+    if (int rc = exx_energy(plan, Psi, n_occ, P->N, f, W, P->N, E_x_h, stream)) return rc;
+    launches += P->launches;
+    int rc = ace_build(plan, Psi, n, P->N, W, P->N, xi, P->N, nullptr, info_h, stream);
+    launches += P->launches;
+    P->launches = launches;
+    if (rc) return rc;
+    EXX_CUDA(cudaMemcpy2DAsync(xi_h, size_t(ld_xi) * sizeof(double), xi, size_t(P->N) * sizeof(double),
+                               size_t(P->N) * sizeof(double), n, cudaMemcpyDeviceToHost, s));
+    EXX_CUDA(cudaStreamSynchronize(s));
+    return EXX_OK;
+}
+
+int exx_apply_batched(const exx_plan *plans, int nsys, const exx_apply_args *args, exx_stream_t stream)
+{
+    if (!plans || !args || nsys < 1) return invalid("exx_apply_batched: bad arguments");
+    for (int i = 0; i < nsys; ++i) {
+        if (int rc = exx_apply(plans[i], args[i].Psi_occ, args[i].n_occ, args[i].ld_occ, args[i].f,
+                               args[i].Psi_in, args[i].n_in, args[i].ld_in, args[i].out, args[i].ld_out, stream))
+            return rc;
+    }
+    return EXX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,304 @@
+// FP64 reductions and dense linear algebra of the path: exchange energy, the ACE
+// matrices of Sec. III.A (M = dV Psi^T W, Cholesky factor of -sym(M), its inverse,
+// xi = W L^{-T}) and the ACE application of Sec. III.B.
+#include "exx_internal.h"
+
+#include <algorithm>
+
+namespace exx {
+
+namespace {
+
+// Neumaier-compensated accumulator (s, c)
+struct KSum {
+    double s, c;
+};
+__device__ __forceinline__ void kadd(KSum &k, double x)
+{
+    double t = k.s + x;
+    if (fabs(k.s) >= fabs(x)) k.c += (k.s - t) + x;
+    else k.c += (x - t) + k.s;
+    k.s = t;
+}
+__device__ __forceinline__ void kmerge(KSum &a, const KSum &b)
+{
+    kadd(a, b.s);
+    a.c += b.c;
+}
+
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 512;
+
+// E partial sums over a fixed grid: element e = n*N + r handled by thread (e mod T);
+// every thread adds its elements in increasing e, the block merges in a fixed tree.
+__global__ void __launch_bounds__(kRedThreads)
+energy_partial_kernel(const double *psi, int n, long ld, const double *f, const double *v, long ldv,
+                      long N, double dV, KSum *partials)
+{
+    __shared__ KSum sh[kRedThreads];
+    KSum acc{0.0, 0.0};
+    const long total = long(n) * N;
+    const long T = long(gridDim.x) * blockDim.x;
+    for (long e = long(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += T) {
+        long col = e / N, r = e - col * N;
+        double w = 0.25 * f[col] * dV;
+        kadd(acc, w * psi[col * ld + r] * v[col * ldv + r]);
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int stride = kRedThreads / 2; stride > 0; stride >>= 1) {
+        if (threadIdx.x < stride) kmerge(sh[threadIdx.x], sh[threadIdx.x + stride]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+}
+
+__global__ void reduce_partials_kernel(const KSum *partials, int np, double *out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    KSum acc{0.0, 0.0};
+    for (int i = 0; i < np; ++i) kmerge(acc, partials[i]);
+    out[0] = acc.s + acc.c;
+}
+
+// ---- FP64 GEMMs (DFMA; GB300's FP64 rate makes these compute-bound) -----------------
+constexpr int kTile = 64, kKt = 16, kGemmThreads = 256;
+
+// C_z[i][j] = sum_{r in chunk z} A(r, i) B(r, j); A(r, i) = A[r + lda*i] (the columns of
+// A and B are orbitals, r runs over the grid).  Partial tiles go to ws[z].
+__global__ void __launch_bounds__(kGemmThreads)
+gemm_tn_partial_kernel(int na, int nb, long K, long kchunk, const double *A, long lda,
+                       const double *B, long ldb, double *ws)
+{
+    __shared__ double As[kKt][kTile + 1];
+    __shared__ double Bs[kKt][kTile + 1];
+    const int i0 = blockIdx.x * kTile, j0 = blockIdx.y * kTile;
+    const long k_begin = long(blockIdx.z) * kchunk;
+    const long k_end = min(K, k_begin + kchunk);
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    double acc[4][4] = {};
+    for (long k0 = k_begin; k0 < k_end; k0 += kKt) {
+        for (int t = threadIdx.x; t < kKt * kTile; t += kGemmThreads) {
+            int kk = t % kKt, ii = t / kKt;
+            long r = k0 + kk;
+            As[kk][ii] = (r < k_end && i0 + ii < na) ? A[r + lda * (i0 + ii)] : 0.0;
+            Bs[kk][ii] = (r < k_end && j0 + ii < nb) ? B[r + ldb * (j0 + ii)] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < kKt; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] = As[kk][ty + 16 * u];
+                b[u] = Bs[kk][tx + 16 * u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int w = 0; w < 4; ++w) acc[u][w] = fma(a[u], b[w], acc[u][w]);
+        }
+        __syncthreads();
+    }
+    double *wz = ws + size_t(blockIdx.z) * na * nb;
+    for (int u = 0; u < 4; ++u)
+        for (int w = 0; w < 4; ++w) {
+            int i = i0 + ty + 16 * u, j = j0 + tx + 16 * w;
+            if (i < na && j < nb) wz[i + size_t(na) * j] = acc[u][w];
+        }
+}
+
+__global__ void splitk_reduce_kernel(const double *ws, int nsplit, int na, int nb, double alpha,
+                                     double *C, int ldc)
+{
+    const long e = long(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= long(na) * nb) return;
+    int i = int(e % na), j = int(e / na);
+    double s = 0.0;
+    for (int z = 0; z < nsplit; ++z) s += ws[size_t(z) * na * nb + e];
+    C[i + size_t(ldc) * j] = alpha * s;
+}
+
+// C(r, j) = alpha * sum_k A(r, k) Bop(k, j), A(r, k) = A[r + lda*k],
+// Bop(k, j) = B[j*sbj + k*sbk];  r < M (grid rows), j < Nc, k < K.
+__global__ void __launch_bounds__(kGemmThreads)
+gemm_rows_kernel(long M, int Nc, int K, const double *A, long lda, const double *B, long sbj,
+                 long sbk, double alpha, double *C, long ldc)
+{
+    __shared__ double As[kKt][kTile + 1];
+    __shared__ double Bs[kKt][kTile + 1];
+    const long r0 = long(blockIdx.x) * kTile;
+    const int j0 = blockIdx.y * kTile;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    double acc[4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += kKt) {
+        for (int t = threadIdx.x; t < kKt * kTile; t += kGemmThreads) {
+            int rr = t % kTile, kk = t / kTile;
+            As[kk][rr] = (r0 + rr < M && k0 + kk < K) ? A[(r0 + rr) + lda * (k0 + kk)] : 0.0;
+            int jj = t % kTile;
+            Bs[kk][jj] = (j0 + jj < Nc && k0 + kk < K) ? B[(j0 + jj) * sbj + (k0 + kk) * sbk] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < kKt; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] = As[kk][tx + 16 * u];
+                b[u] = Bs[kk][ty + 16 * u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int w = 0; w < 4; ++w) acc[u][w] = fma(a[u], b[w], acc[u][w]);
+        }
+        __syncthreads();
+    }
+    for (int u = 0; u < 4; ++u)
+        for (int w = 0; w < 4; ++w) {
+            long r = r0 + tx + 16 * u;
+            int j = j0 + ty + 16 * w;
+            if (r < M && j < Nc) C[r + ldc * j] = alpha * acc[u][w];
+        }
+}
+
+// One CTA: A = -(M + M^T)/2 (lower part), right-looking Cholesky A = L L^T in place,
+// then Linv = L^{-1} (lower).  info_d[0] = 0 or 1 + failing pivot.
+constexpr int kCholThreads = 1024;
+__global__ void __launch_bounds__(kCholThreads)
+cholesky_inverse_kernel(int n, const double *M, double *L, double *Linv, int *info_d)
+{
+    __shared__ int failed;
+    const int tid = threadIdx.x;
+    for (long e = tid; e < long(n) * n; e += blockDim.x) {
+        int i = int(e % n), j = int(e / n);
+        L[e] = (i >= j) ? -0.5 * (M[i + size_t(n) * j] + M[j + size_t(n) * i]) : 0.0;
+        Linv[e] = 0.0;
+    }
+    if (tid == 0) {
+        failed = 0;
+        info_d[0] = 0;
+    }
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {
+        if (tid == 0) {
+            double d = L[j + size_t(n) * j];
+            if (!(d > 0.0)) {
+                failed = 1;
+                info_d[0] = j + 1;
+            } else {
+                L[j + size_t(n) * j] = sqrt(d);
+            }
+        }
+        __syncthreads();
+        if (failed) return;
+        const double djj = L[j + size_t(n) * j];
+        for (int i = j + 1 + tid; i < n; i += blockDim.x) L[i + size_t(n) * j] /= djj;
+        __syncthreads();
+        // trailing update of the lower triangle, columns k in (j, n), rows i >= k
+        const int m = n - j - 1;
+        for (long e = tid; e < long(m) * m; e += blockDim.x) {
+            int ii = int(e % m), kk = int(e / m);
+            if (ii < kk) continue;
+            int i = j + 1 + ii, k = j + 1 + kk;
+            L[i + size_t(n) * k] -= L[i + size_t(n) * j] * L[k + size_t(n) * j];
+        }
+        __syncthreads();
+    }
+    // Linv: row by row, X(i, c) = (delta_ic - sum_{k=c}^{i-1} L(i,k) X(k,c)) / L(i,i), c <= i
+    for (int i = 0; i < n; ++i) {
+        const double lii = L[i + size_t(n) * i];
+        for (int c = tid; c <= i; c += blockDim.x) {
+            double s = (c == i) ? 1.0 : 0.0;
+            for (int k = c; k < i; ++k) s -= L[i + size_t(n) * k] * Linv[k + size_t(n) * c];
+            Linv[i + size_t(n) * c] = s / lii;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+int energy_fp64(Plan &P, const double *psi, int n, long ld, const double *f, const double *v, long ld_v,
+                double *E_h, cudaStream_t s)
+{
+    size_t need = kRedBlocks * sizeof(KSum) + 64;
+    if (int rc = dev_reserve(P.red_ws, need)) return rc;
+    KSum *parts = static_cast<KSum *>(P.red_ws.p);
+    double *res = reinterpret_cast<double *>(static_cast<char *>(P.red_ws.p) + kRedBlocks * sizeof(KSum));
+    int tb = timing_begin(P, EXX_TIMING_ENERGY, s);
+    energy_partial_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(psi, n, ld, f, v, ld_v, P.N, P.dV, parts);
+    EXX_LAUNCH("energy_partial_kernel");
+    reduce_partials_kernel<<<1, 32, 0, s>>>(parts, kRedBlocks, res);
+    timing_end(P, tb, s);
+    EXX_LAUNCH("reduce_partials_kernel");
+    P.launches += 2;
+    EXX_CUDA(cudaMemcpyAsync(E_h, res, sizeof(double), cudaMemcpyDeviceToHost, s));
+    EXX_CUDA(cudaStreamSynchronize(s));
+    return EXX_OK;
+}
+
+int gemm_fp64_tn_splitk(Plan &P, int na, int nb, int K, const double *A, long lda, const double *B,
+                        long ldb, double alpha, double *C, int ldc, cudaStream_t s)
+{
+    const int gx = (na + kTile - 1) / kTile, gy = (nb + kTile - 1) / kTile;
+    // enough CTAs to fill the GPU twice over, each with a K chunk of at least 256
+    int nsplit = std::max(1, (2 * P.num_sms + gx * gy - 1) / (gx * gy));
+    long kchunk = (long(K) + nsplit - 1) / nsplit;
+    kchunk = ((kchunk + kKt - 1) / kKt) * kKt;
+    if (kchunk < 256) kchunk = 256;
+    nsplit = int((long(K) + kchunk - 1) / kchunk);
+    if (int rc = dev_reserve(P.gemm_ws, size_t(nsplit) * na * nb * sizeof(double))) return rc;
+    double *ws = static_cast<double *>(P.gemm_ws.p);
+    int tb = timing_begin(P, EXX_TIMING_GEMM, s);
+    gemm_tn_partial_kernel<<<dim3(gx, gy, nsplit), kGemmThreads, 0, s>>>(na, nb, K, kchunk, A, lda, B,
+                                                                         ldb, ws);
+    EXX_LAUNCH("gemm_tn_partial_kernel");
+    long tot = long(na) * nb;
+    splitk_reduce_kernel<<<unsigned((tot + 255) / 256), 256, 0, s>>>(ws, nsplit, na, nb, alpha, C, ldc);
+    timing_end(P, tb, s);
+    EXX_LAUNCH("splitk_reduce_kernel");
+    P.launches += 2;
+    return EXX_OK;
+}
+
+int gemm_fp64_nt(Plan &P, int M, int Nc, int K, const double *A, long lda, const double *B, long ldb,
+                 double alpha, double *C, long ldc, cudaStream_t s)
+{
+    // Bop(k, j) = B(j, k) = B[j + ldb*k]
+    dim3 grid(unsigned((long(M) + kTile - 1) / kTile), unsigned((Nc + kTile - 1) / kTile));
+    int tb = timing_begin(P, EXX_TIMING_GEMM, s);
+    gemm_rows_kernel<<<grid, kGemmThreads, 0, s>>>(M, Nc, K, A, lda, B, 1, ldb, alpha, C, ldc);
+    timing_end(P, tb, s);
+    EXX_LAUNCH("gemm_rows_kernel");
+    P.launches++;
+    return EXX_OK;
+}
+
+int gemm_fp64_nn(Plan &P, int M, int Nc, int K, const double *A, long lda, const double *B, long ldb,
+                 double alpha, double *C, long ldc, cudaStream_t s)
+{
+    // Bop(k, j) = B(k, j) = B[k + ldb*j]
+    dim3 grid(unsigned((long(M) + kTile - 1) / kTile), unsigned((Nc + kTile - 1) / kTile));
+    int tb = timing_begin(P, EXX_TIMING_GEMM, s);
+    gemm_rows_kernel<<<grid, kGemmThreads, 0, s>>>(M, Nc, K, A, lda, B, ldb, 1, alpha, C, ldc);
+    timing_end(P, tb, s);
+    EXX_LAUNCH("gemm_rows_kernel");
+    P.launches++;
+    return EXX_OK;
+}
+
+int cholesky_neg_sym_and_inverse(Plan &P, int n, const double *M, double *Linv, int *info_d,
+                                 cudaStream_t s)
+{
+    if (int rc = dev_reserve(P.small_ws, size_t(n) * n * sizeof(double))) return rc;
+    double *L = static_cast<double *>(P.small_ws.p);
+    int tb = timing_begin(P, EXX_TIMING_CHOL, s);
+    cholesky_inverse_kernel<<<1, kCholThreads, 0, s>>>(n, M, L, Linv, info_d);
+    timing_end(P, tb, s);
+    EXX_LAUNCH("cholesky_inverse_kernel");
+    P.launches++;
+    return EXX_OK;
+}
+
+}  // namespace exx

@@ -1,0 +1,179 @@
+"""GPU parity of the FP64 path against the CPU oracle, through the C interface.
+
+Bar: relative Frobenius error <= 1e-10 on VxPsi (the FP64 target), energies to 1e-11
+relative, ACE xi to 1e-9.  Sizes span many kernel tiles and ragged tails; the
+48^3 / 128-orbital workload is checked on sampled output columns the oracle computes
+one by one.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import pinmath as pm
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+
+
+@pytest.fixture(scope="module")
+def exx():
+    import paper_2501_16572_gb300 as m
+    m.load()
+    assert torch.cuda.is_available()
+    return m
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _run(exx, s, prec=0, batch=None, n_in=None):
+    plan = exx.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    plan.set_precision(prec)
+    if batch is not None:
+        plan.set_batch(*batch)
+    psi = _dev(s.psi if n_in is None else s.psi[:n_in])
+    f = _dev(s.f)
+    vx = plan.apply(psi[:s.n_occ], f, psi)
+    torch.cuda.synchronize()
+    return plan, psi, f, vx
+
+
+CASES = [
+    dict(n=(14, 12, 10), bc=(0, 1, 0), n_orb=6, kernel=0),
+    dict(n=(9, 16, 7), bc=(1, 1, 1), n_orb=5, kernel=1, omega=0.106),
+    dict(n=(20, 11, 13), bc=(1, 1, 0), n_orb=9, kernel=1, omega=0.106),
+    dict(n=(6, 6, 6), bc=(0, 0, 0), n_orb=4, kernel=0),
+    dict(n=(17, 19, 23), bc=(0, 0, 0), n_orb=11, kernel=0),
+    dict(n=(12, 10, 9), bc=(1, 0, 1), n_orb=7, kernel=2, omega=0.2),
+    dict(n=(2, 3, 4), bc=(0, 0, 0), n_orb=3, kernel=0),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "x".join(map(str, c["n"])))
+def test_fp64_exx_apply_matches_oracle(exx, case):
+    s = synth.small_system(h=0.4, seed=3, **case)
+    plan, psi, f, vx = _run(exx, s)
+    orc = oracle.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    ref = orc.exx_apply(s.psi[:s.n_occ], s.f, s.psi)
+    assert pm.rel(vx.cpu().numpy(), ref) < TOL64
+    e = plan.energy(psi[:s.n_occ], f, vx)
+    e_ref = orc.energy(s.psi[:s.n_occ], s.f, ref)
+    assert abs(e - e_ref) <= 1e-11 * abs(e_ref)
+
+
+def test_fp64_unoccupied_outputs_and_separate_inputs(exx):
+    """n_in > n_occ (ACE case) and a Psi_in that is a different buffer (no symmetry)."""
+    s = synth.small_system(n=(13, 11, 12), h=0.4, bc=(0, 0, 1), n_orb=10, kernel=0, seed=5, n_occ=6)
+    orc = oracle.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    ref = orc.exx_apply(s.psi[:6], s.f, s.psi)
+    plan = exx.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    psi = _dev(s.psi)
+    f = _dev(s.f)
+    vx = plan.apply(psi[:6], f, psi)
+    assert pm.rel(vx.cpu().numpy(), ref) < TOL64
+    other = psi.clone()
+    vx2 = plan.apply(psi[:6], f, other)
+    assert pm.rel(vx2.cpu().numpy(), ref) < TOL64
+    # subset of outputs, non-aliased, strided rows (ld > N)
+    big = torch.zeros((3, s.N + 37), dtype=torch.float64, device="cuda")
+    big[:, :s.N] = psi[[9, 2, 7]]
+    out = torch.zeros((3, s.N + 5), dtype=torch.float64, device="cuda")[:, :s.N]
+    plan.apply(psi[:6], f, big[:, :s.N], out=out)
+    assert pm.rel(out.cpu().numpy(), ref[[9, 2, 7]]) < TOL64
+
+
+@pytest.mark.parametrize("batch", [(1, 1), (4, 2), (64, 8), (9, 3), (0, 0)])
+def test_batch_invariance(exx, batch):
+    """Sec. II.B: the solution of a system does not depend on the batch it is solved in."""
+    s = synth.small_system(n=(11, 10, 12), h=0.4, bc=(1, 0, 0), n_orb=9, kernel=0, seed=6)
+    _, _, _, ref = _run(exx, s, batch=(0, 0))
+    _, _, _, vx = _run(exx, s, batch=batch)
+    assert pm.rel(vx.cpu().numpy(), ref.cpu().numpy()) < 1e-13
+
+
+def test_config1_dirichlet24_all_pairs(exx):
+    s = synth.config1()
+    plan, psi, f, vx = _run(exx, s)
+    orc = oracle.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    ref = orc.exx_apply(s.psi, s.f, s.psi)
+    assert pm.rel(vx.cpu().numpy(), ref) < TOL64
+    e = plan.energy(psi, f, vx)
+    assert abs(e - orc.energy(s.psi, s.f, ref)) <= 1e-11 * abs(e)
+    assert e < 0
+
+
+@pytest.fixture(scope="module")
+def cfg2():
+    return synth.config2()
+
+
+def test_config2_periodic48_sampled_columns(exx, cfg2):
+    """Full 48^3 / 128-orbital apply on the GPU; the oracle recomputes 3 sampled outputs."""
+    s = cfg2
+    plan, psi, f, vx = _run(exx, s)
+    orc = oracle.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    cols = [0, 77, 127]
+    ref = orc.exx_apply(s.psi, s.f, s.psi, cols=cols)
+    got = vx.cpu().numpy()[cols]
+    assert pm.rel(got, ref) < TOL64
+    # invariant at full size: M = dV Psi^T Vx Psi symmetric negative definite
+    M = (s.dV * (psi @ vx.T)).cpu().numpy()
+    assert np.linalg.norm(M - M.T) <= 1e-11 * np.linalg.norm(M)
+    assert np.max(np.linalg.eigvalsh(0.5 * (M + M.T))) < 0
+
+
+@pytest.mark.parametrize("case", [dict(n=(14, 12, 10), bc=(0, 1, 0), n_orb=8, kernel=0),
+                                  dict(n=(12, 12, 12), bc=(1, 1, 1), n_orb=12, kernel=1, omega=0.106)],
+                         ids=["mixed", "periodic"])
+def test_fp64_ace_matches_oracle(exx, case):
+    s = synth.small_system(h=0.4, seed=9, **case)
+    plan, psi, f, vx = _run(exx, s)
+    Md = torch.zeros((s.n_orb, s.n_orb), dtype=torch.float64, device="cuda")
+    xi = plan.ace_build(psi, vx, M=Md)
+    M_ref, L_ref, xi_ref = oracle.ace(s.psi, vx.cpu().numpy(), s.dV)
+    assert pm.rel(Md.cpu().numpy().T, M_ref) < 1e-12      # M_out is column-major
+    assert pm.rel(xi.cpu().numpy(), xi_ref) < 1e-10
+    back = plan.ace_apply(xi, psi)
+    assert pm.rel(back.cpu().numpy(), vx.cpu().numpy()) < 1e-10
+
+
+def test_ace_not_positive_definite(exx):
+    s = synth.small_system(n=(10, 9, 8), h=0.4, bc=(0, 0, 0), n_orb=4, kernel=0, seed=10)
+    plan = exx.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    psi = _dev(s.psi)
+    W = torch.zeros_like(psi)
+    W[:2] = -psi[:2]
+    with pytest.raises(exx.ExxError) as ei:
+        plan.ace_build(psi, W)
+    assert ei.value.status == exx.EXX_ERR_NOT_POSDEF and ei.value.pivot == 2
+
+
+def test_host_buffer_step_matches_device_path(exx):
+    s = synth.small_system(n=(12, 11, 10), h=0.4, bc=(1, 1, 0), n_orb=7, kernel=1, omega=0.106, seed=12)
+    plan, psi, f, vx = _run(exx, s)
+    e_dev = plan.energy(psi[:s.n_occ], f, vx)
+    xi_dev = plan.ace_build(psi, vx).cpu().numpy()
+    psi_h = torch.from_numpy(s.psi.copy()).pin_memory()
+    f_h = torch.from_numpy(s.f.copy()).pin_memory()
+    xi_h = torch.zeros_like(psi_h).pin_memory()
+    e = plan.ace_step_host(psi_h, s.n_occ, f_h, xi_h)
+    assert abs(e - e_dev) <= 1e-13 * abs(e_dev)
+    assert pm.rel(xi_h.numpy(), xi_dev) < 1e-13
+
+
+def test_timing_and_launch_counts(exx):
+    s = synth.small_system(n=(10, 9, 8), h=0.4, bc=(0, 0, 0), n_orb=5, kernel=0, seed=13)
+    plan = exx.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    psi, f = _dev(s.psi), _dev(s.f)
+    plan.set_timing(True)
+    plan.apply(psi, f, psi)
+    launches = plan.launch_count()
+    t = plan.timing()
+    plan.set_timing(False)
+    assert launches > 0
+    assert sum(n for _, n in t.values()) == launches
+    assert all(ms > 0 for ms, _ in t.values())

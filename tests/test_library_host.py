@@ -1,0 +1,161 @@
+"""CPU checks of libexx_gb300: it loads, exports every symbol its headers declare,
+rejects bad arguments before touching a GPU, and its host-side plan setup and pair
+scheduler are right (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from tests import pinmath as pm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2501_16572_gb300 import _build
+    _build.build()
+    import paper_2501_16572_gb300 as exx
+    L = exx.load()
+    D = ctypes.POINTER(ctypes.c_double)
+    L.exx_debug_fd_weights.argtypes = [ctypes.c_int, D]
+    L.exx_debug_second_derivative.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, D]
+    L.exx_debug_sym_eig.argtypes = [ctypes.c_int, D, D, D]
+    Lp = ctypes.POINTER(ctypes.c_long)
+    Ip = ctypes.POINTER(ctypes.c_int)
+    L.exx_debug_schedule.argtypes = [ctypes.c_int] * 5 + [Lp, Lp, Lp, Ip, Ip, Ip]
+    return L
+
+
+def _declared(header):
+    txt = open(os.path.join(ROOT, "include", header)).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?(?:int|long|void|char|double)\s*\*?\s*(\w+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol(lib):
+    import paper_2501_16572_gb300 as exx
+    decl = _declared("exx.h") + _declared("exx_debug.h")
+    assert "exx_apply" in decl and "ace_build" in decl and "exx_debug_schedule" in decl
+    for name in decl:
+        assert hasattr(lib, name), name
+    assert sorted(exx.EXPORTED) == sorted(_declared("exx.h"))
+
+
+def test_status_strings(lib):
+    lib.exx_status_string.restype = ctypes.c_char_p
+    for st in range(7):
+        s = lib.exx_status_string(st)
+        assert s and s.startswith(b"EXX_")
+    assert lib.exx_status_string(99) == b"unknown exx status"
+
+
+def test_invalid_arguments_rejected_on_host(lib):
+    import paper_2501_16572_gb300 as exx
+    h = ctypes.c_void_p()
+    bc = (ctypes.c_int * 3)(0, 0, 0)
+    create = lib.exx_plan_create
+    assert create(ctypes.byref(h), 1, 8, 8, 0.3, bc, 12, 0, 0.0) == exx.EXX_ERR_INVALID_ARG
+    assert create(ctypes.byref(h), 8, 8, 8, -0.3, bc, 12, 0, 0.0) == exx.EXX_ERR_INVALID_ARG
+    assert create(ctypes.byref(h), 8, 8, 8, 0.3, bc, 11, 0, 0.0) == exx.EXX_ERR_INVALID_ARG
+    assert create(ctypes.byref(h), 8, 8, 8, 0.3, bc, 12, 1, 0.0) == exx.EXX_ERR_INVALID_ARG
+    assert create(ctypes.byref(h), 8, 8, 8, 0.3, bc, 12, 7, 0.1) == exx.EXX_ERR_INVALID_ARG
+    per = (ctypes.c_int * 3)(1, 1, 1)
+    assert create(ctypes.byref(h), 8, 8, 8, 0.3, per, 12, 0, 0.0) == exx.EXX_ERR_UNSUPPORTED
+    bad = (ctypes.c_int * 3)(0, 2, 0)
+    assert create(ctypes.byref(h), 8, 8, 8, 0.3, bad, 12, 0, 0.0) == exx.EXX_ERR_INVALID_ARG
+    assert h.value is None
+    null = ctypes.c_void_p()
+    assert lib.exx_apply(null, null, 1, 8, null, null, 1, 8, null, 8, null) == exx.EXX_ERR_INVALID_ARG
+    lib.exx_last_error.restype = ctypes.c_char_p
+    assert b"plan is NULL" in lib.exx_last_error()
+
+
+@pytest.mark.parametrize("p", [1, 2, 6, 9])
+def test_fd_weights_match_exact(lib, p):
+    w = np.zeros(p + 1)
+    assert lib.exx_debug_fd_weights(p, w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == 0
+    np.testing.assert_allclose(w, [float(x) for x in pm.fd_weights_taylor(p)], rtol=1e-14, atol=1e-16)
+
+
+@pytest.mark.parametrize("n,bc,p", [(24, 0, 6), (48, 1, 6), (6, 1, 6), (6, 0, 6), (37, 0, 2), (144, 0, 6),
+                                    (72, 1, 6), (2, 0, 6), (3, 1, 1)])
+def test_plan_eigensolver(lib, n, bc, p):
+    """Library eigensolver (Householder + QL) vs the closed form / an independent solver."""
+    h = 0.25
+    D = np.zeros(n * n)
+    Dp = D.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert lib.exx_debug_second_derivative(n, h, bc, p, Dp) == 0
+    Dm = D.reshape(n, n, order="F")
+    np.testing.assert_allclose(Dm, pm.op1d_dense(n, h, bc, p), rtol=1e-15, atol=1e-12)
+    V = np.zeros(n * n)
+    lam = np.zeros(n)
+    assert lib.exx_debug_sym_eig(n, Dp, V.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                 lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == 0
+    V = V.reshape(n, n, order="F")
+    nrm = max(1.0, np.linalg.norm(Dm, 2))
+    assert np.linalg.norm(Dm @ V - V * lam[None, :]) <= 1e-13 * nrm * n
+    assert np.linalg.norm(V.T @ V - np.eye(n)) <= 1e-13 * n
+    assert np.all(np.diff(lam) >= 0)
+    np.testing.assert_allclose(lam, oracle.jacobi_eigh(Dm)[0], rtol=0, atol=1e-12 * nrm)
+
+
+def schedule(lib, n_occ, n_in, aliased, block, maxp):
+    Lp = ctypes.c_long
+    npairs, nb, nbl = Lp(), Lp(), Lp()
+    assert lib.exx_debug_schedule(n_occ, n_in, aliased, block, maxp, ctypes.byref(npairs), ctypes.byref(nb),
+                                  ctypes.byref(nbl), None, None, None) == 0
+    pairs = np.zeros(2 * npairs.value, dtype=np.int32)
+    batches = np.zeros(3 * nb.value, dtype=np.int32)
+    blocks = np.zeros(6 * nbl.value, dtype=np.int32)
+    Ip = ctypes.POINTER(ctypes.c_int)
+    assert lib.exx_debug_schedule(n_occ, n_in, aliased, block, maxp, ctypes.byref(npairs), ctypes.byref(nb),
+                                  ctypes.byref(nbl), pairs.ctypes.data_as(Ip), batches.ctypes.data_as(Ip),
+                                  blocks.ctypes.data_as(Ip)) == 0
+    return pairs.reshape(-1, 2), batches.reshape(-1, 3), blocks.reshape(-1, 6)
+
+
+@pytest.mark.parametrize("n_occ,n_in,aliased,block,maxp", [
+    (16, 16, 1, 8, 128), (128, 128, 1, 8, 128), (100, 128, 1, 8, 64), (13, 29, 1, 4, 16),
+    (7, 7, 1, 8, 64), (1, 5, 1, 8, 64), (10, 12, 0, 4, 48), (800, 1024, 1, 8, 512), (5, 3, 0, 2, 4)])
+def test_schedule_covers_each_pair_once_with_disjoint_outputs(lib, n_occ, n_in, aliased, block, maxp):
+    pairs, batches, blocks = schedule(lib, n_occ, n_in, aliased, block, maxp)
+    seen = {}
+    for m, n in pairs:
+        key = (min(m, n), max(m, n)) if (aliased and n < n_occ) else (m, n)
+        seen[key] = seen.get(key, 0) + 1
+    if aliased:
+        expect = {(m, n) for m in range(n_occ) for n in range(m, n_occ)}
+        expect |= {(m, n) for m in range(n_occ) for n in range(n_occ, n_in)}
+    else:
+        expect = {(m, n) for m in range(n_occ) for n in range(n_in)}
+    assert set(seen) == expect
+    assert all(v == 1 for v in seen.values())
+    p0 = 0
+    for nf, b0, nbk in batches:
+        assert nf <= max(maxp, block * block)
+        outs = set()
+        field = 0
+        for I0, nI, J0, nJ, kind, f0 in blocks[b0:b0 + nbk]:
+            assert f0 == field
+            w = set(range(J0, J0 + nJ)) if kind == 2 else set(range(I0, I0 + nI))
+            if kind == 0:
+                w |= set(range(J0, J0 + nJ))
+            assert not (outs & w), "two blocks of one batch write the same output"
+            outs |= w
+            cnt = nI * (nI + 1) // 2 if kind == 1 else nI * nJ
+            # the block's fields hold exactly its pairs, in order
+            blk_pairs = pairs[p0 + f0:p0 + f0 + cnt]
+            if kind == 1:
+                ref = [(I0 + x, I0 + y) for x in range(nI) for y in range(x, nI)]
+            else:
+                ref = [(I0 + x, J0 + y) for x in range(nI) for y in range(nJ)]
+            assert [tuple(v) for v in blk_pairs] == ref
+            field += cnt
+        assert field == nf
+        p0 += nf
+    assert p0 == len(pairs)
