@@ -27,6 +27,12 @@ int exx_debug_sym_eig(int n, const double *A, double *V, double *lam);
 int exx_debug_schedule(int n_occ, int n_in, int aliased, int block, int max_pairs, long *npairs,
                        long *nbatches, long *nblocks, int *pairs, int *batches, int *blocks);
 
+/* One 128 x n x k tensor-core tile (tcgen05.mma, one bf16 or tf32 piece per operand,
+ * FP32 accumulation): D (128 x n, row-major) = A (128 x k, row-major) B (n x k,
+ * row-major)^T.  DEVICE pointers; n, k multiples of 16 in [16, 256].  Synchronizes the
+ * device.  Checks the operand layout and descriptors of the split-precision path. */
+int exx_debug_tc_gemm(int tf32, int n, int k, const float *A, const float *B, float *D, int *err);
+
 #ifdef __cplusplus
 }
 #endif

@@ -61,7 +61,8 @@ static void free_plan_buffers(Plan &P)
         for (auto &b : row) dev_free(b);
     for (auto *b : {&P.F64, &P.F32, &P.work[0], &P.work[1], &P.work[2], &P.pairs_d, &P.blocks_d,
                     &P.acc_hi, &P.acc_lo, &P.g32, &P.psi32, &P.gemm_ws, &P.small_ws, &P.info_d,
-                    &P.red_ws, &P.host_stage_psi, &P.host_stage_f, &P.host_stage_xi, &P.host_stage_w})
+                    &P.red_ws, &P.host_stage_psi, &P.host_stage_f, &P.host_stage_xi, &P.host_stage_w,
+                    &P.err_d})
         dev_free(*b);
 }
 
@@ -359,8 +360,7 @@ int exx_apply(exx_plan plan, const double *Psi_occ, int n_occ, long ld_occ, cons
         if (int rc = tc_solve_batch(*P, prec, pairs_d + S.pair0[b], bt.nfields, static_cast<float *>(P->work[0].p),
                                     static_cast<float *>(P->work[1].p), s))
             return rc;
-        if (int rc = tc_accumulate(*P, blocks_d + bt.block0, bt.nblocks, static_cast<float *>(P->work[0].p), s))
-            return rc;
+        if (int rc = tc_accumulate(*P, blocks_d + bt.block0, bt.nblocks, P->tc_result, s)) return rc;
     }
     return tc_finalize(*P, n_in, out, ld_out, s);
 }
@@ -372,7 +372,9 @@ int exx_energy(exx_plan plan, const double *Psi_occ, int n_occ, long ld, const d
     if (!P) return invalid("exx_energy: plan is NULL");
     if (!Psi_occ || !f || !VxPsi || !E_x_h) return invalid("exx_energy: NULL argument");
     if (n_occ < 1 || ld < P->N || ld_v < P->N) return invalid("exx_energy: bad sizes");
-    return energy_fp64(*P, Psi_occ, n_occ, ld, f, VxPsi, ld_v, E_x_h, reinterpret_cast<cudaStream_t>(stream));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (int rc = tc_check_error(*P, s)) return rc;   // a bounded wait of an earlier exx_apply ran out
+    return energy_fp64(*P, Psi_occ, n_occ, ld, f, VxPsi, ld_v, E_x_h, s);
 }
 
 int ace_build(exx_plan plan, const double *Psi, int n, long ld, const double *W, long ld_w, double *xi,
@@ -384,6 +386,7 @@ int ace_build(exx_plan plan, const double *Psi, int n, long ld, const double *W,
     if (n < 1 || n > 2048 || ld < P->N || ld_w < P->N || ld_xi < P->N) return invalid("ace_build: bad sizes");
     *info_h = 0;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (int rc = tc_check_error(*P, s)) return rc;
     P->launches = 0;
     // device scratch: M (n x n), Linv (n x n), info
     size_t nn = size_t(n) * n;

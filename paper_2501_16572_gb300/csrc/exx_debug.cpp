@@ -55,4 +55,10 @@ int exx_debug_schedule(int n_occ, int n_in, int aliased, int block, int max_pair
     return EXX_OK;
 }
 
+int exx_debug_tc_gemm(int tf32, int n, int k, const float *A, const float *B, float *D, int *err)
+{
+    if (!A || !B || !D || !err) return EXX_ERR_INVALID_ARG;
+    return exx::tc_unit_gemm(tf32, n, k, A, B, D, err);
+}
+
 }  // extern "C"

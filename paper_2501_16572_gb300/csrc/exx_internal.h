@@ -126,6 +126,9 @@ struct Plan {
     DevBuf acc_hi, acc_lo, g32, psi32;  // split path accumulators and fp32 orbital copies
     DevBuf gemm_ws, small_ws, info_d, red_ws;
     DevBuf host_stage_psi, host_stage_f, host_stage_xi, host_stage_w;
+    DevBuf err_d;                   // device error word of the bounded waits
+    int tc_occ_off = 0;             // column of Psi_occ in the fp32 planes (0 when aliased)
+    float *tc_result = nullptr;     // buffer holding the last batch's solutions
     long launches = 0;
     Timing timing;
     // cached schedule
@@ -150,6 +153,8 @@ int tc_solve_batch(Plan &P, int prec, const int2 *pairs_d, int nfields, float *b
                    cudaStream_t s);
 int tc_accumulate(Plan &P, const Block *blocks_d, int nblocks, const float *V, cudaStream_t s);
 int tc_finalize(Plan &P, int n_in, double *out, long ld_out, cudaStream_t s);
+int tc_check_error(Plan &P, cudaStream_t s);
+int tc_unit_gemm(int tf32, int n, int k, const float *A, const float *B, float *D, int *err);
 
 // reductions, GEMM, Cholesky (exx_linalg.cu)
 int energy_fp64(Plan &P, const double *psi, int n, long ld, const double *f, const double *v,

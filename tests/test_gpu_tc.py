@@ -1,0 +1,149 @@
+"""GPU checks of the split-precision tensor-core path (tcgen05), through the C interface.
+
+1. One 128 x n x k tcgen05 tile with bf16 / tf32 operands against an FP64 matmul of the
+   same rounded operands (checks descriptors, operand layout, TMEM read-back).
+2. exx_apply in BF16X6 and TF32X3 against the CPU oracle: <= 1e-6 relative Frobenius on
+   VxPsi and <= 1e-8 relative on E_x (the split-precision targets); BF16X3 is reported
+   against its own, looser bound (two bf16 pieces carry ~16 bits).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import pinmath as pm
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SPLIT = {"bf16x6": (3, 1e-6, 1e-8), "tf32x3": (2, 1e-6, 1e-8), "bf16x3": (1, 1e-4, 1e-6)}
+
+
+@pytest.fixture(scope="module")
+def exx():
+    import paper_2501_16572_gb300 as m
+    L = m.load()
+    vp = ctypes.c_void_p
+    L.exx_debug_tc_gemm.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]
+    return m
+
+
+def _round_tf32(x):
+    u = x.astype(np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0xFFF + ((u >> 13) & 1)) & 0xFFFFE000
+    return u.astype(np.uint32).view(np.float32)
+
+
+@pytest.mark.parametrize("tf32", [0, 1], ids=["bf16", "tf32"])
+@pytest.mark.parametrize("n,k", [(16, 16), (48, 48), (64, 32), (128, 96), (256, 64), (32, 144)])
+def test_single_tile_tcgen05_gemm(exx, tf32, n, k):
+    rng = np.random.Generator(np.random.PCG64(n * 1000 + k + tf32))
+    A = rng.normal(size=(128, k)).astype(np.float32)
+    B = rng.normal(size=(n, k)).astype(np.float32)
+    if tf32:
+        A, B = _round_tf32(A), _round_tf32(B)
+    else:
+        A = torch.from_numpy(A).to(torch.bfloat16).float().numpy()
+        B = torch.from_numpy(B).to(torch.bfloat16).float().numpy()
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    dD = torch.zeros((128, n), dtype=torch.float32, device="cuda")
+    err = torch.zeros(4, dtype=torch.int32, device="cuda")
+    rc = exx.load().exx_debug_tc_gemm(tf32, n, k, dA.data_ptr(), dB.data_ptr(), dD.data_ptr(), err.data_ptr())
+    assert rc == 0
+    assert int(err[0]) == 0
+    ref = A.astype(np.float64) @ B.astype(np.float64).T
+    got = dD.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(np.abs(ref))
+
+
+def _apply(exx, s, prec, batch=None):
+    plan = exx.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    plan.set_precision(prec)
+    if batch:
+        plan.set_batch(*batch)
+    psi = torch.from_numpy(s.psi).cuda()
+    f = torch.from_numpy(s.f).cuda()
+    vx = plan.apply(psi[:s.n_occ], f, psi)
+    e = plan.energy(psi[:s.n_occ], f, vx)
+    return plan, psi, f, vx, e
+
+
+CASES = [
+    dict(n=(14, 12, 10), bc=(0, 1, 0), n_orb=6, kernel=0),
+    dict(n=(16, 16, 16), bc=(1, 1, 1), n_orb=9, kernel=1, omega=0.106),
+    dict(n=(20, 11, 13), bc=(1, 1, 0), n_orb=8, kernel=1, omega=0.106),
+    dict(n=(17, 19, 23), bc=(0, 0, 0), n_orb=7, kernel=0),
+]
+
+
+@pytest.mark.parametrize("name", list(SPLIT))
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "x".join(map(str, c["n"])))
+def test_split_exx_apply_matches_oracle(exx, name, case):
+    code, tol_v, tol_e = SPLIT[name]
+    s = synth.small_system(h=0.4, seed=21, **case)
+    plan, psi, f, vx, e = _apply(exx, s, code)
+    orc = oracle.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    ref = orc.exx_apply(s.psi[:s.n_occ], s.f, s.psi)
+    e_ref = orc.energy(s.psi[:s.n_occ], s.f, ref)
+    err_v = pm.rel(vx.cpu().numpy(), ref)
+    err_e = abs(e - e_ref) / abs(e_ref)
+    print(f"{name} {case['n']}: VxPsi {err_v:.2e}  E_x {err_e:.2e}")
+    assert err_v < tol_v
+    assert err_e < tol_e
+
+
+@pytest.mark.parametrize("name", ["bf16x6", "tf32x3"])
+def test_split_config1_all_pairs(exx, name):
+    code, tol_v, tol_e = SPLIT[name]
+    s = synth.config1()
+    plan, psi, f, vx, e = _apply(exx, s, code)
+    orc = oracle.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    ref = orc.exx_apply(s.psi, s.f, s.psi)
+    e_ref = orc.energy(s.psi, s.f, ref)
+    assert pm.rel(vx.cpu().numpy(), ref) < tol_v
+    assert abs(e - e_ref) <= tol_e * abs(e_ref)
+
+
+@pytest.mark.parametrize("name", ["bf16x6", "tf32x3"])
+def test_split_batch_invariance_and_separate_inputs(exx, name):
+    code = SPLIT[name][0]
+    s = synth.small_system(n=(13, 11, 12), h=0.4, bc=(0, 0, 1), n_orb=10, kernel=0, seed=5, n_occ=6)
+    _, psi, f, ref, _ = _apply(exx, s, code, batch=(0, 0))
+    _, _, _, vx, _ = _apply(exx, s, code, batch=(4, 2))
+    # the same solves in different batches: identical up to the compensated sum order
+    assert pm.rel(vx.cpu().numpy(), ref.cpu().numpy()) < 1e-9
+    plan = exx.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    plan.set_precision(code)
+    other = psi.clone()
+    vx2 = plan.apply(psi[:6], f, other)
+    orc = oracle.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    full = orc.exx_apply(s.psi[:6], s.f, s.psi)
+    assert pm.rel(vx2.cpu().numpy(), full) < 1e-6
+
+
+@pytest.fixture(scope="module")
+def cfg2():
+    return synth.config2()
+
+
+@pytest.mark.parametrize("name", ["bf16x6", "tf32x3"])
+def test_split_config2_sampled_columns(exx, cfg2, name):
+    """48^3 periodic screened, 128 orbitals: 3 sampled outputs vs the oracle, E_x and
+    xi vs the FP64 path (which the oracle pins to 1e-13 in test_gpu_fp64)."""
+    code, tol_v, tol_e = SPLIT[name]
+    s = cfg2
+    plan, psi, f, vx, e = _apply(exx, s, code)
+    cols = [0, 77, 127]
+    orc = oracle.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    ref = orc.exx_apply(s.psi, s.f, s.psi, cols=cols)
+    err_cols = pm.rel(vx.cpu().numpy()[cols], ref)
+    p64 = exx.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    vx64 = p64.apply(psi, f, psi)
+    e64 = p64.energy(psi, f, vx64)
+    err_full = float(torch.linalg.norm(vx - vx64) / torch.linalg.norm(vx64))
+    print(f"{name} config2: sampled {err_cols:.2e} full-vs-fp64 {err_full:.2e} E_x {abs(e - e64) / abs(e64):.2e}")
+    assert err_cols < tol_v
+    assert err_full < tol_v
+    assert abs(e - e64) <= tol_e * abs(e64)
