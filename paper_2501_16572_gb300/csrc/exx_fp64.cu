@@ -251,7 +251,7 @@ int fp64_upload(Plan &P)
     // F in the P3 layout: [b][a][c] -> F(a, b, c)
     const int n1 = P.n[0], n2 = P.n[1], n3 = P.n[2];
     std::vector<double> F3(size_t(P.N));
-    std::vector<float> F3f(size_t(P.N));
+    std::vector<float> F3f(2 * size_t(P.N));   // hi plane, then lo plane
     for (int b = 0; b < n2; ++b)
         for (int a = 0; a < n1; ++a)
             for (int c = 0; c < n3; ++c) {
@@ -259,6 +259,7 @@ int fp64_upload(Plan &P)
                 size_t idx = size_t(b) * n1 * n3 + size_t(a) * n3 + c;
                 F3[idx] = v;
                 F3f[idx] = float(v);
+                F3f[idx + size_t(P.N)] = float(v - double(float(v)));
             }
     if (int rc = dev_reserve(P.F64, F3.size() * sizeof(double))) return rc;
     EXX_CUDA(cudaMemcpy(P.F64.p, F3.data(), F3.size() * sizeof(double), cudaMemcpyHostToDevice));

@@ -116,7 +116,7 @@ struct Plan {
     // FP64 path: per pass the K x K contraction matrix B[k*K + j] (output j, input k)
     DevBuf B64[6];                  // P1, P2, P3-forward, P3-inverse, P4, P5
     DevBuf F64;                     // F in the P3 layout [b][a][c]
-    DevBuf F32;                     // same, float
+    DevBuf F32;                     // same as two float planes, hi then lo
     // tensor path: per pass and precision the B operand pieces, canonical SMEM image
     DevBuf Btc[4][6];               // [prec][pass slot]
     size_t Btc_bytes[4][6] = {};

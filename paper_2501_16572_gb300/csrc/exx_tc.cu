@@ -3,21 +3,32 @@
 // Each mode product of Sec. II.B is a GEMM  D[row][n] = sum_k A[row][k] B[n][k]  where a
 // row is a pencil of the grid function along the contracted axis (128 rows per tile,
 // one row per thread, one TMEM lane per row) and B is the 1D eigenvector matrix (or its
-// transpose).  Operands are split into bf16 or tf32 pieces, x = x0 + x1 (+ x2), and the
-// cross products that matter are accumulated in one FP32 TMEM accumulator:
-//   BF16X3: x1*y0 + x0*y1 + x0*y0          (2 bf16 pieces, ~16 significant bits)
-//   BF16X6: x2*y0 + x1*y1 + x0*y2 + x1*y0 + x0*y1 + x0*y0   (3 pieces, ~24 bits)
-//   TF32X3: x1*y0 + x0*y1 + x0*y0          (2 tf32 pieces, ~22 bits)
-// smallest terms first.  The pair density psi_m psi_n is formed in the prologue from
-// compensated FP32 copies of the orbitals (hi + lo), the Hadamard scaling by f(Lambda)
-// sits between the forward and the inverse y products of pass 3 (both on-chip), and the
-// accumulation over pairs is a separate compensated FP32 kernel.
+// transpose).  Two ways of splitting the FP32 operands are built:
+//
+//  * Fixed-point bf16 slices (BF16X3: 2 slices, BF16X6: 3 slices).  Every row of A and
+//    every row of B gets a power-of-two scale from its largest entry, and the scaled
+//    row is cut into integer slices of at most 8 bits, x = 2^(e-7) (q0 + q1/2^8 + q2/2^16),
+//    stored exactly as bf16.  Slice products of one "level" (i + j = l) share one unit,
+//    so each level is summed in its own TMEM accumulator as an integer below 2^24: the
+//    tensor core never rounds.  The levels are combined and rescaled in FP32 in the
+//    epilogue.  The result is the fixed-point product to about 2^-8S of the row maxima,
+//    with round-to-nearest slicing and no directed rounding anywhere.
+//  * Floating tf32 split (TF32X3): x = x0 + x1 with x0 = tf32(x), x1 = tf32(x - x0), the
+//    three leading cross products accumulated in one FP32 accumulator.  The tensor core
+//    rounds its FP32 accumulation toward zero, which biases every product slightly
+//    toward zero; this form is kept for comparison.
+//
+// The pair density psi_m psi_n is formed in the prologue from compensated FP32 copies of
+// the orbitals (hi + lo), the Hadamard scaling by f(Lambda) sits between the forward and
+// inverse y products of pass 3 (both on-chip), and the accumulation over pairs is a
+// separate compensated FP32 kernel.
 #include "exx_internal.h"
 #include "tc_ptx.cuh"
 
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 
 namespace exx {
@@ -27,35 +38,38 @@ namespace {
 constexpr int kRows = 128;          // tile rows = TMEM lanes = threads
 constexpr uint32_t kWaitLimit = 1u << 22;
 
+enum { MODE_FLOAT_TF32 = 0, MODE_FIXED_BF16 = 1 };
+
 struct PrecInfo {
-    bool tf32;
-    int np;          // pieces per operand
+    int mode;
+    int S;           // pieces (float) or slices (fixed) of the data operand A
+    int SB;          // pieces / slices of the matrix operand B
     int es;          // bytes per element
-    int nprod;       // products
+    int nacc;        // TMEM accumulators per GEMM
 };
+// BF16X6 carries the matrices with a fourth slice, used only against the leading data
+// slice: the matrices are shared by every pair, so their representation error does not
+// average out over pairs the way the data's does.
 __host__ __device__ inline PrecInfo prec_info(int prec)
 {
     switch (prec) {
-    case EXX_PREC_BF16X3: return {false, 2, 2, 3};
-    case EXX_PREC_BF16X6: return {false, 3, 2, 6};
-    default: return {true, 2, 4, 3};   // TF32X3
-    }
-}
-// products (a piece, b piece), smallest first
-__host__ __device__ inline void product(int prec, int i, int &pa, int &pb)
-{
-    if (prec == EXX_PREC_BF16X6) {
-        const int A[6] = {2, 1, 0, 1, 0, 0}, B[6] = {0, 1, 2, 0, 1, 0};
-        pa = A[i];
-        pb = B[i];
-    } else {
-        const int A[3] = {1, 0, 0}, B[3] = {0, 1, 0};
-        pa = A[i];
-        pb = B[i];
+    case EXX_PREC_BF16X3: return {MODE_FIXED_BF16, 2, 2, 2, 2};
+    case EXX_PREC_BF16X6: return {MODE_FIXED_BF16, 3, 4, 2, 4};
+    default: return {MODE_FLOAT_TF32, 2, 2, 4, 1};   // TF32X3
     }
 }
 
 inline int pad16(int n) { return (n + 15) & ~15; }
+inline int pow2_cols(int c) { return c <= 32 ? 32 : c <= 64 ? 64 : c <= 128 ? 128 : c <= 256 ? 256 : 512; }
+
+// bytes of one operand image: SB pieces of Np x Np, then (fixed mode) Np column scales
+inline size_t image_bytes(int prec, int Np)
+{
+    const PrecInfo pi = prec_info(prec);
+    size_t b = size_t(pi.SB) * Np * Np * pi.es;
+    if (pi.mode == MODE_FIXED_BF16) b += size_t(Np) * 4;
+    return (b + 15) & ~size_t(15);
+}
 
 // canonical K-major no-swizzle image: byte offset of (row, 16-byte chunk c)
 __host__ __device__ inline uint32_t img_off(int row, int c, uint32_t sbo)
@@ -64,16 +78,6 @@ __host__ __device__ inline uint32_t img_off(int row, int c, uint32_t sbo)
 }
 
 // ---- host rounding (round to nearest even) ----
-inline float host_bf16(double v)
-{
-    float f = float(v);
-    uint32_t u;
-    std::memcpy(&u, &f, 4);
-    u += 0x7FFFu + ((u >> 16) & 1u);
-    u &= 0xFFFF0000u;
-    std::memcpy(&f, &u, 4);
-    return f;
-}
 inline float host_tf32(double v)
 {
     float f = float(v);
@@ -85,51 +89,45 @@ inline float host_tf32(double v)
     return f;
 }
 
-// ---- device: split a value (hi + lo) into pieces ----
-template <bool TF32, int NP>
-__device__ __forceinline__ void split(float hi, float lo, float (&p)[3])
+// ---- device: operand pieces -------------------------------------------------------------
+// Floating tf32 split of (hi + lo).
+__device__ __forceinline__ void split_tf32(float hi, float lo, float (&p)[3])
 {
-    if (TF32) {
-        p[0] = tc::to_tf32(hi);
-        p[1] = tc::to_tf32((hi - p[0]) + lo);
-        p[2] = 0.f;
-    } else {
-        p[0] = __bfloat162float(__float2bfloat16_rn(hi));
-        float r = (hi - p[0]) + lo;
-        p[1] = __bfloat162float(__float2bfloat16_rn(r));
-        p[2] = (NP == 3) ? __bfloat162float(__float2bfloat16_rn(r - p[1])) : 0.f;
-    }
+    p[0] = tc::to_tf32(hi);
+    p[1] = tc::to_tf32((hi - p[0]) + lo);
+    p[2] = 0.f;
 }
 
-// Write one 16-byte chunk per piece (8 bf16 or 4 tf32 values of row `row`).
-template <bool TF32, int NP>
-__device__ __forceinline__ void put_chunk(uint8_t *img, uint32_t piece_bytes, int row, int c, uint32_t sbo,
-                                          const float *hi, const float *lo)
+// Fixed-point slices of (hi + lo) * s, s = 2^(7 - e): integers of at most 8 bits.
+template <int S>
+__device__ __forceinline__ void slice_fixed(float hi, float lo, float s, float (&q)[3])
 {
-    constexpr int EPC = TF32 ? 4 : 8;   // elements per 16-byte chunk
-    float pc[3][EPC];
-#pragma unroll
-    for (int e = 0; e < EPC; ++e) {
-        float p[3];
-        split<TF32, NP>(hi[e], lo ? lo[e] : 0.f, p);
-#pragma unroll
-        for (int q = 0; q < 3; ++q) pc[q][e] = p[q];
-    }
+    const float t = hi * s;
+    q[0] = rintf(t);
+    const float t1 = ((t - q[0]) + lo * s) * 256.f;
+    q[1] = (S >= 2) ? rintf(t1) : 0.f;
+    q[2] = (S >= 3) ? rintf((t1 - q[1]) * 256.f) : 0.f;
+}
+
+// Store one 16-byte chunk per piece: vals[q][e] for e < 16/ES elements of row `row`.
+template <int ES, int S>
+__device__ __forceinline__ void store_chunk(uint8_t *img, uint32_t piece_bytes, int row, int c, uint32_t sbo,
+                                            const float (&vals)[3][8])
+{
     const uint32_t off = img_off(row, c, sbo);
 #pragma unroll
-    for (int q = 0; q < NP; ++q) {
+    for (int q = 0; q < S; ++q) {
         uint4 v;
-        if (TF32) {
-            v.x = __float_as_uint(pc[q][0]);
-            v.y = __float_as_uint(pc[q][1]);
-            v.z = __float_as_uint(pc[q][2]);
-            v.w = __float_as_uint(pc[q][3]);
+        if (ES == 4) {
+            v = make_uint4(__float_as_uint(vals[q][0]), __float_as_uint(vals[q][1]), __float_as_uint(vals[q][2]),
+                           __float_as_uint(vals[q][3]));
         } else {
             uint32_t w[4];
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
-                uint32_t lo16 = __float_as_uint(pc[q][2 * t]) >> 16;
-                uint32_t hi16 = __float_as_uint(pc[q][2 * t + 1]) & 0xFFFF0000u;
+                // values are bf16-exact (small integers or bf16-rounded): take the top half
+                uint32_t lo16 = __float_as_uint(vals[q][2 * t]) >> 16;
+                uint32_t hi16 = __float_as_uint(vals[q][2 * t + 1]) & 0xFFFF0000u;
                 w[t] = lo16 | hi16;
             }
             v = make_uint4(w[0], w[1], w[2], w[3]);
@@ -138,25 +136,68 @@ __device__ __forceinline__ void put_chunk(uint8_t *img, uint32_t piece_bytes, in
     }
 }
 
-// Issue the split products of one GEMM (A pieces x B pieces) into TMEM column d_col.
-template <bool TF32>
-__device__ __forceinline__ void issue_gemm(int prec, uint32_t d_tmem, uint32_t a_base, uint32_t a_piece,
-                                           uint32_t a_sbo, uint32_t b_base, uint32_t b_piece, uint32_t b_sbo,
-                                           int ksteps, uint32_t idesc)
+// Issue one GEMM into the accumulator(s) starting at TMEM column `d`.  Fixed mode:
+// level l < S holds the products (i, l - i); level S (when SB > S) the product (0, S).
+template <int MODE, int S, int SB>
+__device__ __forceinline__ void issue_gemm(uint32_t d, int Np, uint32_t a_base, uint32_t a_piece, uint32_t b_base,
+                                           uint32_t b_piece, uint32_t sbo, int ksteps, uint32_t idesc)
 {
-    const PrecInfo pi = prec_info(prec);
-    uint32_t acc = 0;
-    for (int t = 0; t < pi.nprod; ++t) {
-        int pa, pb;
-        product(prec, t, pa, pb);
-        for (int ks = 0; ks < ksteps; ++ks) {
-            uint64_t ad = tc::smem_desc(a_base + pa * a_piece + ks * 256u, 128u, a_sbo);
-            uint64_t bd = tc::smem_desc(b_base + pb * b_piece + ks * 256u, 128u, b_sbo);
-            if (TF32) tc::mma_tf32(d_tmem, ad, bd, idesc, acc);
-            else tc::mma_bf16(d_tmem, ad, bd, idesc, acc);
-            acc = 1;
+    if (MODE == MODE_FLOAT_TF32) {
+        const int PA[3] = {1, 0, 0}, PB[3] = {0, 1, 0};   // small terms first
+        uint32_t acc = 0;
+        for (int t = 0; t < 3; ++t)
+            for (int ks = 0; ks < ksteps; ++ks) {
+                uint64_t ad = tc::smem_desc(a_base + PA[t] * a_piece + ks * 256u, 128u, sbo);
+                uint64_t bd = tc::smem_desc(b_base + PB[t] * b_piece + ks * 256u, 128u, sbo);
+                tc::mma_tf32(d, ad, bd, idesc, acc);
+                acc = 1;
+            }
+    } else {
+        for (int l = 0; l < S; ++l) {
+            uint32_t acc = 0;
+            for (int i = 0; i <= l; ++i) {
+                const int j = l - i;
+                for (int ks = 0; ks < ksteps; ++ks) {
+                    uint64_t ad = tc::smem_desc(a_base + i * a_piece + ks * 256u, 128u, sbo);
+                    uint64_t bd = tc::smem_desc(b_base + j * b_piece + ks * 256u, 128u, sbo);
+                    tc::mma_bf16(d + uint32_t(l * Np), ad, bd, idesc, acc);
+                    acc = 1;
+                }
+            }
+        }
+        if (SB > S) {
+            for (int ks = 0; ks < ksteps; ++ks) {
+                uint64_t ad = tc::smem_desc(a_base + ks * 256u, 128u, sbo);
+                uint64_t bd = tc::smem_desc(b_base + S * b_piece + ks * 256u, 128u, sbo);
+                tc::mma_bf16(d + uint32_t(S * Np), ad, bd, idesc, ks > 0);
+            }
         }
     }
+}
+
+// Read 16 result columns [c0, c0+16) of this thread's row, combining the NACC levels
+// (level l carries weight 2^(-8 l)) and applying the row and column scales.
+template <int MODE, int NACC>
+__device__ __forceinline__ void read_result(uint32_t d, int Np, int c0, float rs, const float *cs, float (&v)[16])
+{
+    if (MODE == MODE_FLOAT_TF32) {
+        tc::tmem_ld16(d + uint32_t(c0), v);
+        return;
+    }
+    float t[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) t[e] = 0.f;
+#pragma unroll
+    for (int l = NACC - 1; l >= 1; --l) {
+        float lv[16];
+        tc::tmem_ld16(d + uint32_t(l * Np + c0), lv);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) t[e] = (lv[e] + t[e]) * (1.f / 256.f);
+    }
+    float l0[16];
+    tc::tmem_ld16(d + uint32_t(c0), l0);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = (l0[e] + t[e]) * rs * cs[c0 + e];
 }
 
 // ---------------------------------------------------------------------------------------
@@ -166,38 +207,39 @@ struct TcPassArgs {
     long N;
     const float *in;
     float *out;
-    const uint8_t *B1, *B2;         // operand images (pieces concatenated)
-    const float *F;                 // [col][row] scaling for the double pass
+    const uint8_t *B1, *B2;         // operand images
+    uint32_t img_bytes;             // bytes of one image
+    const float *F, *Flo;           // [col][row] scaling for the double pass, hi + lo
     const float *psi_hi, *psi_lo;   // fp32 orbital planes (pair prologue)
     int occ_off;                    // column offset of the occupied set in the planes
     const int2 *pairs;
     int *err;
 };
 
-template <bool TF32, int NP, int LOAD, int STORE, bool DOUBLE>
-__global__ void __launch_bounds__(kRows, 1) tc_pass_kernel(TcPassArgs a, int prec)
+template <int MODE, int S, int SB, int LOAD, int STORE, bool DOUBLE>
+__global__ void __launch_bounds__(kRows, 1) tc_pass_kernel(TcPassArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
-    constexpr int ES = TF32 ? 4 : 2;
+    constexpr int ES = MODE == MODE_FLOAT_TF32 ? 4 : 2;
     constexpr int EPC = 16 / ES;
-    const int Kp = a.Np;
-    const uint32_t a_sbo = uint32_t(Kp) * ES * 8;     // bytes per 8-row group
-    const uint32_t b_sbo = a_sbo;
+    constexpr int NACC = MODE == MODE_FLOAT_TF32 ? 1 : (SB > S ? S + 1 : S);
+    const int Np = a.Np, Kp = a.Np;
+    const uint32_t sbo = uint32_t(Kp) * ES * 8;          // bytes per 8-row group
     const uint32_t a_piece = uint32_t(kRows) * Kp * ES;
-    const uint32_t b_piece = uint32_t(a.Np) * Kp * ES;
-    const uint32_t b_bytes = b_piece * NP;
+    const uint32_t b_piece = uint32_t(Np) * Kp * ES;
     uint8_t *sB1 = smem;
-    uint8_t *sB2 = smem + b_bytes;
-    uint8_t *sA = smem + (DOUBLE ? 2 : 1) * b_bytes;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sA + a_piece * NP);
+    uint8_t *sB2 = smem + a.img_bytes;
+    uint8_t *sA = smem + (DOUBLE ? 2 : 1) * a.img_bytes;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sA + a_piece * S);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
     int *sflag = reinterpret_cast<int *>(tslot + 1);
+    const float *cs1 = reinterpret_cast<const float *>(sB1 + SB * b_piece);
+    const float *cs2 = reinterpret_cast<const float *>(sB2 + SB * b_piece);
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int ncols_tmem = DOUBLE ? (2 * a.Np <= 32 ? 32 : 2 * a.Np <= 64 ? 64 : 2 * a.Np <= 128 ? 128 : 256)
-                                  : (a.Np <= 32 ? 32 : a.Np <= 64 ? 64 : a.Np <= 128 ? 128 : 256);
+    const int ncols = NACC * Np <= 32 ? 32 : NACC * Np <= 64 ? 64 : NACC * Np <= 128 ? 128 : NACC * Np <= 256 ? 256 : 512;
 
     // operand images of the contraction matrices, copied once per CTA
-    for (uint32_t i = tid * 16; i < b_bytes; i += kRows * 16) {
+    for (uint32_t i = tid * 16; i < a.img_bytes; i += kRows * 16) {
         *reinterpret_cast<uint4 *>(sB1 + i) = *reinterpret_cast<const uint4 *>(a.B1 + i);
         if (DOUBLE) *reinterpret_cast<uint4 *>(sB2 + i) = *reinterpret_cast<const uint4 *>(a.B2 + i);
     }
@@ -205,14 +247,13 @@ __global__ void __launch_bounds__(kRows, 1) tc_pass_kernel(TcPassArgs a, int pre
         tc::mbar_init(bar, 1);
         *sflag = 0;
     }
-    if (warp == 0) tc::tmem_alloc(tslot, ncols_tmem);
+    if (warp == 0) tc::tmem_alloc(tslot, ncols);
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tslot;
-    const uint32_t d1 = tmem, d2 = tmem + (DOUBLE ? uint32_t(a.Np) : 0u);
-    const uint32_t lane_off = uint32_t(warp * 32) << 16;
-    const uint32_t idesc = tc::instr_desc(TF32, a.Np);
+    const uint32_t dacc = tmem + (uint32_t(warp * 32) << 16);   // this warp's lanes
+    const uint32_t idesc = tc::instr_desc(MODE == MODE_FLOAT_TF32, Np);
     const int ksteps = Kp * ES / 32;
     const uint32_t sA_addr = tc::smem_addr(sA), sB1_addr = tc::smem_addr(sB1), sB2_addr = tc::smem_addr(sB2);
     uint32_t phase = 0;
@@ -224,47 +265,64 @@ __global__ void __launch_bounds__(kRows, 1) tc_pass_kernel(TcPassArgs a, int pre
         const bool active = g < rows;
         const int p = active ? int(g / a.R) : 0;
         const int r = active ? int(g - long(p) * a.R) : 0;
-        // ---- prologue: this thread's row (K values) -> split pieces in SMEM ----
-        {
-            const float *in = a.in + size_t(p) * a.N;
-            const float *mh = nullptr, *ml = nullptr, *nh = nullptr, *nl = nullptr;
-            if (LOAD == LOAD_PAIR && active) {
-                const int2 mn = a.pairs[p];
-                mh = a.psi_hi + size_t(a.occ_off + mn.x) * a.N;
-                ml = a.psi_lo + size_t(a.occ_off + mn.x) * a.N;
-                nh = a.psi_hi + size_t(mn.y) * a.N;
-                nl = a.psi_lo + size_t(mn.y) * a.N;
+        // ---- prologue: this thread's row (K values) -> pieces in SMEM ----
+        const float *in = a.in + size_t(p) * a.N;
+        const float *mh = nullptr, *ml = nullptr, *nh = nullptr, *nl = nullptr;
+        if (LOAD == LOAD_PAIR && active) {
+            const int2 mn = a.pairs[p];
+            mh = a.psi_hi + size_t(a.occ_off + mn.x) * a.N;
+            ml = a.psi_lo + size_t(a.occ_off + mn.x) * a.N;
+            nh = a.psi_hi + size_t(mn.y) * a.N;
+            nl = a.psi_lo + size_t(mn.y) * a.N;
+        }
+        auto load = [&](int k, float &hi, float &lo) {
+            hi = 0.f;
+            lo = 0.f;
+            if (!active || k >= a.K) return;
+            if (LOAD == LOAD_PAIR) {
+                const size_t idx = size_t(k) * a.R + r;
+                const float ah = mh[idx], al = ml[idx], bh = nh[idx], bl = nl[idx];
+                hi = ah * bh;
+                lo = fmaf(ah, bh, -hi) + fmaf(ah, bl, al * bh);
+            } else if (LOAD == LOAD_KSLOW) {
+                hi = in[size_t(k) * a.R + r];
+            } else {
+                hi = in[size_t(r) * a.K + k];
             }
-            for (int c = 0; c < Kp / EPC; ++c) {
-                float hi[EPC], lo[EPC];
+        };
+        float s_in = 1.f, rs1 = 1.f;
+        if (MODE == MODE_FIXED_BF16) {
+            float mx = 0.f;
+            for (int k = 0; k < a.K; ++k) {
+                float hi, lo;
+                load(k, hi, lo);
+                mx = fmaxf(mx, fabsf(hi));
+            }
+            int e = 0;
+            if (mx > 0.f) frexpf(mx, &e);
+            e = max(e, -100);   // rows below 2^-100 are flushed to zero slices
+            s_in = ldexpf(1.f, 7 - e);
+            rs1 = ldexpf(1.f, e - 7);
+        }
+        for (int c = 0; c < Kp / EPC; ++c) {
+            float vals[3][8];
 #pragma unroll
-                for (int e = 0; e < EPC; ++e) {
-                    const int k = c * EPC + e;
-                    hi[e] = 0.f;
-                    lo[e] = 0.f;
-                    if (active && k < a.K) {
-                        if (LOAD == LOAD_PAIR) {
-                            const size_t idx = size_t(k) * a.R + r;
-                            const float ah = mh[idx], al = ml[idx], bh = nh[idx], bl = nl[idx];
-                            const float ph = ah * bh;
-                            hi[e] = ph;
-                            lo[e] = fmaf(ah, bh, -ph) + fmaf(ah, bl, al * bh);
-                        } else if (LOAD == LOAD_KSLOW) {
-                            hi[e] = in[size_t(k) * a.R + r];
-                        } else {
-                            hi[e] = in[size_t(r) * a.K + k];
-                        }
-                    }
-                }
-                put_chunk<TF32, NP>(sA, a_piece, tid, c, a_sbo, hi, LOAD == LOAD_PAIR ? lo : nullptr);
+            for (int e = 0; e < EPC; ++e) {
+                float hi, lo, q[3];
+                load(c * EPC + e, hi, lo);
+                if (MODE == MODE_FLOAT_TF32) split_tf32(hi, lo, q);
+                else slice_fixed<S>(hi, lo, s_in, q);
+#pragma unroll
+                for (int t = 0; t < 3; ++t) vals[t][e] = q[t];
             }
+            store_chunk<ES, S>(sA, a_piece, tid, c, sbo, vals);
         }
         tc::fence_proxy_async_smem();
         tc::tc_fence_before();
         __syncthreads();
         if (tid == 0) {
             tc::tc_fence_after();
-            issue_gemm<TF32>(prec, d1, sA_addr, a_piece, a_sbo, sB1_addr, b_piece, b_sbo, ksteps, idesc);
+            issue_gemm<MODE, S, SB>(tmem, Np, sA_addr, a_piece, sB1_addr, b_piece, sbo, ksteps, idesc);
             tc::mma_commit(bar);
         }
         if (!tc::mbar_wait_bounded(bar, phase, kWaitLimit)) atomicExch(sflag, 1);
@@ -272,26 +330,60 @@ __global__ void __launch_bounds__(kRows, 1) tc_pass_kernel(TcPassArgs a, int pre
         tc::tc_fence_after();
         __syncthreads();
         if (*sflag) break;
+        float rs_out = rs1;
+        const float *cs_out = cs1;
         if (DOUBLE) {
-            // D1 -> scale by f(Lambda) -> split -> A (same rows, K = modes) -> second GEMM
-            for (int c0 = 0; c0 < a.Np; c0 += 16) {
-                float v[16];
-                tc::tmem_ld16(d1 + lane_off + uint32_t(c0), v);
+            // D1 * f(Lambda) -> pieces of A (same rows, K = modes) -> second GEMM, same TMEM
+            float s2 = 1.f, rs2 = 1.f;
+            if (MODE == MODE_FIXED_BF16) {
+                float mx = 0.f;
+                for (int c0 = 0; c0 < Np; c0 += 16) {
+                    float v[16];
+                    read_result<MODE, NACC>(dacc, Np, c0, rs1, cs1, v);
 #pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                    const int col = c0 + e;
-                    v[e] = (active && col < a.K) ? v[e] * a.F[size_t(col) * a.R + r] : 0.f;
+                    for (int e = 0; e < 16; ++e) {
+                        const int col = c0 + e;
+                        if (active && col < a.K) {
+                            const size_t fi = size_t(col) * a.R + r;
+                            mx = fmaxf(mx, fabsf(fmaf(v[e], a.F[fi], v[e] * a.Flo[fi])));
+                        }
+                    }
                 }
+                int e2 = 0;
+                if (mx > 0.f) frexpf(mx, &e2);
+                e2 = max(e2, -100);
+                s2 = ldexpf(1.f, 7 - e2);
+                rs2 = ldexpf(1.f, e2 - 7);
+            }
+            for (int c0 = 0; c0 < Np; c0 += 16) {
+                float v[16];
+                read_result<MODE, NACC>(dacc, Np, c0, rs1, cs1, v);
 #pragma unroll
-                for (int h = 0; h < 16 / EPC; ++h)
-                    put_chunk<TF32, NP>(sA, a_piece, tid, c0 / EPC + h, a_sbo, v + h * EPC, nullptr);
+                for (int h = 0; h < 16 / EPC; ++h) {
+                    float vals[3][8];
+#pragma unroll
+                    for (int e = 0; e < EPC; ++e) {
+                        const int col = c0 + h * EPC + e;
+                        float x = 0.f;
+                        if (active && col < a.K) {
+                            const size_t fi = size_t(col) * a.R + r;
+                            x = fmaf(v[h * EPC + e], a.F[fi], v[h * EPC + e] * a.Flo[fi]);
+                        }
+                        float q[3];
+                        if (MODE == MODE_FLOAT_TF32) split_tf32(x, 0.f, q);
+                        else slice_fixed<S>(x, 0.f, s2, q);
+#pragma unroll
+                        for (int t = 0; t < 3; ++t) vals[t][e] = q[t];
+                    }
+                    store_chunk<ES, S>(sA, a_piece, tid, c0 / EPC + h, sbo, vals);
+                }
             }
             tc::fence_proxy_async_smem();
             tc::tc_fence_before();
             __syncthreads();
             if (tid == 0) {
                 tc::tc_fence_after();
-                issue_gemm<TF32>(prec, d2, sA_addr, a_piece, a_sbo, sB2_addr, b_piece, b_sbo, ksteps, idesc);
+                issue_gemm<MODE, S, SB>(tmem, Np, sA_addr, a_piece, sB2_addr, b_piece, sbo, ksteps, idesc);
                 tc::mma_commit(bar);
             }
             if (!tc::mbar_wait_bounded(bar, phase, kWaitLimit)) atomicExch(sflag, 1);
@@ -299,13 +391,14 @@ __global__ void __launch_bounds__(kRows, 1) tc_pass_kernel(TcPassArgs a, int pre
             tc::tc_fence_after();
             __syncthreads();
             if (*sflag) break;
+            rs_out = rs2;
+            cs_out = cs2;
         }
         // ---- epilogue: TMEM -> registers -> global ----
         float *out = a.out + size_t(p) * a.N;
-        const uint32_t dres = DOUBLE ? d2 : d1;
-        for (int c0 = 0; c0 < a.Np; c0 += 16) {
+        for (int c0 = 0; c0 < Np; c0 += 16) {
             float v[16];
-            tc::tmem_ld16(dres + lane_off + uint32_t(c0), v);
+            read_result<MODE, NACC>(dacc, Np, c0, rs_out, cs_out, v);
             if (active) {
 #pragma unroll
                 for (int e = 0; e < 16; ++e) {
@@ -325,7 +418,7 @@ __global__ void __launch_bounds__(kRows, 1) tc_pass_kernel(TcPassArgs a, int pre
     __syncthreads();
     if (warp == 0) {
         tc::tc_fence_after();
-        tc::tmem_dealloc(tmem, ncols_tmem);
+        tc::tmem_dealloc(tmem, ncols);
     }
 }
 
@@ -345,13 +438,16 @@ __global__ void __launch_bounds__(kRows, 1) tc_unit_gemm_kernel(int n, int k, co
     uint64_t *bar = reinterpret_cast<uint64_t *>(sB + b_bytes + 4096);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
     const int tid = threadIdx.x, warp = tid >> 5;
+    auto round1 = [](float x) {
+        return TF32 ? tc::to_tf32(x) : __bfloat162float(__float2bfloat16_rn(x));
+    };
     for (int c = 0; c < Kp / EPC; ++c) {
-        float v[EPC];
-        for (int e = 0; e < EPC; ++e) v[e] = A[size_t(tid) * k + c * EPC + e];
-        put_chunk<TF32, 1>(sA, a_bytes, tid, c, sbo, v, nullptr);
+        float v[3][8] = {};
+        for (int e = 0; e < EPC; ++e) v[0][e] = round1(A[size_t(tid) * k + c * EPC + e]);
+        store_chunk<ES, 1>(sA, a_bytes, tid, c, sbo, v);
         for (int row = tid; row < Np; row += kRows) {
-            for (int e = 0; e < EPC; ++e) v[e] = B[size_t(row) * k + c * EPC + e];
-            put_chunk<TF32, 1>(sB, b_bytes, row, c, sbo, v, nullptr);
+            for (int e = 0; e < EPC; ++e) v[0][e] = round1(B[size_t(row) * k + c * EPC + e]);
+            store_chunk<ES, 1>(sB, b_bytes, row, c, sbo, v);
         }
     }
     const int ncols = Np <= 32 ? 32 : Np <= 64 ? 64 : Np <= 128 ? 128 : 256;
@@ -486,31 +582,26 @@ __global__ void tc_finalize_kernel(long N, int n_in, const float *acc_hi, const 
 size_t pass_smem(int prec, int Np, bool dbl)
 {
     const PrecInfo pi = prec_info(prec);
-    size_t b = size_t(pi.np) * Np * Np * pi.es;
-    size_t a = size_t(pi.np) * kRows * Np * pi.es;
-    return (dbl ? 2 : 1) * b + a + 64;
+    size_t a = size_t(pi.S) * kRows * Np * pi.es;
+    return (dbl ? 2 : 1) * image_bytes(prec, Np) + a + 64;
 }
 
-int tmem_cols(int Np, bool dbl)
-{
-    int c = dbl ? 2 * Np : Np;
-    return c <= 32 ? 32 : c <= 64 ? 64 : c <= 128 ? 128 : 256;
-}
+int tmem_cols(int prec, int Np) { return pow2_cols(prec_info(prec).nacc * Np); }
 
-template <bool TF32, int NP, int LOAD, int STORE, bool DOUBLE>
+template <int MODE, int S, int SB, int LOAD, int STORE, bool DOUBLE>
 int launch_tc_pass(Plan &P, int kind, int prec, const TcPassArgs &a, cudaStream_t s)
 {
-    auto kern = tc_pass_kernel<TF32, NP, LOAD, STORE, DOUBLE>;
+    auto kern = tc_pass_kernel<MODE, S, SB, LOAD, STORE, DOUBLE>;
     size_t smem = pass_smem(prec, a.Np, DOUBLE);
     // TMEM: co-resident CTAs must not ask for more than 512 columns in total, so the
     // shared-memory request is raised until at most 512 / cols CTAs fit on one SM.
-    const int cols = tmem_cols(a.Np, DOUBLE);
+    const int cols = tmem_cols(prec, a.Np);
     const int max_ctas = std::max(1, 512 / cols);
     const size_t sm_total = 233472;   // 228 KB of shared memory per SM
     size_t floor_req = sm_total / size_t(max_ctas + 1) - 1024 + 64;
     smem = std::max(smem, floor_req);
-    if (smem > 232448) {
-        set_error("split-precision pass: operand images exceed shared memory for this grid size");
+    if (smem > 232448 || cols > 512) {
+        set_error("split-precision pass: operand images exceed on-chip memory for this grid size");
         return EXX_ERR_UNSUPPORTED;
     }
     EXX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
@@ -521,14 +612,14 @@ int launch_tc_pass(Plan &P, int kind, int prec, const TcPassArgs &a, cudaStream_
     const long ntiles = (rows + kRows - 1) / kRows;
     const int grid = int(std::min<long>(ntiles, long(P.num_sms) * per_sm));
     int tb = timing_begin(P, kind, s);
-    kern<<<grid, kRows, smem, s>>>(a, prec);
+    kern<<<grid, kRows, smem, s>>>(a);
     timing_end(P, tb, s);
     EXX_LAUNCH("tc_pass_kernel");
     P.launches++;
     return EXX_OK;
 }
 
-template <bool TF32, int NP>
+template <int MODE, int S, int SB>
 int solve_batch_t(Plan &P, int prec, const int2 *pairs_d, int nfields, float *bufA, float *bufB, cudaStream_t s)
 {
     float *src = nullptr, *dst = bufA;
@@ -542,10 +633,12 @@ int solve_batch_t(Plan &P, int prec, const int2 *pairs_d, int nfields, float *bu
         a.N = P.N;
         a.in = src;
         a.out = dst;
-        const int slot = pass < 2 ? pass : pass + 1;   // P3 uses slots 2 (fwd) and 3 (inv)
+        const int slot = pass <= 2 ? pass : pass + 1;  // P3 uses slots 2 (fwd) and 3 (inv)
         a.B1 = static_cast<const uint8_t *>(P.Btc[prec][slot].p);
         a.B2 = pass == 2 ? static_cast<const uint8_t *>(P.Btc[prec][3].p) : nullptr;
+        a.img_bytes = uint32_t(image_bytes(prec, a.Np));
         a.F = static_cast<const float *>(P.F32.p);
+        a.Flo = a.F + P.N;
         a.psi_hi = static_cast<const float *>(P.psi32.p);
         a.psi_lo = a.psi_hi + P.psi32.bytes / 8;
         a.occ_off = P.tc_occ_off;
@@ -553,11 +646,11 @@ int solve_batch_t(Plan &P, int prec, const int2 *pairs_d, int nfields, float *bu
         a.err = static_cast<int *>(P.err_d.p);
         int rc;
         switch (pass) {
-        case 0: rc = launch_tc_pass<TF32, NP, LOAD_PAIR, STORE_NSLOW, false>(P, EXX_TIMING_PASS1, prec, a, s); break;
-        case 1: rc = launch_tc_pass<TF32, NP, LOAD_KFAST, STORE_NSLOW, false>(P, EXX_TIMING_PASS2, prec, a, s); break;
-        case 2: rc = launch_tc_pass<TF32, NP, LOAD_KFAST, STORE_NFAST, true>(P, EXX_TIMING_PASS3, prec, a, s); break;
-        case 3: rc = launch_tc_pass<TF32, NP, LOAD_KSLOW, STORE_NFAST, false>(P, EXX_TIMING_PASS4, prec, a, s); break;
-        default: rc = launch_tc_pass<TF32, NP, LOAD_KSLOW, STORE_NSLOW, false>(P, EXX_TIMING_PASS5, prec, a, s); break;
+        case 0: rc = launch_tc_pass<MODE, S, SB, LOAD_PAIR, STORE_NSLOW, false>(P, EXX_TIMING_PASS1, prec, a, s); break;
+        case 1: rc = launch_tc_pass<MODE, S, SB, LOAD_KFAST, STORE_NSLOW, false>(P, EXX_TIMING_PASS2, prec, a, s); break;
+        case 2: rc = launch_tc_pass<MODE, S, SB, LOAD_KFAST, STORE_NFAST, true>(P, EXX_TIMING_PASS3, prec, a, s); break;
+        case 3: rc = launch_tc_pass<MODE, S, SB, LOAD_KSLOW, STORE_NFAST, false>(P, EXX_TIMING_PASS4, prec, a, s); break;
+        default: rc = launch_tc_pass<MODE, S, SB, LOAD_KSLOW, STORE_NSLOW, false>(P, EXX_TIMING_PASS5, prec, a, s); break;
         }
         if (rc) return rc;
         src = dst;
@@ -576,7 +669,7 @@ int tc_upload(Plan &P, int prec)
     const int inv_of[6] = {0, 0, 0, 1, 1, 1};
     for (int d = 0; d < 3; ++d) {
         const int Np = pad16(P.n[d]);
-        if (pass_smem(prec, Np, d == 1) > 232448) {
+        if (pass_smem(prec, Np, d == 1) > 232448 || tmem_cols(prec, Np) > 512) {
             set_error("split precision: grid axis too long for the on-chip operand images of this build");
             return EXX_ERR_UNSUPPORTED;
         }
@@ -585,27 +678,53 @@ int tc_upload(Plan &P, int prec)
         const int d = axis_of[slot], nd = P.n[d], Np = pad16(nd);
         const uint32_t sbo = uint32_t(Np) * pi.es * 8;
         const size_t piece = size_t(Np) * Np * pi.es;
-        std::vector<uint8_t> img(piece * pi.np, 0);
-        for (int n = 0; n < nd; ++n)
-            for (int k = 0; k < nd; ++k) {
-                // output mode n from input k: forward V(k, n), inverse V(n, k)
-                double v = inv_of[slot] ? P.V[d][n + size_t(nd) * k] : P.V[d][k + size_t(nd) * n];
-                double rem = v;
-                for (int q = 0; q < pi.np; ++q) {
-                    float pv = pi.tf32 ? host_tf32(rem) : host_bf16(rem);
-                    rem -= double(pv);
-                    const int epc = 16 / pi.es;
-                    size_t off = piece * q + img_off(n, k / epc, sbo) + size_t(k % epc) * pi.es;
-                    if (pi.tf32) {
-                        std::memcpy(&img[off], &pv, 4);
-                    } else {
-                        uint32_t u;
-                        std::memcpy(&u, &pv, 4);
-                        uint16_t h = uint16_t(u >> 16);
-                        std::memcpy(&img[off], &h, 2);
+        const int epc = 16 / pi.es;
+        std::vector<uint8_t> img(image_bytes(prec, Np), 0);
+        // coefficient of output mode n from input k: forward V(k, n), inverse V(n, k)
+        auto coef = [&](int n, int k) {
+            if (n >= nd || k >= nd) return 0.0;
+            return inv_of[slot] ? P.V[d][n + size_t(nd) * k] : P.V[d][k + size_t(nd) * n];
+        };
+        auto put = [&](int q, int n, int k, float v) {
+            size_t off = piece * q + img_off(n, k / epc, sbo) + size_t(k % epc) * pi.es;
+            if (pi.es == 4) {
+                std::memcpy(&img[off], &v, 4);
+            } else {
+                uint32_t u;
+                std::memcpy(&u, &v, 4);
+                uint16_t h = uint16_t(u >> 16);   // v is bf16-exact (a small integer)
+                std::memcpy(&img[off], &h, 2);
+            }
+        };
+        std::vector<float> cs(Np, 1.0f);
+        for (int n = 0; n < Np; ++n) {
+            if (pi.mode == MODE_FIXED_BF16) {
+                double mx = 0.0;
+                for (int k = 0; k < Np; ++k) mx = std::max(mx, std::fabs(coef(n, k)));
+                int e = 0;
+                if (mx > 0.0) std::frexp(mx, &e);
+                const double sc = std::ldexp(1.0, 7 - e);
+                cs[n] = float(std::ldexp(1.0, e - 7));
+                for (int k = 0; k < Np; ++k) {
+                    double t = coef(n, k) * sc;
+                    for (int s = 0; s < pi.SB; ++s) {   // t = q0 + q1/2^8 + q2/2^16 + ...
+                        const double q = std::nearbyint(t);
+                        put(s, n, k, float(q));
+                        t = (t - q) * 256.0;
+                    }
+                }
+            } else {
+                for (int k = 0; k < Np; ++k) {
+                    double rem = coef(n, k);
+                    for (int s = 0; s < pi.SB; ++s) {
+                        float pv = host_tf32(rem);
+                        rem -= double(pv);
+                        put(s, n, k, pv);
                     }
                 }
             }
+        }
+        if (pi.mode == MODE_FIXED_BF16) std::memcpy(&img[piece * pi.SB], cs.data(), size_t(Np) * 4);
         if (int rc = dev_reserve(P.Btc[prec][slot], img.size())) return rc;
         EXX_CUDA(cudaMemcpy(P.Btc[prec][slot].p, img.data(), img.size(), cudaMemcpyHostToDevice));
     }
@@ -619,12 +738,8 @@ int tc_prepare_orbitals(Plan &P, const double *psi_occ, int n_occ, long ld_occ, 
 {
     const int ncols = n_in + (aliased ? 0 : n_occ);
     const size_t plane = size_t(ncols) * P.N;
+    if (P.psi32.bytes != 2 * plane * sizeof(float)) dev_free(P.psi32);   // psi_lo follows psi_hi exactly
     if (int rc = dev_reserve(P.psi32, 2 * plane * sizeof(float))) return rc;
-    // psi_lo is located right after psi_hi: keep the reservation exact
-    if (P.psi32.bytes != 2 * plane * sizeof(float)) {
-        dev_free(P.psi32);
-        if (int rc = dev_reserve(P.psi32, 2 * plane * sizeof(float))) return rc;
-    }
     if (int rc = dev_reserve(P.g32, size_t(n_occ) * P.N * sizeof(float))) return rc;
     if (int rc = dev_reserve(P.acc_hi, size_t(n_in) * P.N * sizeof(float))) return rc;
     if (int rc = dev_reserve(P.acc_lo, size_t(n_in) * P.N * sizeof(float))) return rc;
@@ -643,9 +758,9 @@ int tc_prepare_orbitals(Plan &P, const double *psi_occ, int n_occ, long ld_occ, 
 int tc_solve_batch(Plan &P, int prec, const int2 *pairs_d, int nfields, float *bufA, float *bufB, cudaStream_t s)
 {
     switch (prec) {
-    case EXX_PREC_BF16X3: return solve_batch_t<false, 2>(P, prec, pairs_d, nfields, bufA, bufB, s);
-    case EXX_PREC_BF16X6: return solve_batch_t<false, 3>(P, prec, pairs_d, nfields, bufA, bufB, s);
-    case EXX_PREC_TF32X3: return solve_batch_t<true, 2>(P, prec, pairs_d, nfields, bufA, bufB, s);
+    case EXX_PREC_BF16X3: return solve_batch_t<MODE_FIXED_BF16, 2, 2>(P, prec, pairs_d, nfields, bufA, bufB, s);
+    case EXX_PREC_BF16X6: return solve_batch_t<MODE_FIXED_BF16, 3, 4>(P, prec, pairs_d, nfields, bufA, bufB, s);
+    case EXX_PREC_TF32X3: return solve_batch_t<MODE_FLOAT_TF32, 2, 2>(P, prec, pairs_d, nfields, bufA, bufB, s);
     default: return EXX_ERR_INVALID_ARG;
     }
 }
