@@ -67,13 +67,22 @@ enum { EXX_KERNEL_COULOMB = 0, EXX_KERNEL_ERFC = 1, EXX_KERNEL_ERFC_PAPER16PI = 
 
 /* Arithmetic of the mode products (the six contractions of the batched Kronecker
  * solve, Sec. II.B):
- *   FP64    double precision on the CUDA cores;
- *   BF16X3  tcgen05 tensor cores, operands split in two bf16 pieces, 3 products,
- *           FP32 accumulation;
- *   TF32X3  tcgen05 tensor cores, two tf32 pieces, 3 products, FP32 accumulation;
- *   BF16X6  tcgen05 tensor cores, three bf16 pieces, 6 products, FP32 accumulation.
+ *   FP64     double precision on the CUDA cores;
+ *   BF16X3   tcgen05 tensor cores; every row is scaled by a power of two and cut into
+ *            two 8-bit fixed-point slices stored as bf16; the 3 slice products of
+ *            levels 0-1 are summed exactly (one FP32 TMEM accumulator per level, every
+ *            partial sum an integer below 2^24); ~16 bits;
+ *   BF16X6   as BF16X3 with three data slices (6 products, levels 0-2) and a fourth
+ *            slice of the shared eigenvector matrices used against the leading data
+ *            slice; ~24 bits, FP32 intermediates between passes;
+ *   BF16X10  four slices per operand (10 products, levels 0-3) and intermediates kept
+ *            as hi+lo FP32 pairs between passes; ~32 bits;
+ *   TF32X3   floating tf32 split, 3 products into one FP32 accumulator (the tensor core
+ *            rounds that accumulation toward zero, a bias common to all pairs); kept
+ *            for comparison.
  * Pair densities and the accumulation over pairs are compensated in every mode. */
-enum { EXX_PREC_FP64 = 0, EXX_PREC_BF16X3 = 1, EXX_PREC_TF32X3 = 2, EXX_PREC_BF16X6 = 3 };
+enum { EXX_PREC_FP64 = 0, EXX_PREC_BF16X3 = 1, EXX_PREC_TF32X3 = 2, EXX_PREC_BF16X6 = 3,
+       EXX_PREC_BF16X10 = 4 };
 
 /* Create a plan for one grid (Sec. II.A, Eqs. 6-7).  Host FP64 work, done once:
  * FD weights of order fd_order (even, 2..24), the three 1D second-derivative

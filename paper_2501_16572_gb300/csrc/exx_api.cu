@@ -70,7 +70,7 @@ static void free_plan_buffers(Plan &P)
 // the batch buffers stay a modest part of L2 (tensor path) or of HBM (FP64 path).
 static int default_pairs(const Plan &P, int block)
 {
-    long per_field = long(P.N) * (P.prec == EXX_PREC_FP64 ? 8 : 4);
+    long per_field = long(P.N) * (P.prec == EXX_PREC_FP64 || P.prec == EXX_PREC_BF16X10 ? 8 : 4);
     long budget = (P.prec == EXX_PREC_FP64) ? (256L << 20) : (48L << 20);
     long pairs = std::max<long>(block * block, budget / per_field);
     pairs = std::min<long>(pairs, 1024);
@@ -221,7 +221,7 @@ int exx_plan_set_precision(exx_plan plan, int prec)
 {
     Plan *P = as_plan(plan);
     if (!P) return invalid("exx_plan_set_precision: plan is NULL");
-    if (prec < EXX_PREC_FP64 || prec > EXX_PREC_BF16X6) return invalid("exx_plan_set_precision: bad precision");
+    if (prec < EXX_PREC_FP64 || prec > EXX_PREC_BF16X10) return invalid("exx_plan_set_precision: bad precision");
     if (prec != EXX_PREC_FP64) {
         if (int rc = tc_upload(*P, prec)) return rc;
     }
@@ -352,7 +352,9 @@ int exx_apply(exx_plan plan, const double *Psi_occ, int n_occ, long ld_occ, cons
     // split precision on the tensor cores
     const int prec = P->prec;
     if (int rc = tc_prepare_orbitals(*P, Psi_occ, n_occ, ld_occ, f, Psi_in, n_in, ld_in, aliased, s)) return rc;
-    size_t fb = size_t(S.max_fields) * P->N * sizeof(float);
+    const bool hl = tc_is_hilo(prec);
+    P->tc_lo_off = hl ? long(S.max_fields) * P->N : 0;
+    size_t fb = size_t(S.max_fields) * P->N * sizeof(float) * (hl ? 2 : 1);
     if (int rc = dev_reserve(P->work[0], fb)) return rc;
     if (int rc = dev_reserve(P->work[1], fb)) return rc;
     for (size_t b = 0; b < S.batches.size(); ++b) {

@@ -118,8 +118,7 @@ struct Plan {
     DevBuf F64;                     // F in the P3 layout [b][a][c]
     DevBuf F32;                     // same as two float planes, hi then lo
     // tensor path: per pass and precision the B operand pieces, canonical SMEM image
-    DevBuf Btc[4][6];               // [prec][pass slot]
-    size_t Btc_bytes[4][6] = {};
+    DevBuf Btc[5][6];               // [prec][pass slot]
     // workspace
     DevBuf work[3];                 // batch buffers (fields x N)
     DevBuf pairs_d, blocks_d;       // schedule on the device
@@ -129,6 +128,7 @@ struct Plan {
     DevBuf err_d;                   // device error word of the bounded waits
     int tc_occ_off = 0;             // column of Psi_occ in the fp32 planes (0 when aliased)
     float *tc_result = nullptr;     // buffer holding the last batch's solutions
+    long tc_lo_off = 0;             // hi+lo intermediates: offset of the lo plane (floats)
     long launches = 0;
     Timing timing;
     // cached schedule
@@ -154,6 +154,7 @@ int tc_solve_batch(Plan &P, int prec, const int2 *pairs_d, int nfields, float *b
 int tc_accumulate(Plan &P, const Block *blocks_d, int nblocks, const float *V, cudaStream_t s);
 int tc_finalize(Plan &P, int n_in, double *out, long ld_out, cudaStream_t s);
 int tc_check_error(Plan &P, cudaStream_t s);
+bool tc_is_hilo(int prec);
 int tc_unit_gemm(int tf32, int n, int k, const float *A, const float *B, float *D, int *err);
 
 // reductions, GEMM, Cholesky (exx_linalg.cu)

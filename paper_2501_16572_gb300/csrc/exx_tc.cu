@@ -46,6 +46,7 @@ struct PrecInfo {
     int SB;          // pieces / slices of the matrix operand B
     int es;          // bytes per element
     int nacc;        // TMEM accumulators per GEMM
+    int hl;          // intermediates between passes kept as hi + lo FP32 pairs
 };
 // BF16X6 carries the matrices with a fourth slice, used only against the leading data
 // slice: the matrices are shared by every pair, so their representation error does not
@@ -53,9 +54,10 @@ struct PrecInfo {
 __host__ __device__ inline PrecInfo prec_info(int prec)
 {
     switch (prec) {
-    case EXX_PREC_BF16X3: return {MODE_FIXED_BF16, 2, 2, 2, 2};
-    case EXX_PREC_BF16X6: return {MODE_FIXED_BF16, 3, 4, 2, 4};
-    default: return {MODE_FLOAT_TF32, 2, 2, 4, 1};   // TF32X3
+    case EXX_PREC_BF16X3: return {MODE_FIXED_BF16, 2, 2, 2, 2, 0};
+    case EXX_PREC_BF16X6: return {MODE_FIXED_BF16, 3, 4, 2, 4, 0};
+    case EXX_PREC_BF16X10: return {MODE_FIXED_BF16, 4, 4, 2, 4, 1};
+    default: return {MODE_FLOAT_TF32, 2, 2, 4, 1, 0};   // TF32X3
     }
 }
 
@@ -91,28 +93,32 @@ inline float host_tf32(double v)
 
 // ---- device: operand pieces -------------------------------------------------------------
 // Floating tf32 split of (hi + lo).
-__device__ __forceinline__ void split_tf32(float hi, float lo, float (&p)[3])
+__device__ __forceinline__ void split_tf32(float hi, float lo, float (&p)[4])
 {
     p[0] = tc::to_tf32(hi);
     p[1] = tc::to_tf32((hi - p[0]) + lo);
     p[2] = 0.f;
+    p[3] = 0.f;
 }
 
 // Fixed-point slices of (hi + lo) * s, s = 2^(7 - e): integers of at most 8 bits.
+// Each residual (t_i - q_i) is exact; only the first one absorbs lo.
 template <int S>
-__device__ __forceinline__ void slice_fixed(float hi, float lo, float s, float (&q)[3])
+__device__ __forceinline__ void slice_fixed(float hi, float lo, float s, float (&q)[4])
 {
     const float t = hi * s;
     q[0] = rintf(t);
     const float t1 = ((t - q[0]) + lo * s) * 256.f;
     q[1] = (S >= 2) ? rintf(t1) : 0.f;
-    q[2] = (S >= 3) ? rintf((t1 - q[1]) * 256.f) : 0.f;
+    const float t2 = (t1 - q[1]) * 256.f;
+    q[2] = (S >= 3) ? rintf(t2) : 0.f;
+    q[3] = (S >= 4) ? rintf((t2 - q[2]) * 256.f) : 0.f;
 }
 
 // Store one 16-byte chunk per piece: vals[q][e] for e < 16/ES elements of row `row`.
 template <int ES, int S>
 __device__ __forceinline__ void store_chunk(uint8_t *img, uint32_t piece_bytes, int row, int c, uint32_t sbo,
-                                            const float (&vals)[3][8])
+                                            const float (&vals)[4][8])
 {
     const uint32_t off = img_off(row, c, sbo);
 #pragma unroll
@@ -200,6 +206,36 @@ __device__ __forceinline__ void read_result(uint32_t d, int Np, int c0, float rs
     for (int e = 0; e < 16; ++e) v[e] = (l0[e] + t[e]) * rs * cs[c0 + e];
 }
 
+// As read_result (fixed mode) but returns each value as an unevaluated sum vh + vl:
+// level 0 is an exact integer, the lower levels are folded into t, and TwoSum keeps
+// the rounding error of l0 + t; the scales are powers of two (exact).
+template <int NACC>
+__device__ __forceinline__ void read_result_hl(uint32_t d, int Np, int c0, float rs, const float *cs, float (&vh)[16],
+                                               float (&vl)[16])
+{
+    float t[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) t[e] = 0.f;
+#pragma unroll
+    for (int l = NACC - 1; l >= 1; --l) {
+        float lv[16];
+        tc::tmem_ld16(d + uint32_t(l * Np + c0), lv);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) t[e] = (lv[e] + t[e]) * (1.f / 256.f);
+    }
+    float l0[16];
+    tc::tmem_ld16(d + uint32_t(c0), l0);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        const float h = l0[e] + t[e];
+        const float bp = h - l0[e];
+        const float lo = (l0[e] - (h - bp)) + (t[e] - bp);
+        const float sc = rs * cs[c0 + e];
+        vh[e] = h * sc;
+        vl[e] = lo * sc;
+    }
+}
+
 // ---------------------------------------------------------------------------------------
 // Pass kernel.  Rows of the batch are cut into tiles of 128; CTAs loop over tiles.
 struct TcPassArgs {
@@ -207,6 +243,7 @@ struct TcPassArgs {
     long N;
     const float *in;
     float *out;
+    long lo_off;                    // hi + lo intermediates: offset of the lo plane (floats)
     const uint8_t *B1, *B2;         // operand images
     uint32_t img_bytes;             // bytes of one image
     const float *F, *Flo;           // [col][row] scaling for the double pass, hi + lo
@@ -216,7 +253,7 @@ struct TcPassArgs {
     int *err;
 };
 
-template <int MODE, int S, int SB, int LOAD, int STORE, bool DOUBLE>
+template <int MODE, int S, int SB, bool HL, int LOAD, int STORE, bool DOUBLE>
 __global__ void __launch_bounds__(kRows, 1) tc_pass_kernel(TcPassArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -284,10 +321,10 @@ __global__ void __launch_bounds__(kRows, 1) tc_pass_kernel(TcPassArgs a)
                 const float ah = mh[idx], al = ml[idx], bh = nh[idx], bl = nl[idx];
                 hi = ah * bh;
                 lo = fmaf(ah, bh, -hi) + fmaf(ah, bl, al * bh);
-            } else if (LOAD == LOAD_KSLOW) {
-                hi = in[size_t(k) * a.R + r];
             } else {
-                hi = in[size_t(r) * a.K + k];
+                const size_t idx = (LOAD == LOAD_KSLOW) ? size_t(k) * a.R + r : size_t(r) * a.K + k;
+                hi = in[idx];
+                if (HL) lo = in[a.lo_off + idx];
             }
         };
         float s_in = 1.f, rs1 = 1.f;
@@ -305,15 +342,15 @@ __global__ void __launch_bounds__(kRows, 1) tc_pass_kernel(TcPassArgs a)
             rs1 = ldexpf(1.f, e - 7);
         }
         for (int c = 0; c < Kp / EPC; ++c) {
-            float vals[3][8];
+            float vals[4][8];
 #pragma unroll
             for (int e = 0; e < EPC; ++e) {
-                float hi, lo, q[3];
+                float hi, lo, q[4];
                 load(c * EPC + e, hi, lo);
                 if (MODE == MODE_FLOAT_TF32) split_tf32(hi, lo, q);
                 else slice_fixed<S>(hi, lo, s_in, q);
 #pragma unroll
-                for (int t = 0; t < 3; ++t) vals[t][e] = q[t];
+                for (int t = 0; t < 4; ++t) vals[t][e] = q[t];
             }
             store_chunk<ES, S>(sA, a_piece, tid, c, sbo, vals);
         }
@@ -343,10 +380,7 @@ __global__ void __launch_bounds__(kRows, 1) tc_pass_kernel(TcPassArgs a)
 #pragma unroll
                     for (int e = 0; e < 16; ++e) {
                         const int col = c0 + e;
-                        if (active && col < a.K) {
-                            const size_t fi = size_t(col) * a.R + r;
-                            mx = fmaxf(mx, fabsf(fmaf(v[e], a.F[fi], v[e] * a.Flo[fi])));
-                        }
+                        if (active && col < a.K) mx = fmaxf(mx, fabsf(v[e] * a.F[size_t(col) * a.R + r]));
                     }
                 }
                 int e2 = 0;
@@ -356,24 +390,31 @@ __global__ void __launch_bounds__(kRows, 1) tc_pass_kernel(TcPassArgs a)
                 rs2 = ldexpf(1.f, e2 - 7);
             }
             for (int c0 = 0; c0 < Np; c0 += 16) {
-                float v[16];
-                read_result<MODE, NACC>(dacc, Np, c0, rs1, cs1, v);
+                float v[16], vlo[16];
+                if (HL) read_result_hl<NACC>(dacc, Np, c0, rs1, cs1, v, vlo);
+                else read_result<MODE, NACC>(dacc, Np, c0, rs1, cs1, v);
 #pragma unroll
                 for (int h = 0; h < 16 / EPC; ++h) {
-                    float vals[3][8];
+                    float vals[4][8];
 #pragma unroll
                     for (int e = 0; e < EPC; ++e) {
-                        const int col = c0 + h * EPC + e;
-                        float x = 0.f;
+                        const int col = c0 + h * EPC + e, j = h * EPC + e;
+                        float x = 0.f, xl = 0.f;
                         if (active && col < a.K) {
                             const size_t fi = size_t(col) * a.R + r;
-                            x = fmaf(v[h * EPC + e], a.F[fi], v[h * EPC + e] * a.Flo[fi]);
+                            const float fh = a.F[fi], fl = a.Flo[fi];
+                            if (HL) {   // (v + vlo)(fh + fl) as x + xl
+                                x = v[j] * fh;
+                                xl = fmaf(v[j], fh, -x) + fmaf(v[j], fl, vlo[j] * fh);
+                            } else {
+                                x = fmaf(v[j], fh, v[j] * fl);
+                            }
                         }
-                        float q[3];
+                        float q[4];
                         if (MODE == MODE_FLOAT_TF32) split_tf32(x, 0.f, q);
-                        else slice_fixed<S>(x, 0.f, s2, q);
+                        else slice_fixed<S>(x, xl, s2, q);
 #pragma unroll
-                        for (int t = 0; t < 3; ++t) vals[t][e] = q[t];
+                        for (int t = 0; t < 4; ++t) vals[t][e] = q[t];
                     }
                     store_chunk<ES, S>(sA, a_piece, tid, c0 / EPC + h, sbo, vals);
                 }
@@ -397,15 +438,17 @@ __global__ void __launch_bounds__(kRows, 1) tc_pass_kernel(TcPassArgs a)
         // ---- epilogue: TMEM -> registers -> global ----
         float *out = a.out + size_t(p) * a.N;
         for (int c0 = 0; c0 < Np; c0 += 16) {
-            float v[16];
-            read_result<MODE, NACC>(dacc, Np, c0, rs_out, cs_out, v);
+            float v[16], vlo[16];
+            if (HL) read_result_hl<NACC>(dacc, Np, c0, rs_out, cs_out, v, vlo);
+            else read_result<MODE, NACC>(dacc, Np, c0, rs_out, cs_out, v);
             if (active) {
 #pragma unroll
                 for (int e = 0; e < 16; ++e) {
                     const int col = c0 + e;
                     if (col < a.K) {
-                        if (STORE == STORE_NSLOW) out[size_t(col) * a.R + r] = v[e];
-                        else out[size_t(r) * a.K + col] = v[e];
+                        const size_t idx = (STORE == STORE_NSLOW) ? size_t(col) * a.R + r : size_t(r) * a.K + col;
+                        out[idx] = v[e];
+                        if (HL) out[a.lo_off + idx] = vlo[e];
                     }
                 }
             }
@@ -442,7 +485,7 @@ __global__ void __launch_bounds__(kRows, 1) tc_unit_gemm_kernel(int n, int k, co
         return TF32 ? tc::to_tf32(x) : __bfloat162float(__float2bfloat16_rn(x));
     };
     for (int c = 0; c < Kp / EPC; ++c) {
-        float v[3][8] = {};
+        float v[4][8] = {};
         for (int e = 0; e < EPC; ++e) v[0][e] = round1(A[size_t(tid) * k + c * EPC + e]);
         store_chunk<ES, 1>(sA, a_bytes, tid, c, sbo, v);
         for (int row = tid; row < Np; row += kRows) {
@@ -527,13 +570,18 @@ __device__ __forceinline__ void two_sum_add(float &s, float &c, float x)
 
 __device__ __forceinline__ int diag_idx(int i, int j, int nI) { return i * nI - (i * (i - 1)) / 2 + (j - i); }
 
-__global__ void __launch_bounds__(256) tc_accum_kernel(long N, const Block *blocks, const float *V,
+template <bool HL>
+__global__ void __launch_bounds__(256) tc_accum_kernel(long N, const Block *blocks, const float *V, long lo_off,
                                                        const float *g, float *acc_hi, float *acc_lo)
 {
     const Block b = blocks[blockIdx.y];
     const long r = long(blockIdx.x) * blockDim.x + threadIdx.x;
     if (r >= N) return;
     const float *Vb = V + size_t(b.field0) * N + r;
+    // -g V (V = hi + lo when the intermediates carry a lo plane)
+    auto term = [&](float gv, size_t fo) {
+        return HL ? -fmaf(gv, Vb[fo], gv * Vb[lo_off + fo]) : -gv * Vb[fo];
+    };
     auto finish = [&](int t, float s, float c) {
         float hs = s + c;
         acc_lo[size_t(t) * N + r] = c - (hs - s);
@@ -545,7 +593,7 @@ __global__ void __launch_bounds__(256) tc_accum_kernel(long N, const Block *bloc
             float s = acc_hi[size_t(o) * N + r], c = acc_lo[size_t(o) * N + r];
             for (int q = 0; q < b.nI; ++q) {
                 const int fi = q <= t ? diag_idx(q, t, b.nI) : diag_idx(t, q, b.nI);
-                two_sum_add(s, c, -g[size_t(b.I0 + q) * N + r] * Vb[size_t(fi) * N]);
+                two_sum_add(s, c, term(g[size_t(b.I0 + q) * N + r], size_t(fi) * N));
             }
             finish(o, s, c);
         }
@@ -554,7 +602,7 @@ __global__ void __launch_bounds__(256) tc_accum_kernel(long N, const Block *bloc
     for (int j = 0; j < b.nJ; ++j) {
         const int o = b.J0 + j;
         float s = acc_hi[size_t(o) * N + r], c = acc_lo[size_t(o) * N + r];
-        for (int i = 0; i < b.nI; ++i) two_sum_add(s, c, -g[size_t(b.I0 + i) * N + r] * Vb[size_t(i * b.nJ + j) * N]);
+        for (int i = 0; i < b.nI; ++i) two_sum_add(s, c, term(g[size_t(b.I0 + i) * N + r], size_t(i * b.nJ + j) * N));
         finish(o, s, c);
     }
     if (b.kind == BLK_SYM_OFF) {
@@ -562,7 +610,7 @@ __global__ void __launch_bounds__(256) tc_accum_kernel(long N, const Block *bloc
             const int o = b.I0 + i;
             float s = acc_hi[size_t(o) * N + r], c = acc_lo[size_t(o) * N + r];
             for (int j = 0; j < b.nJ; ++j)
-                two_sum_add(s, c, -g[size_t(b.J0 + j) * N + r] * Vb[size_t(i * b.nJ + j) * N]);
+                two_sum_add(s, c, term(g[size_t(b.J0 + j) * N + r], size_t(i * b.nJ + j) * N));
             finish(o, s, c);
         }
     }
@@ -588,10 +636,10 @@ size_t pass_smem(int prec, int Np, bool dbl)
 
 int tmem_cols(int prec, int Np) { return pow2_cols(prec_info(prec).nacc * Np); }
 
-template <int MODE, int S, int SB, int LOAD, int STORE, bool DOUBLE>
+template <int MODE, int S, int SB, bool HL, int LOAD, int STORE, bool DOUBLE>
 int launch_tc_pass(Plan &P, int kind, int prec, const TcPassArgs &a, cudaStream_t s)
 {
-    auto kern = tc_pass_kernel<MODE, S, SB, LOAD, STORE, DOUBLE>;
+    auto kern = tc_pass_kernel<MODE, S, SB, HL, LOAD, STORE, DOUBLE>;
     size_t smem = pass_smem(prec, a.Np, DOUBLE);
     // TMEM: co-resident CTAs must not ask for more than 512 columns in total, so the
     // shared-memory request is raised until at most 512 / cols CTAs fit on one SM.
@@ -619,7 +667,7 @@ int launch_tc_pass(Plan &P, int kind, int prec, const TcPassArgs &a, cudaStream_
     return EXX_OK;
 }
 
-template <int MODE, int S, int SB>
+template <int MODE, int S, int SB, bool HL>
 int solve_batch_t(Plan &P, int prec, const int2 *pairs_d, int nfields, float *bufA, float *bufB, cudaStream_t s)
 {
     float *src = nullptr, *dst = bufA;
@@ -633,6 +681,7 @@ int solve_batch_t(Plan &P, int prec, const int2 *pairs_d, int nfields, float *bu
         a.N = P.N;
         a.in = src;
         a.out = dst;
+        a.lo_off = HL ? P.tc_lo_off : 0;
         const int slot = pass <= 2 ? pass : pass + 1;  // P3 uses slots 2 (fwd) and 3 (inv)
         a.B1 = static_cast<const uint8_t *>(P.Btc[prec][slot].p);
         a.B2 = pass == 2 ? static_cast<const uint8_t *>(P.Btc[prec][3].p) : nullptr;
@@ -646,11 +695,11 @@ int solve_batch_t(Plan &P, int prec, const int2 *pairs_d, int nfields, float *bu
         a.err = static_cast<int *>(P.err_d.p);
         int rc;
         switch (pass) {
-        case 0: rc = launch_tc_pass<MODE, S, SB, LOAD_PAIR, STORE_NSLOW, false>(P, EXX_TIMING_PASS1, prec, a, s); break;
-        case 1: rc = launch_tc_pass<MODE, S, SB, LOAD_KFAST, STORE_NSLOW, false>(P, EXX_TIMING_PASS2, prec, a, s); break;
-        case 2: rc = launch_tc_pass<MODE, S, SB, LOAD_KFAST, STORE_NFAST, true>(P, EXX_TIMING_PASS3, prec, a, s); break;
-        case 3: rc = launch_tc_pass<MODE, S, SB, LOAD_KSLOW, STORE_NFAST, false>(P, EXX_TIMING_PASS4, prec, a, s); break;
-        default: rc = launch_tc_pass<MODE, S, SB, LOAD_KSLOW, STORE_NSLOW, false>(P, EXX_TIMING_PASS5, prec, a, s); break;
+        case 0: rc = launch_tc_pass<MODE, S, SB, HL, LOAD_PAIR, STORE_NSLOW, false>(P, EXX_TIMING_PASS1, prec, a, s); break;
+        case 1: rc = launch_tc_pass<MODE, S, SB, HL, LOAD_KFAST, STORE_NSLOW, false>(P, EXX_TIMING_PASS2, prec, a, s); break;
+        case 2: rc = launch_tc_pass<MODE, S, SB, HL, LOAD_KFAST, STORE_NFAST, true>(P, EXX_TIMING_PASS3, prec, a, s); break;
+        case 3: rc = launch_tc_pass<MODE, S, SB, HL, LOAD_KSLOW, STORE_NFAST, false>(P, EXX_TIMING_PASS4, prec, a, s); break;
+        default: rc = launch_tc_pass<MODE, S, SB, HL, LOAD_KSLOW, STORE_NSLOW, false>(P, EXX_TIMING_PASS5, prec, a, s); break;
         }
         if (rc) return rc;
         src = dst;
@@ -758,9 +807,10 @@ int tc_prepare_orbitals(Plan &P, const double *psi_occ, int n_occ, long ld_occ, 
 int tc_solve_batch(Plan &P, int prec, const int2 *pairs_d, int nfields, float *bufA, float *bufB, cudaStream_t s)
 {
     switch (prec) {
-    case EXX_PREC_BF16X3: return solve_batch_t<MODE_FIXED_BF16, 2, 2>(P, prec, pairs_d, nfields, bufA, bufB, s);
-    case EXX_PREC_BF16X6: return solve_batch_t<MODE_FIXED_BF16, 3, 4>(P, prec, pairs_d, nfields, bufA, bufB, s);
-    case EXX_PREC_TF32X3: return solve_batch_t<MODE_FLOAT_TF32, 2, 2>(P, prec, pairs_d, nfields, bufA, bufB, s);
+    case EXX_PREC_BF16X3: return solve_batch_t<MODE_FIXED_BF16, 2, 2, false>(P, prec, pairs_d, nfields, bufA, bufB, s);
+    case EXX_PREC_BF16X6: return solve_batch_t<MODE_FIXED_BF16, 3, 4, false>(P, prec, pairs_d, nfields, bufA, bufB, s);
+    case EXX_PREC_BF16X10: return solve_batch_t<MODE_FIXED_BF16, 4, 4, true>(P, prec, pairs_d, nfields, bufA, bufB, s);
+    case EXX_PREC_TF32X3: return solve_batch_t<MODE_FLOAT_TF32, 2, 2, false>(P, prec, pairs_d, nfields, bufA, bufB, s);
     default: return EXX_ERR_INVALID_ARG;
     }
 }
@@ -769,8 +819,12 @@ int tc_accumulate(Plan &P, const Block *blocks_d, int nblocks, const float *V, c
 {
     dim3 grid(unsigned((P.N + 255) / 256), unsigned(nblocks));
     int tb = timing_begin(P, EXX_TIMING_ACCUM, s);
-    tc_accum_kernel<<<grid, 256, 0, s>>>(P.N, blocks_d, V, static_cast<const float *>(P.g32.p),
-                                         static_cast<float *>(P.acc_hi.p), static_cast<float *>(P.acc_lo.p));
+    if (prec_info(P.prec).hl)
+        tc_accum_kernel<true><<<grid, 256, 0, s>>>(P.N, blocks_d, V, P.tc_lo_off, static_cast<const float *>(P.g32.p),
+                                                   static_cast<float *>(P.acc_hi.p), static_cast<float *>(P.acc_lo.p));
+    else
+        tc_accum_kernel<false><<<grid, 256, 0, s>>>(P.N, blocks_d, V, 0, static_cast<const float *>(P.g32.p),
+                                                    static_cast<float *>(P.acc_hi.p), static_cast<float *>(P.acc_lo.p));
     timing_end(P, tb, s);
     EXX_LAUNCH("tc_accum_kernel");
     P.launches++;
@@ -787,6 +841,8 @@ int tc_finalize(Plan &P, int n_in, double *out, long ld_out, cudaStream_t s)
     P.launches++;
     return EXX_OK;
 }
+
+bool tc_is_hilo(int prec) { return prec_info(prec).hl != 0; }
 
 int tc_check_error(Plan &P, cudaStream_t s)
 {
