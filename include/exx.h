@@ -180,6 +180,22 @@ enum { EXX_TIMING_PASS1 = 0, EXX_TIMING_PASS2 = 1, EXX_TIMING_PASS3 = 2, EXX_TIM
 int exx_plan_set_timing(exx_plan plan, int enable);
 int exx_plan_get_timing(exx_plan plan, int kind, double *ms_h, long *launches_h);
 
+/* Gram matrix M = dV Psi^T W (n x n, column-major, written to the DEVICE buffer M)
+ * without any device allocation.  This entry point has no counterpart in the paper; it
+ * serves callers that cannot call cudaMalloc when they need M: code running inside
+ * stream capture, programs whose device memory belongs to a pool or framework allocator
+ * this library cannot use, and processes that reserve all device memory up front.  It
+ * needs no plan.  Psi, W: N x n DEVICE blocks (ld, ld_w >= N), n in [1, 128]; larger n
+ * returns EXX_ERR_INVALID_ARG and launches nothing.  The split-K partial sums go to a
+ * fixed 1 MiB device array inside the library (one per GPU that loads it, kept until
+ * the process exits).  The first call on each device looks up that array's address with
+ * the device current, so make that first call before any stream capture.  Every call
+ * rewrites all of the array it reads, so no clearing is needed, but all calls share the
+ * one array: calls that overlap on the GPU (different streams, or different host
+ * threads) race and must be serialised by the caller.  Asynchronous on `stream`. */
+int exx_gram_noalloc(int N, double dV, const double *Psi, int n, long ld, const double *W, long ld_w,
+                     double *M, exx_stream_t stream);
+
 /* Static text for a status code; never NULL. */
 const char *exx_status_string(int status);
 

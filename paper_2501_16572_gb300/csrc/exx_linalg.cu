@@ -4,6 +4,7 @@
 #include "exx_internal.h"
 
 #include <algorithm>
+#include <mutex>
 
 namespace exx {
 
@@ -301,4 +302,80 @@ int cholesky_neg_sym_and_inverse(Plan &P, int n, const double *M, double *Linv, 
     return EXX_OK;
 }
 
+// ---------------------------------------------------------------------------------------
+// Allocation-free Gram matrix M = dV Psi^T W (exx_gram_noalloc in include/exx.h).
+//
+// Same split-K kernels as the ACE matrix above, but the partial tiles live in a fixed
+// device array that is part of the loaded library, so the call needs no cudaMalloc and
+// no plan.  It exists for callers that must not allocate device memory at the point of
+// the call: code running inside stream capture, callers whose device memory is owned by
+// a pool or framework allocator that this library cannot use, and memory-capped
+// processes that reserve everything up front.
+namespace {
+
+constexpr int kGramNoAllocMaxN = 128;      // largest n accepted
+constexpr int kGramNoAllocMaxSplit = 8;    // K chunks (partial tiles per entry)
+
+// One copy per GPU that loads the library (1 MiB), held until the process exits.  Host
+// code must not pass this name to a kernel: on the host it is only a stand-in symbol.
+static __device__ __align__(256) double g_gram_partials[kGramNoAllocMaxSplit * kGramNoAllocMaxN * kGramNoAllocMaxN];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_gram_mutex;
+double *g_gram_addr[kMaxDevices] = {};     // device address of g_gram_partials, per device
+
+// Device address of the scratch array on the current device (looked up once per device).
+int gram_scratch(double **out)
+{
+    int dev = 0;
+    EXX_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_error("exx_gram_noalloc: device ordinal out of range");
+        return EXX_ERR_UNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lock(g_gram_mutex);
+    if (!g_gram_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_gram_partials);
+        if (e != cudaSuccess) return cuda_fail(e, "exx_gram_noalloc: cudaGetSymbolAddress");
+        g_gram_addr[dev] = static_cast<double *>(p);
+    }
+    *out = g_gram_addr[dev];
+    return EXX_OK;
+}
+
+}  // namespace
 }  // namespace exx
+
+extern "C" int exx_gram_noalloc(int N, double dV, const double *Psi, int n, long ld, const double *W, long ld_w,
+                                double *M, exx_stream_t stream)
+{
+    using namespace exx;
+    if (!Psi || !W || !M) {
+        set_error("exx_gram_noalloc: NULL array");
+        return EXX_ERR_INVALID_ARG;
+    }
+    if (N < 1 || ld < N || ld_w < N) {
+        set_error("exx_gram_noalloc: need N >= 1 and leading dimensions >= N");
+        return EXX_ERR_INVALID_ARG;
+    }
+    if (n < 1 || n > kGramNoAllocMaxN) {
+        set_error("exx_gram_noalloc: n must be in [1, 128] (the fixed scratch holds 8 partial 128 x 128 tiles)");
+        return EXX_ERR_INVALID_ARG;
+    }
+    double *ws = nullptr;
+    if (int rc = gram_scratch(&ws)) return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int g = (n + kTile - 1) / kTile;
+    long kchunk = (long(N) + kGramNoAllocMaxSplit - 1) / kGramNoAllocMaxSplit;
+    kchunk = std::max<long>(256, ((kchunk + kKt - 1) / kKt) * kKt);
+    const int nsplit = int((long(N) + kchunk - 1) / kchunk);   // <= kGramNoAllocMaxSplit
+    // every partial tile entry (z, i < n, j < n) is rewritten below, so nothing from an
+    // earlier call survives into this one and no clearing is needed
+    gemm_tn_partial_kernel<<<dim3(g, g, nsplit), kGemmThreads, 0, s>>>(n, n, N, kchunk, Psi, ld, W, ld_w, ws);
+    EXX_LAUNCH("gemm_tn_partial_kernel (no-alloc)");
+    const long tot = long(n) * n;
+    splitk_reduce_kernel<<<unsigned((tot + 255) / 256), 256, 0, s>>>(ws, nsplit, n, n, dV, M, n);
+    EXX_LAUNCH("splitk_reduce_kernel (no-alloc)");
+    return EXX_OK;
+}
