@@ -267,7 +267,18 @@ __global__ void __launch_bounds__(kRows, 1) tc_pass_kernel(TcPassArgs a)
     uint8_t *sB1 = smem;
     uint8_t *sB2 = smem + a.img_bytes;
     uint8_t *sA = smem + (DOUBLE ? 2 : 1) * a.img_bytes;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sA + a_piece * S);
+    // Input staging, filled by cp.async one tile ahead.  KSLOW / PAIR: [k][thread] (a warp
+    // touches 32 consecutive words); KFAST: [thread][Kp + 4] (16-byte copies of the row,
+    // read back as float4, conflict-free because (Kp + 4) / 4 is odd).  PAIR stages
+    // psi_m hi, psi_m lo, psi_n hi, psi_n lo; the others stage hi and lo.
+    constexpr int NSTG = LOAD == LOAD_PAIR ? 4 : (HL ? 2 : 1);
+    const int stg_len = kRows * (Kp + 4);
+    float *stg = reinterpret_cast<float *>(sA + a_piece * S);
+    // pass 3 stages f(Lambda) D1 ([col][thread], hi and lo) in the same space: the next
+    // tile is fetched only after that middle step has consumed it
+    float *mid_hi = stg;
+    float *mid_lo = stg + Np * kRows;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(stg + std::max(NSTG * stg_len, DOUBLE ? 2 * Np * kRows : 0));
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
     int *sflag = reinterpret_cast<int *>(tslot + 1);
     const float *cs1 = reinterpret_cast<const float *>(sB1 + SB * b_piece);
@@ -280,6 +291,7 @@ __global__ void __launch_bounds__(kRows, 1) tc_pass_kernel(TcPassArgs a)
         *reinterpret_cast<uint4 *>(sB1 + i) = *reinterpret_cast<const uint4 *>(a.B1 + i);
         if (DOUBLE) *reinterpret_cast<uint4 *>(sB2 + i) = *reinterpret_cast<const uint4 *>(a.B2 + i);
     }
+    for (int i = tid; i < NSTG * stg_len; i += kRows) stg[i] = 0.f;
     if (tid == 0) {
         tc::mbar_init(bar, 1);
         *sflag = 0;
@@ -297,44 +309,79 @@ __global__ void __launch_bounds__(kRows, 1) tc_pass_kernel(TcPassArgs a)
 
     const long rows = long(a.nfields) * a.R;
     const long ntiles = (rows + kRows - 1) / kRows;
+    const bool vec16 = ((a.K & 3) == 0) && ((a.N & 3) == 0) && ((a.lo_off & 3) == 0);
+    // Issue the copies of this thread's row of tile t into the staging (rows past the
+    // end are skipped; the conversion treats them as zero).
+    auto prefetch = [&](long t) {
+        if (t >= ntiles) return;
+        const long gg = t * kRows + tid;
+        if (gg >= rows) return;
+        const int pp = int(gg / a.R), rr = int(gg - long(pp) * a.R);
+        if (LOAD == LOAD_PAIR) {
+            const int2 mn = a.pairs[pp];
+            const float *src[4] = {a.psi_hi + size_t(a.occ_off + mn.x) * a.N, a.psi_lo + size_t(a.occ_off + mn.x) * a.N,
+                                   a.psi_hi + size_t(mn.y) * a.N, a.psi_lo + size_t(mn.y) * a.N};
+            for (int k = 0; k < a.K; ++k)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) tc::cp_async4(stg + q * stg_len + k * kRows + tid, src[q] + size_t(k) * a.R + rr);
+        } else if (LOAD == LOAD_KSLOW) {
+            const float *src = a.in + size_t(pp) * a.N + rr;
+            for (int k = 0; k < a.K; ++k) {
+                tc::cp_async4(stg + k * kRows + tid, src + size_t(k) * a.R);
+                if (HL) tc::cp_async4(stg + stg_len + k * kRows + tid, src + a.lo_off + size_t(k) * a.R);
+            }
+        } else {
+            const float *src = a.in + size_t(pp) * a.N + size_t(rr) * a.K;
+            float *dh = stg + tid * (Kp + 4);
+            if (vec16) {
+                for (int k = 0; k < a.K; k += 4) {
+                    tc::cp_async16(dh + k, src + k);
+                    if (HL) tc::cp_async16(dh + stg_len + k, src + a.lo_off + k);
+                }
+            } else {
+                for (int k = 0; k < a.K; ++k) {
+                    tc::cp_async4(dh + k, src + k);
+                    if (HL) tc::cp_async4(dh + stg_len + k, src + a.lo_off + k);
+                }
+            }
+        }
+        tc::cp_async_commit();
+    };
+    // Staged value (hi, lo) of element k of this thread's row.
+    auto staged = [&](int k, float &hi, float &lo) {
+        if (LOAD == LOAD_PAIR) {
+            const float ah = stg[k * kRows + tid], al = stg[stg_len + k * kRows + tid];
+            const float bh = stg[2 * stg_len + k * kRows + tid], bl = stg[3 * stg_len + k * kRows + tid];
+            hi = ah * bh;
+            lo = fmaf(ah, bh, -hi) + fmaf(ah, bl, al * bh);
+        } else if (LOAD == LOAD_KSLOW) {
+            hi = stg[k * kRows + tid];
+            lo = HL ? stg[stg_len + k * kRows + tid] : 0.f;
+        } else {
+            hi = stg[tid * (Kp + 4) + k];
+            lo = HL ? stg[stg_len + tid * (Kp + 4) + k] : 0.f;
+        }
+    };
+    prefetch(blockIdx.x);
     for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const long g = tile * kRows + tid;
         const bool active = g < rows;
         const int p = active ? int(g / a.R) : 0;
         const int r = active ? int(g - long(p) * a.R) : 0;
-        // ---- prologue: this thread's row (K values) -> pieces in SMEM ----
-        const float *in = a.in + size_t(p) * a.N;
-        const float *mh = nullptr, *ml = nullptr, *nh = nullptr, *nl = nullptr;
-        if (LOAD == LOAD_PAIR && active) {
-            const int2 mn = a.pairs[p];
-            mh = a.psi_hi + size_t(a.occ_off + mn.x) * a.N;
-            ml = a.psi_lo + size_t(a.occ_off + mn.x) * a.N;
-            nh = a.psi_hi + size_t(mn.y) * a.N;
-            nl = a.psi_lo + size_t(mn.y) * a.N;
-        }
-        auto load = [&](int k, float &hi, float &lo) {
-            hi = 0.f;
-            lo = 0.f;
-            if (!active || k >= a.K) return;
-            if (LOAD == LOAD_PAIR) {
-                const size_t idx = size_t(k) * a.R + r;
-                const float ah = mh[idx], al = ml[idx], bh = nh[idx], bl = nl[idx];
-                hi = ah * bh;
-                lo = fmaf(ah, bh, -hi) + fmaf(ah, bl, al * bh);
-            } else {
-                const size_t idx = (LOAD == LOAD_KSLOW) ? size_t(k) * a.R + r : size_t(r) * a.K + k;
-                hi = in[idx];
-                if (HL) lo = in[a.lo_off + idx];
-            }
-        };
-        float s_in = 1.f, rs1 = 1.f;
-        if (MODE == MODE_FIXED_BF16) {
-            float mx = 0.f;
-            for (int k = 0; k < a.K; ++k) {
+        // ---- prologue: staged row -> row maximum -> pieces in SMEM ----
+        tc::cp_async_wait_all();
+        float mx = 0.f;
+        for (int k0 = 0; k0 < Kp; k0 += 4) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
                 float hi, lo;
-                load(k, hi, lo);
+                staged(k0 + e, hi, lo);
                 mx = fmaxf(mx, fabsf(hi));
             }
+        }
+        if (!active) mx = 0.f;
+        float s_in = 1.f, rs1 = 1.f;
+        if (MODE == MODE_FIXED_BF16) {
             int e = 0;
             if (mx > 0.f) frexpf(mx, &e);
             e = max(e, -100);   // rows below 2^-100 are flushed to zero slices
@@ -346,7 +393,8 @@ __global__ void __launch_bounds__(kRows, 1) tc_pass_kernel(TcPassArgs a)
 #pragma unroll
             for (int e = 0; e < EPC; ++e) {
                 float hi, lo, q[4];
-                load(c * EPC + e, hi, lo);
+                staged(c * EPC + e, hi, lo);
+                if (!active) hi = lo = 0.f;
                 if (MODE == MODE_FLOAT_TF32) split_tf32(hi, lo, q);
                 else slice_fixed<S>(hi, lo, s_in, q);
 #pragma unroll
@@ -354,6 +402,7 @@ __global__ void __launch_bounds__(kRows, 1) tc_pass_kernel(TcPassArgs a)
             }
             store_chunk<ES, S>(sA, a_piece, tid, c, sbo, vals);
         }
+        if (!DOUBLE) prefetch(tile + gridDim.x);   // staged row consumed: fetch the next
         tc::fence_proxy_async_smem();
         tc::tc_fence_before();
         __syncthreads();
@@ -370,58 +419,66 @@ __global__ void __launch_bounds__(kRows, 1) tc_pass_kernel(TcPassArgs a)
         float rs_out = rs1;
         const float *cs_out = cs1;
         if (DOUBLE) {
-            // D1 * f(Lambda) -> pieces of A (same rows, K = modes) -> second GEMM, same TMEM
-            float s2 = 1.f, rs2 = 1.f;
-            if (MODE == MODE_FIXED_BF16) {
-                float mx = 0.f;
-                for (int c0 = 0; c0 < Np; c0 += 16) {
-                    float v[16];
-                    read_result<MODE, NACC>(dacc, Np, c0, rs1, cs1, v);
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) {
-                        const int col = c0 + e;
-                        if (active && col < a.K) mx = fmaxf(mx, fabsf(v[e] * a.F[size_t(col) * a.R + r]));
-                    }
-                }
-                int e2 = 0;
-                if (mx > 0.f) frexpf(mx, &e2);
-                e2 = max(e2, -100);
-                s2 = ldexpf(1.f, 7 - e2);
-                rs2 = ldexpf(1.f, e2 - 7);
-            }
+            // D1 * f(Lambda) -> staging (one TMEM read) -> pieces of A (same rows, K = modes)
+            // -> second GEMM into the same TMEM columns
+            float mx2 = 0.f;
             for (int c0 = 0; c0 < Np; c0 += 16) {
                 float v[16], vlo[16];
                 if (HL) read_result_hl<NACC>(dacc, Np, c0, rs1, cs1, v, vlo);
                 else read_result<MODE, NACC>(dacc, Np, c0, rs1, cs1, v);
+                float fh[16], fl[16];
 #pragma unroll
-                for (int h = 0; h < 16 / EPC; ++h) {
-                    float vals[4][8];
-#pragma unroll
-                    for (int e = 0; e < EPC; ++e) {
-                        const int col = c0 + h * EPC + e, j = h * EPC + e;
-                        float x = 0.f, xl = 0.f;
-                        if (active && col < a.K) {
-                            const size_t fi = size_t(col) * a.R + r;
-                            const float fh = a.F[fi], fl = a.Flo[fi];
-                            if (HL) {   // (v + vlo)(fh + fl) as x + xl
-                                x = v[j] * fh;
-                                xl = fmaf(v[j], fh, -x) + fmaf(v[j], fl, vlo[j] * fh);
-                            } else {
-                                x = fmaf(v[j], fh, v[j] * fl);
-                            }
-                        }
-                        float q[4];
-                        if (MODE == MODE_FLOAT_TF32) split_tf32(x, 0.f, q);
-                        else slice_fixed<S>(x, xl, s2, q);
-#pragma unroll
-                        for (int t = 0; t < 4; ++t) vals[t][e] = q[t];
+                for (int e = 0; e < 16; ++e) {
+                    const int col = c0 + e;
+                    fh[e] = 0.f;
+                    fl[e] = 0.f;
+                    if (active && col < a.K) {
+                        const size_t fi = size_t(col) * a.R + r;
+                        fh[e] = a.F[fi];
+                        fl[e] = a.Flo[fi];
                     }
-                    store_chunk<ES, S>(sA, a_piece, tid, c0 / EPC + h, sbo, vals);
                 }
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    float x, xl = 0.f;
+                    if (HL) {   // (v + vlo)(fh + fl) as x + xl
+                        x = v[e] * fh[e];
+                        xl = fmaf(v[e], fh[e], -x) + fmaf(v[e], fl[e], vlo[e] * fh[e]);
+                    } else {
+                        x = fmaf(v[e], fh[e], v[e] * fl[e]);
+                    }
+                    mx2 = fmaxf(mx2, fabsf(x));
+                    mid_hi[(c0 + e) * kRows + tid] = x;
+                    mid_lo[(c0 + e) * kRows + tid] = xl;
+                }
+            }
+            float s2 = 1.f, rs2 = 1.f;
+            if (MODE == MODE_FIXED_BF16) {
+                int e2 = 0;
+                if (mx2 > 0.f) frexpf(mx2, &e2);
+                e2 = max(e2, -100);
+                s2 = ldexpf(1.f, 7 - e2);
+                rs2 = ldexpf(1.f, e2 - 7);
+            }
+            for (int c = 0; c < Np / EPC; ++c) {
+                float vals[4][8];
+#pragma unroll
+                for (int e = 0; e < EPC; ++e) {
+                    const int k = c * EPC + e;
+                    float q[4];
+                    if (MODE == MODE_FLOAT_TF32) split_tf32(mid_hi[k * kRows + tid], 0.f, q);
+                    else slice_fixed<S>(mid_hi[k * kRows + tid], mid_lo[k * kRows + tid], s2, q);
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) vals[t][e] = q[t];
+                }
+                store_chunk<ES, S>(sA, a_piece, tid, c, sbo, vals);
             }
             tc::fence_proxy_async_smem();
             tc::tc_fence_before();
             __syncthreads();
+            // every thread is past the middle step, whose staging (laid out [col][thread])
+            // overlaps other threads' input rows: only now fetch the next tile
+            prefetch(tile + gridDim.x);
             if (tid == 0) {
                 tc::tc_fence_after();
                 issue_gemm<MODE, S, SB>(tmem, Np, sA_addr, a_piece, sB2_addr, b_piece, sbo, ksteps, idesc);
@@ -456,6 +513,7 @@ __global__ void __launch_bounds__(kRows, 1) tc_pass_kernel(TcPassArgs a)
         tc::tc_fence_before();
         __syncthreads();   // TMEM reads done before the next tile's MMA overwrites it
     }
+    tc::cp_async_wait_all();   // no copy may still target shared memory at exit
     if (tid == 0 && *sflag) atomicExch(a.err, 1);
     tc::tc_fence_before();
     __syncthreads();
@@ -627,11 +685,13 @@ __global__ void tc_finalize_kernel(long N, int n_in, const float *acc_hi, const 
 }
 
 // ---- launch helpers -------------------------------------------------------------------
-size_t pass_smem(int prec, int Np, bool dbl)
+size_t pass_smem(int prec, int Np, bool dbl, int load)
 {
     const PrecInfo pi = prec_info(prec);
     size_t a = size_t(pi.S) * kRows * Np * pi.es;
-    return (dbl ? 2 : 1) * image_bytes(prec, Np) + a + 64;
+    size_t staging = size_t(load == LOAD_PAIR ? 4 : (pi.hl ? 2 : 1)) * kRows * (Np + 4) * sizeof(float);
+    if (dbl) staging = std::max(staging, size_t(2) * kRows * Np * sizeof(float));
+    return (dbl ? 2 : 1) * image_bytes(prec, Np) + a + staging + 64;
 }
 
 int tmem_cols(int prec, int Np) { return pow2_cols(prec_info(prec).nacc * Np); }
@@ -640,7 +700,7 @@ template <int MODE, int S, int SB, bool HL, int LOAD, int STORE, bool DOUBLE>
 int launch_tc_pass(Plan &P, int kind, int prec, const TcPassArgs &a, cudaStream_t s)
 {
     auto kern = tc_pass_kernel<MODE, S, SB, HL, LOAD, STORE, DOUBLE>;
-    size_t smem = pass_smem(prec, a.Np, DOUBLE);
+    size_t smem = pass_smem(prec, a.Np, DOUBLE, LOAD);
     // TMEM: co-resident CTAs must not ask for more than 512 columns in total, so the
     // shared-memory request is raised until at most 512 / cols CTAs fit on one SM.
     const int cols = tmem_cols(prec, a.Np);
@@ -718,7 +778,9 @@ int tc_upload(Plan &P, int prec)
     const int inv_of[6] = {0, 0, 0, 1, 1, 1};
     for (int d = 0; d < 3; ++d) {
         const int Np = pad16(P.n[d]);
-        if (pass_smem(prec, Np, d == 1) > 232448 || tmem_cols(prec, Np) > 512) {
+        // the largest footprint of the passes on this axis: pair prologue (z), double (y)
+        const size_t need = std::max(pass_smem(prec, Np, d == 1, LOAD_KSLOW), pass_smem(prec, Np, false, d == 2 ? LOAD_PAIR : LOAD_KSLOW));
+        if (need > 232448 || tmem_cols(prec, Np) > 512) {
             set_error("split precision: grid axis too long for the on-chip operand images of this build");
             return EXX_ERR_UNSUPPORTED;
         }
