@@ -102,6 +102,13 @@ int exx_plan_set_precision(exx_plan plan, int prec);
  * orbitals per pair block (0 = default).  Results do not depend on either. */
 int exx_plan_set_batch(exx_plan plan, int pairs_per_batch, int block_orbitals);
 
+/* Shard the pair solves of exx_apply over `world` processes (one GPU each): this plan then
+ * runs only the batches b with b mod world == rank and writes PARTIAL outputs; summing
+ * `out` over the ranks (one all-reduce or reduce-scatter of N x n_in doubles) gives the
+ * full result.  Each unique pair is solved by exactly one rank.  world = 1 (default)
+ * runs everything.  0 <= rank < world. */
+int exx_plan_set_shard(exx_plan plan, int rank, int world);
+
 /* Free the plan and its device workspace (synchronizes the device first). */
 int exx_plan_destroy(exx_plan plan);
 

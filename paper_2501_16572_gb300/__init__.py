@@ -43,7 +43,7 @@ PREC_NAMES = {EXX_PREC_FP64: "fp64", EXX_PREC_BF16X3: "bf16x3", EXX_PREC_TF32X3:
 EXPORTED = ["exx_plan_create", "exx_plan_set_precision", "exx_plan_set_batch", "exx_plan_destroy",
             "exx_plan_get", "exx_apply", "exx_energy", "ace_build", "ace_apply", "exx_ace_step_host",
             "exx_apply_batched", "exx_plan_launch_count", "exx_status_string", "exx_last_error",
-            "exx_plan_set_timing", "exx_plan_get_timing", "exx_gram_noalloc"]
+            "exx_plan_set_timing", "exx_plan_get_timing", "exx_gram_noalloc", "exx_plan_set_shard"]
 TIMING_KINDS = ["pass1", "pass2", "pass3", "pass4", "pass5", "accum", "prep", "gemm", "chol", "energy"]
 
 _lib = None
@@ -90,6 +90,7 @@ def load():
     L.exx_plan_launch_count.restype = _l
     L.exx_plan_set_timing.argtypes = [_vp, _i]
     L.exx_plan_get_timing.argtypes = [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_l)]
+    L.exx_plan_set_shard.argtypes = [_vp, _i, _i]
     L.exx_gram_noalloc.argtypes = [_i, _d, _vp, _i, _l, _vp, _l, _vp, _vp]
     L.exx_status_string.argtypes = [_i]
     L.exx_status_string.restype = ctypes.c_char_p
@@ -167,6 +168,10 @@ class Plan:
     def set_batch(self, pairs_per_batch=0, block_orbitals=0):
         _check(load().exx_plan_set_batch(self._h, int(pairs_per_batch), int(block_orbitals)),
                "exx_plan_set_batch")
+
+    def set_shard(self, rank, world):
+        """Run only batches b with b % world == rank; outputs become partial sums."""
+        _check(load().exx_plan_set_shard(self._h, int(rank), int(world)), "exx_plan_set_shard")
 
     def eigvals(self, d):
         import numpy as np

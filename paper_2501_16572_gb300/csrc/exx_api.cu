@@ -242,6 +242,16 @@ int exx_plan_set_batch(exx_plan plan, int pairs_per_batch, int block_orbitals)
     return EXX_OK;
 }
 
+int exx_plan_set_shard(exx_plan plan, int rank, int world)
+{
+    Plan *P = as_plan(plan);
+    if (!P) return invalid("exx_plan_set_shard: plan is NULL");
+    if (world < 1 || rank < 0 || rank >= world) return invalid("exx_plan_set_shard: need 0 <= rank < world");
+    P->shard_rank = rank;
+    P->shard_world = world;
+    return EXX_OK;
+}
+
 int exx_plan_destroy(exx_plan plan)
 {
     Plan *P = as_plan(plan);
@@ -337,6 +347,7 @@ int exx_apply(exx_plan plan, const double *Psi_occ, int n_occ, long ld_occ, cons
         EXX_CUDA(cudaMemset2DAsync(out, size_t(ld_out) * sizeof(double), 0, size_t(P->N) * sizeof(double),
                                    n_in, s));
         for (size_t b = 0; b < S.batches.size(); ++b) {
+            if (int(b % P->shard_world) != P->shard_rank) continue;
             const Batch &bt = S.batches[b];
             double *V = nullptr;
             if (int rc = fp64_solve_batch(*P, Psi_occ, ld_occ, Psi_in, ld_in, pairs_d + S.pair0[b], bt.nfields,
@@ -358,6 +369,7 @@ int exx_apply(exx_plan plan, const double *Psi_occ, int n_occ, long ld_occ, cons
     if (int rc = dev_reserve(P->work[0], fb)) return rc;
     if (int rc = dev_reserve(P->work[1], fb)) return rc;
     for (size_t b = 0; b < S.batches.size(); ++b) {
+        if (int(b % P->shard_world) != P->shard_rank) continue;
         const Batch &bt = S.batches[b];
         if (int rc = tc_solve_batch(*P, prec, pairs_d + S.pair0[b], bt.nfields, static_cast<float *>(P->work[0].p),
                                     static_cast<float *>(P->work[1].p), s))

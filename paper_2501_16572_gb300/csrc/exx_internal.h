@@ -110,6 +110,7 @@ struct Plan {
     int prec = EXX_PREC_FP64;
     int pairs_per_batch = 0;   // 0 = default
     int block_orbitals = 0;    // 0 = default
+    int shard_rank = 0, shard_world = 1;   // exx_plan_set_shard
     int device = 0;
     int num_sms = 0;
     std::vector<double> V[3], lam[3], F;   // host copies

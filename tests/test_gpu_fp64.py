@@ -177,3 +177,19 @@ def test_timing_and_launch_counts(exx):
     assert launches > 0
     assert sum(n for _, n in t.values()) == launches
     assert all(ms > 0 for ms, _ in t.values())
+
+
+@pytest.mark.parametrize("prec", [0, 4], ids=["fp64", "bf16x10"])
+def test_shards_sum_to_the_full_result(exx, prec):
+    """Two shards run one after the other on one GPU; their partial outputs add up."""
+    s = synth.small_system(n=(13, 12, 11), h=0.4, bc=(1, 0, 1), n_orb=11, kernel=0, seed=44, n_occ=8)
+    plan, psi, f, full = _run(exx, s, prec=prec, batch=(16, 2))
+    parts = []
+    for rank in range(2):
+        p = exx.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+        p.set_precision(prec)
+        p.set_batch(16, 2)
+        p.set_shard(rank, 2)
+        parts.append(p.apply(psi[:s.n_occ], f, psi))
+    tol = 1e-13 if prec == 0 else 1e-7
+    assert pm.rel((parts[0] + parts[1]).cpu().numpy(), full.cpu().numpy()) < tol
