@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n-orb", type=int, default=128)
+    ap.add_argument("--batch", type=int, default=0, help="pairs per batch (0 = library default)")
     return ap.parse_args()
 
 
@@ -180,6 +181,8 @@ def run_ours(args):
     def make_plan(name):
         p = exx.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
         p.set_precision(prec_code(exx, name))
+        if args.batch:
+            p.set_batch(args.batch, 0)
         return p
 
     plan = make_plan(prec_name)

@@ -66,12 +66,13 @@ static void free_plan_buffers(Plan &P)
         dev_free(*b);
 }
 
-// Default batch size: enough fields per pass to fill the GPU several times over while
-// the batch buffers stay a modest part of L2 (tensor path) or of HBM (FP64 path).
+// Default batch size: enough fields per launch that every SM loops over tens of tiles
+// (launch start-up and the last tile's drain are amortised), capped by a memory budget
+// per batch buffer.
 static int default_pairs(const Plan &P, int block)
 {
     long per_field = long(P.N) * (P.prec == EXX_PREC_FP64 || P.prec == EXX_PREC_BF16X10 ? 8 : 4);
-    long budget = (P.prec == EXX_PREC_FP64) ? (256L << 20) : (48L << 20);
+    long budget = 512L << 20;
     long pairs = std::max<long>(block * block, budget / per_field);
     pairs = std::min<long>(pairs, 1024);
     return int((pairs / (block * block)) * (block * block));

@@ -131,10 +131,9 @@ __device__ __forceinline__ void store_chunk(uint8_t *img, uint32_t piece_bytes, 
             uint32_t w[4];
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
-                // values are bf16-exact (small integers or bf16-rounded): take the top half
-                uint32_t lo16 = __float_as_uint(vals[q][2 * t]) >> 16;
-                uint32_t hi16 = __float_as_uint(vals[q][2 * t + 1]) & 0xFFFF0000u;
-                w[t] = lo16 | hi16;
+                // values are bf16-exact (small integers or bf16-rounded): one packing cvt
+                __nv_bfloat162 b2 = __floats2bfloat162_rn(vals[q][2 * t], vals[q][2 * t + 1]);
+                w[t] = *reinterpret_cast<uint32_t *>(&b2);
             }
             v = make_uint4(w[0], w[1], w[2], w[3]);
         }
@@ -159,85 +158,75 @@ __device__ __forceinline__ void issue_gemm(uint32_t d, int Np, uint32_t a_base, 
                 acc = 1;
             }
     } else {
-        for (int l = 0; l < S; ++l) {
-            uint32_t acc = 0;
-            for (int i = 0; i <= l; ++i) {
-                const int j = l - i;
-                for (int ks = 0; ks < ksteps; ++ks) {
+        // k-step outermost, then level: consecutive MMAs accumulate into different TMEM
+        // accumulators instead of forming one dependent chain
+        for (int ks = 0; ks < ksteps; ++ks) {
+            for (int l = 0; l < S; ++l) {
+                for (int i = 0; i <= l; ++i) {
+                    const int j = l - i;
                     uint64_t ad = tc::smem_desc(a_base + i * a_piece + ks * 256u, 128u, sbo);
                     uint64_t bd = tc::smem_desc(b_base + j * b_piece + ks * 256u, 128u, sbo);
-                    tc::mma_bf16(d + uint32_t(l * Np), ad, bd, idesc, acc);
-                    acc = 1;
+                    tc::mma_bf16(d + uint32_t(l * Np), ad, bd, idesc, (ks > 0 || i > 0) ? 1u : 0u);
                 }
             }
-        }
-        if (SB > S) {
-            for (int ks = 0; ks < ksteps; ++ks) {
+            if (SB > S) {
                 uint64_t ad = tc::smem_desc(a_base + ks * 256u, 128u, sbo);
                 uint64_t bd = tc::smem_desc(b_base + S * b_piece + ks * 256u, 128u, sbo);
-                tc::mma_bf16(d + uint32_t(S * Np), ad, bd, idesc, ks > 0);
+                tc::mma_bf16(d + uint32_t(S * Np), ad, bd, idesc, ks > 0 ? 1u : 0u);
             }
         }
     }
 }
 
-// Read 16 result columns [c0, c0+16) of this thread's row, combining the NACC levels
-// (level l carries weight 2^(-8 l)) and applying the row and column scales.
-template <int MODE, int NACC>
-__device__ __forceinline__ void read_result(uint32_t d, int Np, int c0, float rs, const float *cs, float (&v)[16])
+// Read 8 result columns [c0, c0+8) of this thread's row: combine the NACC levels (level l
+// carries weight 2^(-8 l)) and apply the row and column scales.  With HL the value is
+// returned as an unevaluated sum vh + vl: level 0 is an exact integer, the lower levels
+// are folded into t, and TwoSum keeps the rounding error of l0 + t (the scales are
+// powers of two, exact).
+template <int MODE, int NACC, bool HL>
+__device__ __forceinline__ void read8(uint32_t d, int Np, int c0, float rs, const float *cs, float (&vh)[8],
+                                      float (&vl)[8])
 {
     if (MODE == MODE_FLOAT_TF32) {
-        tc::tmem_ld16(d + uint32_t(c0), v);
+        tc::tmem_ld8(d + uint32_t(c0), vh);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) vl[e] = 0.f;
         return;
     }
-    float t[16];
+    float t[8];
 #pragma unroll
-    for (int e = 0; e < 16; ++e) t[e] = 0.f;
-#pragma unroll
-    for (int l = NACC - 1; l >= 1; --l) {
-        float lv[16];
-        tc::tmem_ld16(d + uint32_t(l * Np + c0), lv);
-#pragma unroll
-        for (int e = 0; e < 16; ++e) t[e] = (lv[e] + t[e]) * (1.f / 256.f);
-    }
-    float l0[16];
-    tc::tmem_ld16(d + uint32_t(c0), l0);
-#pragma unroll
-    for (int e = 0; e < 16; ++e) v[e] = (l0[e] + t[e]) * rs * cs[c0 + e];
-}
-
-// As read_result (fixed mode) but returns each value as an unevaluated sum vh + vl:
-// level 0 is an exact integer, the lower levels are folded into t, and TwoSum keeps
-// the rounding error of l0 + t; the scales are powers of two (exact).
-template <int NACC>
-__device__ __forceinline__ void read_result_hl(uint32_t d, int Np, int c0, float rs, const float *cs, float (&vh)[16],
-                                               float (&vl)[16])
-{
-    float t[16];
-#pragma unroll
-    for (int e = 0; e < 16; ++e) t[e] = 0.f;
+    for (int e = 0; e < 8; ++e) t[e] = 0.f;
 #pragma unroll
     for (int l = NACC - 1; l >= 1; --l) {
-        float lv[16];
-        tc::tmem_ld16(d + uint32_t(l * Np + c0), lv);
+        float lv[8];
+        tc::tmem_ld8(d + uint32_t(l * Np + c0), lv);
 #pragma unroll
-        for (int e = 0; e < 16; ++e) t[e] = (lv[e] + t[e]) * (1.f / 256.f);
+        for (int e = 0; e < 8; ++e) t[e] = (lv[e] + t[e]) * (1.f / 256.f);
     }
-    float l0[16];
-    tc::tmem_ld16(d + uint32_t(c0), l0);
+    float l0[8];
+    tc::tmem_ld8(d + uint32_t(c0), l0);
 #pragma unroll
-    for (int e = 0; e < 16; ++e) {
-        const float h = l0[e] + t[e];
-        const float bp = h - l0[e];
-        const float lo = (l0[e] - (h - bp)) + (t[e] - bp);
+    for (int e = 0; e < 8; ++e) {
         const float sc = rs * cs[c0 + e];
-        vh[e] = h * sc;
-        vl[e] = lo * sc;
+        if (HL) {
+            const float h = l0[e] + t[e];
+            const float bp = h - l0[e];
+            vl[e] = ((l0[e] - (h - bp)) + (t[e] - bp)) * sc;
+            vh[e] = h * sc;
+        } else {
+            vh[e] = (l0[e] + t[e]) * sc;
+            vl[e] = 0.f;
+        }
     }
 }
 
 // ---------------------------------------------------------------------------------------
-// Pass kernel.  Rows of the batch are cut into tiles of 128; CTAs loop over tiles.
+// Pass kernel.  Rows of the batch are cut into tiles of 128 (= TMEM lanes); TPR threads
+// share a row, thread (q, row) = threadIdx.x = q*128 + row owning the 16-byte chunks
+// c = q, q+TPR, ... of the row (copy, slicing) and the 8-column chunks cc = q, q+TPR,
+// ... of the result (TMEM read, stores).  Warps w and w+4 see TMEM lane quarter w%4.
+// CTAs loop over tiles; the next tile's rows arrive by cp.async while the current
+// tile's MMAs and epilogue run.
 struct TcPassArgs {
     int nfields, R, K, Np;          // K = n_d (contracted length), Np = K padded to 16
     long N;
@@ -253,13 +242,14 @@ struct TcPassArgs {
     int *err;
 };
 
-template <int MODE, int S, int SB, bool HL, int LOAD, int STORE, bool DOUBLE>
-__global__ void __launch_bounds__(kRows, 1) tc_pass_kernel(TcPassArgs a)
+template <int MODE, int S, int SB, bool HL, int LOAD, int STORE, bool DOUBLE, int TPR, int NBUF>
+__global__ void __launch_bounds__(kRows * TPR, 1) tc_pass_kernel(TcPassArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     constexpr int ES = MODE == MODE_FLOAT_TF32 ? 4 : 2;
-    constexpr int EPC = 16 / ES;
+    constexpr int EPC = 16 / ES;                       // elements per 16-byte chunk
     constexpr int NACC = MODE == MODE_FLOAT_TF32 ? 1 : (SB > S ? S + 1 : S);
+    constexpr int NT = kRows * TPR;
     const int Np = a.Np, Kp = a.Np;
     const uint32_t sbo = uint32_t(Kp) * ES * 8;          // bytes per 8-row group
     const uint32_t a_piece = uint32_t(kRows) * Kp * ES;
@@ -267,31 +257,30 @@ __global__ void __launch_bounds__(kRows, 1) tc_pass_kernel(TcPassArgs a)
     uint8_t *sB1 = smem;
     uint8_t *sB2 = smem + a.img_bytes;
     uint8_t *sA = smem + (DOUBLE ? 2 : 1) * a.img_bytes;
-    // Input staging, filled by cp.async one tile ahead.  KSLOW / PAIR: [k][thread] (a warp
-    // touches 32 consecutive words); KFAST: [thread][Kp + 4] (16-byte copies of the row,
-    // read back as float4, conflict-free because (Kp + 4) / 4 is odd).  PAIR stages
-    // psi_m hi, psi_m lo, psi_n hi, psi_n lo; the others stage hi and lo.
+    // Input staging.  KSLOW / PAIR: [k][row] (a warp touches 32 consecutive words); KFAST:
+    // [row][Kp + 4] (16-byte copies, read back conflict-free because (Kp + 4)/4 is odd).
+    // PAIR stages psi_m hi, psi_m lo, psi_n hi, psi_n lo; the others hi (and lo).  Pass 3
+    // stages f(Lambda) D1 ([col][row], hi and lo) in the same space after the first GEMM.
     constexpr int NSTG = LOAD == LOAD_PAIR ? 4 : (HL ? 2 : 1);
+    // NBUF staging buffers = tiles whose copies are in flight
     const int stg_len = kRows * (Kp + 4);
-    float *stg = reinterpret_cast<float *>(sA + a_piece * S);
-    // pass 3 stages f(Lambda) D1 ([col][thread], hi and lo) in the same space: the next
-    // tile is fetched only after that middle step has consumed it
-    float *mid_hi = stg;
-    float *mid_lo = stg + Np * kRows;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(stg + std::max(NSTG * stg_len, DOUBLE ? 2 * Np * kRows : 0));
+    const int buf_len = max(NSTG * stg_len, DOUBLE ? 2 * Np * kRows : 0);
+    float *stg0 = reinterpret_cast<float *>(sA + a_piece * S);
+    float *maxbuf = stg0 + NBUF * buf_len;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(maxbuf + NT);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
     int *sflag = reinterpret_cast<int *>(tslot + 1);
     const float *cs1 = reinterpret_cast<const float *>(sB1 + SB * b_piece);
     const float *cs2 = reinterpret_cast<const float *>(sB2 + SB * b_piece);
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, row = tid & (kRows - 1), q = tid / kRows;
     const int ncols = NACC * Np <= 32 ? 32 : NACC * Np <= 64 ? 64 : NACC * Np <= 128 ? 128 : NACC * Np <= 256 ? 256 : 512;
+    const int nchunk = Kp / EPC;
 
-    // operand images of the contraction matrices, copied once per CTA
-    for (uint32_t i = tid * 16; i < a.img_bytes; i += kRows * 16) {
+    for (uint32_t i = tid * 16; i < a.img_bytes; i += NT * 16) {
         *reinterpret_cast<uint4 *>(sB1 + i) = *reinterpret_cast<const uint4 *>(a.B1 + i);
         if (DOUBLE) *reinterpret_cast<uint4 *>(sB2 + i) = *reinterpret_cast<const uint4 *>(a.B2 + i);
     }
-    for (int i = tid; i < NSTG * stg_len; i += kRows) stg[i] = 0.f;
+    for (int i = tid; i < NBUF * buf_len; i += NT) stg0[i] = 0.f;   // padding k >= K stays zero
     if (tid == 0) {
         tc::mbar_init(bar, 1);
         *sflag = 0;
@@ -301,7 +290,7 @@ __global__ void __launch_bounds__(kRows, 1) tc_pass_kernel(TcPassArgs a)
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tslot;
-    const uint32_t dacc = tmem + (uint32_t(warp * 32) << 16);   // this warp's lanes
+    const uint32_t dacc = tmem + (uint32_t((warp & 3) * 32) << 16);   // this warp's lane quarter
     const uint32_t idesc = tc::instr_desc(MODE == MODE_FLOAT_TF32, Np);
     const int ksteps = Kp * ES / 32;
     const uint32_t sA_addr = tc::smem_addr(sA), sB1_addr = tc::smem_addr(sB1), sB2_addr = tc::smem_addr(sB2);
@@ -310,126 +299,170 @@ __global__ void __launch_bounds__(kRows, 1) tc_pass_kernel(TcPassArgs a)
     const long rows = long(a.nfields) * a.R;
     const long ntiles = (rows + kRows - 1) / kRows;
     const bool vec16 = ((a.K & 3) == 0) && ((a.N & 3) == 0) && ((a.lo_off & 3) == 0);
-    // Issue the copies of this thread's row of tile t into the staging (rows past the
-    // end are skipped; the conversion treats them as zero).
-    auto prefetch = [&](long t) {
-        if (t >= ntiles) return;
-        const long gg = t * kRows + tid;
-        if (gg >= rows) return;
+    // Copy this thread's chunks of its row of tile t into staging buffer `stg` (rows past
+    // the end are skipped; the conversion treats them as zero).  Exactly one copy group is
+    // committed per call, empty or not, so that wait_group counts tiles.
+    auto prefetch = [&](long t, float *stg) {
+        const long gg = t * kRows + row;
+        if (t >= ntiles || gg >= rows) {
+            tc::cp_async_commit();
+            return;
+        }
         const int pp = int(gg / a.R), rr = int(gg - long(pp) * a.R);
         if (LOAD == LOAD_PAIR) {
             const int2 mn = a.pairs[pp];
             const float *src[4] = {a.psi_hi + size_t(a.occ_off + mn.x) * a.N, a.psi_lo + size_t(a.occ_off + mn.x) * a.N,
                                    a.psi_hi + size_t(mn.y) * a.N, a.psi_lo + size_t(mn.y) * a.N};
-            for (int k = 0; k < a.K; ++k)
+            for (int c = q; c < nchunk; c += TPR)
+                for (int k = c * EPC; k < min(a.K, (c + 1) * EPC); ++k)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) tc::cp_async4(stg + q * stg_len + k * kRows + tid, src[q] + size_t(k) * a.R + rr);
+                    for (int w = 0; w < 4; ++w) tc::cp_async4(stg + w * stg_len + k * kRows + row, src[w] + size_t(k) * a.R + rr);
         } else if (LOAD == LOAD_KSLOW) {
             const float *src = a.in + size_t(pp) * a.N + rr;
-            for (int k = 0; k < a.K; ++k) {
-                tc::cp_async4(stg + k * kRows + tid, src + size_t(k) * a.R);
-                if (HL) tc::cp_async4(stg + stg_len + k * kRows + tid, src + a.lo_off + size_t(k) * a.R);
-            }
+            for (int c = q; c < nchunk; c += TPR)
+                for (int k = c * EPC; k < min(a.K, (c + 1) * EPC); ++k) {
+                    tc::cp_async4(stg + k * kRows + row, src + size_t(k) * a.R);
+                    if (HL) tc::cp_async4(stg + stg_len + k * kRows + row, src + a.lo_off + size_t(k) * a.R);
+                }
         } else {
             const float *src = a.in + size_t(pp) * a.N + size_t(rr) * a.K;
-            float *dh = stg + tid * (Kp + 4);
-            if (vec16) {
-                for (int k = 0; k < a.K; k += 4) {
-                    tc::cp_async16(dh + k, src + k);
-                    if (HL) tc::cp_async16(dh + stg_len + k, src + a.lo_off + k);
-                }
-            } else {
-                for (int k = 0; k < a.K; ++k) {
-                    tc::cp_async4(dh + k, src + k);
-                    if (HL) tc::cp_async4(dh + stg_len + k, src + a.lo_off + k);
+            float *dh = stg + row * (Kp + 4);
+            for (int c = q; c < nchunk; c += TPR) {
+                const int k1 = min(a.K, (c + 1) * EPC);
+                if (vec16) {
+                    for (int k = c * EPC; k < k1; k += 4) {
+                        tc::cp_async16(dh + k, src + k);
+                        if (HL) tc::cp_async16(dh + stg_len + k, src + a.lo_off + k);
+                    }
+                } else {
+                    for (int k = c * EPC; k < k1; ++k) {
+                        tc::cp_async4(dh + k, src + k);
+                        if (HL) tc::cp_async4(dh + stg_len + k, src + a.lo_off + k);
+                    }
                 }
             }
         }
         tc::cp_async_commit();
     };
-    // Staged value (hi, lo) of element k of this thread's row.
-    auto staged = [&](int k, float &hi, float &lo) {
-        if (LOAD == LOAD_PAIR) {
-            const float ah = stg[k * kRows + tid], al = stg[stg_len + k * kRows + tid];
-            const float bh = stg[2 * stg_len + k * kRows + tid], bl = stg[3 * stg_len + k * kRows + tid];
-            hi = ah * bh;
-            lo = fmaf(ah, bh, -hi) + fmaf(ah, bl, al * bh);
-        } else if (LOAD == LOAD_KSLOW) {
-            hi = stg[k * kRows + tid];
-            lo = HL ? stg[stg_len + k * kRows + tid] : 0.f;
-        } else {
-            hi = stg[tid * (Kp + 4) + k];
-            lo = HL ? stg[stg_len + tid * (Kp + 4) + k] : 0.f;
-        }
-    };
-    prefetch(blockIdx.x);
-    for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const long g = tile * kRows + tid;
-        const bool active = g < rows;
-        const int p = active ? int(g / a.R) : 0;
-        const int r = active ? int(g - long(p) * a.R) : 0;
-        // ---- prologue: staged row -> row maximum -> pieces in SMEM ----
-        tc::cp_async_wait_all();
-        float mx = 0.f;
-        for (int k0 = 0; k0 < Kp; k0 += 4) {
+    // Staged values (hi, lo) of chunk c (EPC elements) of this thread's row.  KFAST rows are
+    // read as float4 (conflict-free with the odd (Kp + 4)/4 row pitch).
+    auto staged_chunk = [&](const float *stg, int c, float (&hi)[8], float (&lo)[8]) {
+        if (LOAD == LOAD_KFAST) {
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                float hi, lo;
-                staged(k0 + e, hi, lo);
-                mx = fmaxf(mx, fabsf(hi));
+            for (int j = 0; j < EPC; j += 4) {
+                const float4 h = *reinterpret_cast<const float4 *>(stg + row * (Kp + 4) + c * EPC + j);
+                hi[j] = h.x; hi[j + 1] = h.y; hi[j + 2] = h.z; hi[j + 3] = h.w;
+                if (HL) {
+                    const float4 l = *reinterpret_cast<const float4 *>(stg + stg_len + row * (Kp + 4) + c * EPC + j);
+                    lo[j] = l.x; lo[j + 1] = l.y; lo[j + 2] = l.z; lo[j + 3] = l.w;
+                } else {
+                    lo[j] = lo[j + 1] = lo[j + 2] = lo[j + 3] = 0.f;
+                }
+            }
+            return;
+        }
+#pragma unroll
+        for (int e = 0; e < EPC; ++e) {
+            const int k = c * EPC + e;
+            if (LOAD == LOAD_PAIR) {
+                const float ah = stg[k * kRows + row], al = stg[stg_len + k * kRows + row];
+                const float bh = stg[2 * stg_len + k * kRows + row], bl = stg[3 * stg_len + k * kRows + row];
+                hi[e] = ah * bh;
+                lo[e] = fmaf(ah, bh, -hi[e]) + fmaf(ah, bl, al * bh);
+            } else {
+                hi[e] = stg[k * kRows + row];
+                lo[e] = HL ? stg[stg_len + k * kRows + row] : 0.f;
             }
         }
-        if (!active) mx = 0.f;
-        float s_in = 1.f, rs1 = 1.f;
+    };
+    // Row maximum from the per-thread partial maxima of the TPR threads of a row.
+    auto row_max = [&](float part) {
+        maxbuf[q * kRows + row] = part;
+        __syncthreads();
+        float m = 0.f;
+#pragma unroll
+        for (int qq = 0; qq < TPR; ++qq) m = fmaxf(m, maxbuf[qq * kRows + row]);
+        return m;
+    };
+    auto scales = [&](float mx, float &s, float &rs) {
+        s = 1.f;
+        rs = 1.f;
         if (MODE == MODE_FIXED_BF16) {
             int e = 0;
             if (mx > 0.f) frexpf(mx, &e);
             e = max(e, -100);   // rows below 2^-100 are flushed to zero slices
-            s_in = ldexpf(1.f, 7 - e);
-            rs1 = ldexpf(1.f, e - 7);
+            s = ldexpf(1.f, 7 - e);
+            rs = ldexpf(1.f, e - 7);
         }
-        for (int c = 0; c < Kp / EPC; ++c) {
-            float vals[4][8];
-#pragma unroll
-            for (int e = 0; e < EPC; ++e) {
-                float hi, lo, q[4];
-                staged(c * EPC + e, hi, lo);
-                if (!active) hi = lo = 0.f;
-                if (MODE == MODE_FLOAT_TF32) split_tf32(hi, lo, q);
-                else slice_fixed<S>(hi, lo, s_in, q);
-#pragma unroll
-                for (int t = 0; t < 4; ++t) vals[t][e] = q[t];
-            }
-            store_chunk<ES, S>(sA, a_piece, tid, c, sbo, vals);
-        }
-        if (!DOUBLE) prefetch(tile + gridDim.x);   // staged row consumed: fetch the next
+    };
+    auto issue_and_wait = [&](uint32_t b_addr) {
         tc::fence_proxy_async_smem();
         tc::tc_fence_before();
         __syncthreads();
         if (tid == 0) {
             tc::tc_fence_after();
-            issue_gemm<MODE, S, SB>(tmem, Np, sA_addr, a_piece, sB1_addr, b_piece, sbo, ksteps, idesc);
+            issue_gemm<MODE, S, SB>(tmem, Np, sA_addr, a_piece, b_addr, b_piece, sbo, ksteps, idesc);
             tc::mma_commit(bar);
         }
         if (!tc::mbar_wait_bounded(bar, phase, kWaitLimit)) atomicExch(sflag, 1);
         phase ^= 1u;
         tc::tc_fence_after();
         __syncthreads();
-        if (*sflag) break;
+        return *sflag == 0;
+    };
+
+#pragma unroll
+    for (int j = 0; j < NBUF; ++j) prefetch(blockIdx.x + long(j) * gridDim.x, stg0 + j * buf_len);
+    long it = 0;
+    for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const long g = tile * kRows + row;
+        const bool active = g < rows;
+        const int p = active ? int(g / a.R) : 0;
+        const int r = active ? int(g - long(p) * a.R) : 0;
+        float *stg = stg0 + (it % NBUF) * buf_len;
+        float *mid_hi = stg;                  // pass 3: f(Lambda) D1 reuses the consumed buffer
+        float *mid_lo = stg + Np * kRows;
+        // ---- prologue: staged row -> row maximum -> pieces in SMEM ----
+        tc::cp_async_wait_group<NBUF - 1>();  // this tile's copies (one group per tile) landed
+        float mx = 0.f;
+        for (int c = q; c < nchunk; c += TPR) {
+            float hi[8], lo[8];
+            staged_chunk(stg, c, hi, lo);
+#pragma unroll
+            for (int e = 0; e < EPC; ++e) mx = fmaxf(mx, fabsf(hi[e]));
+        }
+        mx = row_max(active ? mx : 0.f);
+        float s_in, rs1;
+        scales(mx, s_in, rs1);
+        for (int c = q; c < nchunk; c += TPR) {
+            float vals[4][8], hi[8], lo[8];
+            staged_chunk(stg, c, hi, lo);
+#pragma unroll
+            for (int e = 0; e < EPC; ++e) {
+                float qv[4];
+                if (!active) hi[e] = lo[e] = 0.f;
+                if (MODE == MODE_FLOAT_TF32) split_tf32(hi[e], lo[e], qv);
+                else slice_fixed<S>(hi[e], lo[e], s_in, qv);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) vals[t][e] = qv[t];
+            }
+            store_chunk<ES, S>(sA, a_piece, row, c, sbo, vals);
+        }
+        // own chunks of this buffer consumed: fetch the tile NBUF steps ahead into it
+        if (!DOUBLE) prefetch(tile + long(NBUF) * gridDim.x, stg);
+        if (!issue_and_wait(sB1_addr)) break;
         float rs_out = rs1;
         const float *cs_out = cs1;
         if (DOUBLE) {
-            // D1 * f(Lambda) -> staging (one TMEM read) -> pieces of A (same rows, K = modes)
-            // -> second GEMM into the same TMEM columns
+            // D1 * f(Lambda) -> staging ([col][row], own columns) -> pieces of A (same rows,
+            // K = modes) -> second GEMM into the same TMEM columns
             float mx2 = 0.f;
-            for (int c0 = 0; c0 < Np; c0 += 16) {
-                float v[16], vlo[16];
-                if (HL) read_result_hl<NACC>(dacc, Np, c0, rs1, cs1, v, vlo);
-                else read_result<MODE, NACC>(dacc, Np, c0, rs1, cs1, v);
-                float fh[16], fl[16];
+            for (int cc = q; cc < Np / 8; cc += TPR) {
+                float v[8], vlo[8], fh[8], fl[8];
+                read8<MODE, NACC, HL>(dacc, Np, cc * 8, rs1, cs1, v, vlo);
 #pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                    const int col = c0 + e;
+                for (int e = 0; e < 8; ++e) {
+                    const int col = cc * 8 + e;
                     fh[e] = 0.f;
                     fl[e] = 0.f;
                     if (active && col < a.K) {
@@ -439,7 +472,7 @@ __global__ void __launch_bounds__(kRows, 1) tc_pass_kernel(TcPassArgs a)
                     }
                 }
 #pragma unroll
-                for (int e = 0; e < 16; ++e) {
+                for (int e = 0; e < 8; ++e) {
                     float x, xl = 0.f;
                     if (HL) {   // (v + vlo)(fh + fl) as x + xl
                         x = v[e] * fh[e];
@@ -448,59 +481,59 @@ __global__ void __launch_bounds__(kRows, 1) tc_pass_kernel(TcPassArgs a)
                         x = fmaf(v[e], fh[e], v[e] * fl[e]);
                     }
                     mx2 = fmaxf(mx2, fabsf(x));
-                    mid_hi[(c0 + e) * kRows + tid] = x;
-                    mid_lo[(c0 + e) * kRows + tid] = xl;
+                    mid_hi[(cc * 8 + e) * kRows + row] = x;
+                    mid_lo[(cc * 8 + e) * kRows + row] = xl;
                 }
             }
-            float s2 = 1.f, rs2 = 1.f;
-            if (MODE == MODE_FIXED_BF16) {
-                int e2 = 0;
-                if (mx2 > 0.f) frexpf(mx2, &e2);
-                e2 = max(e2, -100);
-                s2 = ldexpf(1.f, 7 - e2);
-                rs2 = ldexpf(1.f, e2 - 7);
-            }
-            for (int c = 0; c < Np / EPC; ++c) {
-                float vals[4][8];
+            mx2 = row_max(mx2);
+            float s2, rs2;
+            scales(mx2, s2, rs2);
+            for (int cc = q; cc < Np / 8; cc += TPR) {
 #pragma unroll
-                for (int e = 0; e < EPC; ++e) {
-                    const int k = c * EPC + e;
-                    float q[4];
-                    if (MODE == MODE_FLOAT_TF32) split_tf32(mid_hi[k * kRows + tid], 0.f, q);
-                    else slice_fixed<S>(mid_hi[k * kRows + tid], mid_lo[k * kRows + tid], s2, q);
+                for (int h = 0; h < 8 / EPC; ++h) {
+                    const int c = cc * (8 / EPC) + h;
+                    float vals[4][8];
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) vals[t][e] = q[t];
+                    for (int e = 0; e < EPC; ++e) {
+                        const int k = c * EPC + e;
+                        float qv[4];
+                        if (MODE == MODE_FLOAT_TF32) split_tf32(mid_hi[k * kRows + row], 0.f, qv);
+                        else slice_fixed<S>(mid_hi[k * kRows + row], mid_lo[k * kRows + row], s2, qv);
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) vals[t][e] = qv[t];
+                    }
+                    store_chunk<ES, S>(sA, a_piece, row, c, sbo, vals);
                 }
-                store_chunk<ES, S>(sA, a_piece, tid, c, sbo, vals);
             }
             tc::fence_proxy_async_smem();
             tc::tc_fence_before();
             __syncthreads();
-            // every thread is past the middle step, whose staging (laid out [col][thread])
-            // overlaps other threads' input rows: only now fetch the next tile
-            prefetch(tile + gridDim.x);
-            if (tid == 0) {
-                tc::tc_fence_after();
-                issue_gemm<MODE, S, SB>(tmem, Np, sA_addr, a_piece, sB2_addr, b_piece, sbo, ksteps, idesc);
-                tc::mma_commit(bar);
-            }
-            if (!tc::mbar_wait_bounded(bar, phase, kWaitLimit)) atomicExch(sflag, 1);
-            phase ^= 1u;
-            tc::tc_fence_after();
-            __syncthreads();
-            if (*sflag) break;
+            // every thread is past the middle step, whose staging ([col][row]) overlaps
+            // other threads' input rows: only now refill this buffer
+            prefetch(tile + long(NBUF) * gridDim.x, stg);
+            if (!issue_and_wait(sB2_addr)) break;
             rs_out = rs2;
             cs_out = cs2;
         }
-        // ---- epilogue: TMEM -> registers -> global ----
+        // ---- epilogue: TMEM -> registers -> global (own 8-column chunks) ----
         float *out = a.out + size_t(p) * a.N;
-        for (int c0 = 0; c0 < Np; c0 += 16) {
-            float v[16], vlo[16];
-            if (HL) read_result_hl<NACC>(dacc, Np, c0, rs_out, cs_out, v, vlo);
-            else read_result<MODE, NACC>(dacc, Np, c0, rs_out, cs_out, v);
-            if (active) {
+        for (int cc = q; cc < Np / 8; cc += TPR) {
+            float v[8], vlo[8];
+            read8<MODE, NACC, HL>(dacc, Np, cc * 8, rs_out, cs_out, v, vlo);
+            if (!active) continue;
+            const int c0 = cc * 8;
+            if (STORE == STORE_NFAST && vec16 && c0 + 8 <= a.K) {
+                float4 *o = reinterpret_cast<float4 *>(out + size_t(r) * a.K + c0);
+                o[0] = make_float4(v[0], v[1], v[2], v[3]);
+                o[1] = make_float4(v[4], v[5], v[6], v[7]);
+                if (HL) {
+                    float4 *ol = reinterpret_cast<float4 *>(out + a.lo_off + size_t(r) * a.K + c0);
+                    ol[0] = make_float4(vlo[0], vlo[1], vlo[2], vlo[3]);
+                    ol[1] = make_float4(vlo[4], vlo[5], vlo[6], vlo[7]);
+                }
+            } else {
 #pragma unroll
-                for (int e = 0; e < 16; ++e) {
+                for (int e = 0; e < 8; ++e) {
                     const int col = c0 + e;
                     if (col < a.K) {
                         const size_t idx = (STORE == STORE_NSLOW) ? size_t(col) * a.R + r : size_t(r) * a.K + col;
@@ -685,22 +718,26 @@ __global__ void tc_finalize_kernel(long N, int n_in, const float *acc_hi, const 
 }
 
 // ---- launch helpers -------------------------------------------------------------------
-size_t pass_smem(int prec, int Np, bool dbl, int load)
+size_t pass_smem(int prec, int Np, bool dbl, int load, int nbuf = 1)
 {
     const PrecInfo pi = prec_info(prec);
     size_t a = size_t(pi.S) * kRows * Np * pi.es;
     size_t staging = size_t(load == LOAD_PAIR ? 4 : (pi.hl ? 2 : 1)) * kRows * (Np + 4) * sizeof(float);
     if (dbl) staging = std::max(staging, size_t(2) * kRows * Np * sizeof(float));
-    return (dbl ? 2 : 1) * image_bytes(prec, Np) + a + staging + 64;
+    staging *= size_t(nbuf);                                   // staging buffers in flight
+    const size_t maxbuf = size_t(kRows) * 4 * sizeof(float);   // up to 4 threads per row
+    return (dbl ? 2 : 1) * image_bytes(prec, Np) + a + staging + maxbuf + 64;
 }
 
 int tmem_cols(int prec, int Np) { return pow2_cols(prec_info(prec).nacc * Np); }
 
-template <int MODE, int S, int SB, bool HL, int LOAD, int STORE, bool DOUBLE>
-int launch_tc_pass(Plan &P, int kind, int prec, const TcPassArgs &a, cudaStream_t s)
+constexpr int kTPR = 4;   // threads per tile row
+
+template <int MODE, int S, int SB, bool HL, int LOAD, int STORE, bool DOUBLE, int NBUF>
+int launch_tc_pass_nb(Plan &P, int kind, int prec, const TcPassArgs &a, cudaStream_t s)
 {
-    auto kern = tc_pass_kernel<MODE, S, SB, HL, LOAD, STORE, DOUBLE>;
-    size_t smem = pass_smem(prec, a.Np, DOUBLE, LOAD);
+    auto kern = tc_pass_kernel<MODE, S, SB, HL, LOAD, STORE, DOUBLE, kTPR, NBUF>;
+    size_t smem = pass_smem(prec, a.Np, DOUBLE, LOAD, NBUF);
     // TMEM: co-resident CTAs must not ask for more than 512 columns in total, so the
     // shared-memory request is raised until at most 512 / cols CTAs fit on one SM.
     const int cols = tmem_cols(prec, a.Np);
@@ -714,17 +751,26 @@ int launch_tc_pass(Plan &P, int kind, int prec, const TcPassArgs &a, cudaStream_
     }
     EXX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     int per_sm = 0;
-    EXX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRows, smem));
+    EXX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRows * kTPR, smem));
     per_sm = std::max(1, std::min(per_sm, max_ctas));
     const long rows = long(a.nfields) * a.R;
     const long ntiles = (rows + kRows - 1) / kRows;
     const int grid = int(std::min<long>(ntiles, long(P.num_sms) * per_sm));
     int tb = timing_begin(P, kind, s);
-    kern<<<grid, kRows, smem, s>>>(a);
+    kern<<<grid, kRows * kTPR, smem, s>>>(a);
     timing_end(P, tb, s);
     EXX_LAUNCH("tc_pass_kernel");
     P.launches++;
     return EXX_OK;
+}
+
+// Two staging buffers (two tiles of copies in flight) when they fit in shared memory.
+template <int MODE, int S, int SB, bool HL, int LOAD, int STORE, bool DOUBLE>
+int launch_tc_pass(Plan &P, int kind, int prec, const TcPassArgs &a, cudaStream_t s)
+{
+    if (LOAD != LOAD_PAIR && pass_smem(prec, a.Np, DOUBLE, LOAD, 2) <= 232448)
+        return launch_tc_pass_nb<MODE, S, SB, HL, LOAD, STORE, DOUBLE, 2>(P, kind, prec, a, s);
+    return launch_tc_pass_nb<MODE, S, SB, HL, LOAD, STORE, DOUBLE, 1>(P, kind, prec, a, s);
 }
 
 template <int MODE, int S, int SB, bool HL>
