@@ -179,42 +179,48 @@ __device__ __forceinline__ void issue_gemm(uint32_t d, int Np, uint32_t a_base, 
 }
 
 // Read 8 result columns [c0, c0+8) of this thread's row: combine the NACC levels (level l
-// carries weight 2^(-8 l)) and apply the row and column scales.  With HL the value is
-// returned as an unevaluated sum vh + vl: level 0 is an exact integer, the lower levels
-// are folded into t, and TwoSum keeps the rounding error of l0 + t (the scales are
-// powers of two, exact).
+// carries weight 2^(-8 l)) and apply the row and column scales.  All level loads are
+// issued before one tcgen05.wait::ld.  With HL the value is returned as an unevaluated
+// sum vh + vl: level 0 is an exact integer, the lower levels are folded into t, and
+// TwoSum keeps the rounding error of l0 + t (the scales are powers of two, exact).
 template <int MODE, int NACC, bool HL>
 __device__ __forceinline__ void read8(uint32_t d, int Np, int c0, float rs, const float *cs, float (&vh)[8],
                                       float (&vl)[8])
 {
-    if (MODE == MODE_FLOAT_TF32) {
-        tc::tmem_ld8(d + uint32_t(c0), vh);
+    uint32_t r[NACC][8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) vl[e] = 0.f;
+    for (int l = 0; l < NACC; ++l) tc::tmem_ld8_issue(d + uint32_t(l * Np + c0), r[l]);
+    tc::tmem_wait_ld();
+#pragma unroll
+    for (int l = 0; l < NACC; ++l)
+#pragma unroll
+        for (int e = 0; e < 8; ++e) tc::order_after_wait(r[l][e]);
+    if (MODE == MODE_FLOAT_TF32) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            vh[e] = __uint_as_float(r[0][e]);
+            vl[e] = 0.f;
+        }
         return;
     }
     float t[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) t[e] = 0.f;
 #pragma unroll
-    for (int l = NACC - 1; l >= 1; --l) {
-        float lv[8];
-        tc::tmem_ld8(d + uint32_t(l * Np + c0), lv);
+    for (int l = NACC - 1; l >= 1; --l)
 #pragma unroll
-        for (int e = 0; e < 8; ++e) t[e] = (lv[e] + t[e]) * (1.f / 256.f);
-    }
-    float l0[8];
-    tc::tmem_ld8(d + uint32_t(c0), l0);
+        for (int e = 0; e < 8; ++e) t[e] = (__uint_as_float(r[l][e]) + t[e]) * (1.f / 256.f);
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
+        const float l0 = __uint_as_float(r[0][e]);
         const float sc = rs * cs[c0 + e];
         if (HL) {
-            const float h = l0[e] + t[e];
-            const float bp = h - l0[e];
-            vl[e] = ((l0[e] - (h - bp)) + (t[e] - bp)) * sc;
+            const float h = l0 + t[e];
+            const float bp = h - l0;
+            vl[e] = ((l0 - (h - bp)) + (t[e] - bp)) * sc;
             vh[e] = h * sc;
         } else {
-            vh[e] = (l0[e] + t[e]) * sc;
+            vh[e] = (l0 + t[e]) * sc;
             vl[e] = 0.f;
         }
     }
@@ -243,46 +249,50 @@ struct TcPassArgs {
 };
 
 template <int MODE, int S, int SB, bool HL, int LOAD, int STORE, bool DOUBLE, int TPR, int NBUF>
-__global__ void __launch_bounds__(kRows * TPR, 1) tc_pass_kernel(TcPassArgs a)
+__global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     constexpr int ES = MODE == MODE_FLOAT_TF32 ? 4 : 2;
     constexpr int EPC = 16 / ES;                       // elements per 16-byte chunk
     constexpr int NACC = MODE == MODE_FLOAT_TF32 ? 1 : (SB > S ? S + 1 : S);
-    constexpr int NT = kRows * TPR;
+    constexpr int NT = kRows * TPR;          // compute threads; one more warp issues the MMAs
+    constexpr int kBarHandoff = 1, kBarCompute = 2;
     const int Np = a.Np, Kp = a.Np;
     const uint32_t sbo = uint32_t(Kp) * ES * 8;          // bytes per 8-row group
     const uint32_t a_piece = uint32_t(kRows) * Kp * ES;
     const uint32_t b_piece = uint32_t(Np) * Kp * ES;
     uint8_t *sB1 = smem;
     uint8_t *sB2 = smem + a.img_bytes;
-    uint8_t *sA = smem + (DOUBLE ? 2 : 1) * a.img_bytes;
+    // two A buffers (slices of tile t and t+1) and two TMEM accumulator sets
+    uint8_t *sA0 = smem + (DOUBLE ? 2 : 1) * a.img_bytes;
     // Input staging.  KSLOW / PAIR: [k][row] (a warp touches 32 consecutive words); KFAST:
     // [row][Kp + 4] (16-byte copies, read back conflict-free because (Kp + 4)/4 is odd).
     // PAIR stages psi_m hi, psi_m lo, psi_n hi, psi_n lo; the others hi (and lo).  Pass 3
     // stages f(Lambda) D1 ([col][row], hi and lo) in the same space after the first GEMM.
+    // NBUF staging buffers = tiles whose copies are in flight.
     constexpr int NSTG = LOAD == LOAD_PAIR ? 4 : (HL ? 2 : 1);
-    // NBUF staging buffers = tiles whose copies are in flight
     const int stg_len = kRows * (Kp + 4);
     const int buf_len = max(NSTG * stg_len, DOUBLE ? 2 * Np * kRows : 0);
-    float *stg0 = reinterpret_cast<float *>(sA + a_piece * S);
+    float *stg0 = reinterpret_cast<float *>(sA0 + 2 * a_piece * S);
     float *maxbuf = stg0 + NBUF * buf_len;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(maxbuf + NT);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
+    uint64_t *bar1 = reinterpret_cast<uint64_t *>(maxbuf + NT);   // [2]: first GEMM of each set
+    uint64_t *bar2 = bar1 + 2;                                      // [2]: second GEMM (pass 3)
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar2 + 2);
     int *sflag = reinterpret_cast<int *>(tslot + 1);
     const float *cs1 = reinterpret_cast<const float *>(sB1 + SB * b_piece);
     const float *cs2 = reinterpret_cast<const float *>(sB2 + SB * b_piece);
     const int tid = threadIdx.x, warp = tid >> 5, row = tid & (kRows - 1), q = tid / kRows;
-    const int ncols = NACC * Np <= 32 ? 32 : NACC * Np <= 64 ? 64 : NACC * Np <= 128 ? 128 : NACC * Np <= 256 ? 256 : 512;
+    const int set_cols = NACC * Np;
+    const int ncols = 2 * set_cols <= 32 ? 32 : 2 * set_cols <= 64 ? 64 : 2 * set_cols <= 128 ? 128 : 2 * set_cols <= 256 ? 256 : 512;
     const int nchunk = Kp / EPC;
 
-    for (uint32_t i = tid * 16; i < a.img_bytes; i += NT * 16) {
+    for (uint32_t i = tid * 16; i < a.img_bytes; i += (NT + 32) * 16) {
         *reinterpret_cast<uint4 *>(sB1 + i) = *reinterpret_cast<const uint4 *>(a.B1 + i);
         if (DOUBLE) *reinterpret_cast<uint4 *>(sB2 + i) = *reinterpret_cast<const uint4 *>(a.B2 + i);
     }
-    for (int i = tid; i < NBUF * buf_len; i += NT) stg0[i] = 0.f;   // padding k >= K stays zero
+    for (int i = tid; i < NBUF * buf_len; i += NT + 32) stg0[i] = 0.f;   // padding k >= K stays zero
     if (tid == 0) {
-        tc::mbar_init(bar, 1);
+        for (int i = 0; i < 4; ++i) tc::mbar_init(bar1 + i, 1);
         *sflag = 0;
     }
     if (warp == 0) tc::tmem_alloc(tslot, ncols);
@@ -290,11 +300,13 @@ __global__ void __launch_bounds__(kRows * TPR, 1) tc_pass_kernel(TcPassArgs a)
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tslot;
-    const uint32_t dacc = tmem + (uint32_t((warp & 3) * 32) << 16);   // this warp's lane quarter
+    const uint32_t lane_q = uint32_t((warp & 3) * 32) << 16;   // this warp's TMEM lane quarter
     const uint32_t idesc = tc::instr_desc(MODE == MODE_FLOAT_TF32, Np);
     const int ksteps = Kp * ES / 32;
-    const uint32_t sA_addr = tc::smem_addr(sA), sB1_addr = tc::smem_addr(sB1), sB2_addr = tc::smem_addr(sB2);
-    uint32_t phase = 0;
+    const uint32_t sB1_addr = tc::smem_addr(sB1), sB2_addr = tc::smem_addr(sB2);
+    uint32_t ph1 = 0u, ph2 = 0u;   // bit st = phase parity of bar1[st] / bar2[st]
+    auto set_tmem = [&](int st) { return tmem + uint32_t(st * set_cols); };
+    auto set_A = [&](int st) { return sA0 + st * S * a_piece; };
 
     const long rows = long(a.nfields) * a.R;
     const long ntiles = (rows + kRows - 1) / kRows;
@@ -378,51 +390,115 @@ __global__ void __launch_bounds__(kRows * TPR, 1) tc_pass_kernel(TcPassArgs a)
     // Row maximum from the per-thread partial maxima of the TPR threads of a row.
     auto row_max = [&](float part) {
         maxbuf[q * kRows + row] = part;
-        __syncthreads();
+        tc::bar_sync(kBarCompute, NT);
         float m = 0.f;
 #pragma unroll
         for (int qq = 0; qq < TPR; ++qq) m = fmaxf(m, maxbuf[qq * kRows + row]);
         return m;
     };
-    auto scales = [&](float mx, float &s, float &rs) {
-        s = 1.f;
+    auto scales = [&](float mx, float &sc, float &rs) {
+        sc = 1.f;
         rs = 1.f;
         if (MODE == MODE_FIXED_BF16) {
             int e = 0;
             if (mx > 0.f) frexpf(mx, &e);
             e = max(e, -100);   // rows below 2^-100 are flushed to zero slices
-            s = ldexpf(1.f, 7 - e);
+            sc = ldexpf(1.f, 7 - e);
             rs = ldexpf(1.f, e - 7);
         }
     };
-    auto issue_and_wait = [&](uint32_t b_addr) {
+    // Compute threads: publish the A slices written so far to the tensor core and hand
+    // them to the MMA warp (which issues A[st] x B into TMEM set st).  Returns true when
+    // any thread has recorded an error, uniformly on both sides of the hand-off.
+    auto handoff = [&]() {
         tc::fence_proxy_async_smem();
         tc::tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
-            tc::tc_fence_after();
-            issue_gemm<MODE, S, SB>(tmem, Np, sA_addr, a_piece, b_addr, b_piece, sbo, ksteps, idesc);
-            tc::mma_commit(bar);
-        }
-        if (!tc::mbar_wait_bounded(bar, phase, kWaitLimit)) atomicExch(sflag, 1);
-        phase ^= 1u;
-        tc::tc_fence_after();
-        __syncthreads();
-        return *sflag == 0;
+        return tc::bar_red_or(kBarHandoff, NT + 32, *sflag != 0);
     };
 
+    if (tid >= NT) {
+        // ---- MMA warp: one hand-off per GEMM, in the compute threads' order ----
+        long it = 0;
+        for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+            const int st = int(it & 1);
+            if (tc::bar_red_or(kBarHandoff, NT + 32, *sflag != 0)) break;
+            if (tid == NT) {
+                tc::tc_fence_after();
+                issue_gemm<MODE, S, SB>(set_tmem(st), Np, tc::smem_addr(set_A(st)), a_piece, sB1_addr, b_piece, sbo,
+                                        ksteps, idesc);
+                tc::mma_commit(bar1 + st);
+            }
+            if (DOUBLE) {
+                if (tc::bar_red_or(kBarHandoff, NT + 32, *sflag != 0)) break;
+                if (tid == NT) {
+                    tc::tc_fence_after();
+                    issue_gemm<MODE, S, SB>(set_tmem(st), Np, tc::smem_addr(set_A(st)), a_piece, sB2_addr, b_piece, sbo,
+                                            ksteps, idesc);
+                    tc::mma_commit(bar2 + st);
+                }
+            }
+        }
+    } else {
+    auto wait_bar = [&](uint64_t *bar, uint32_t &ph, int st) {
+        if (!tc::mbar_wait_bounded(bar, (ph >> st) & 1u, kWaitLimit)) atomicExch(sflag, 1);
+        ph ^= 1u << st;
+        tc::tc_fence_after();
+    };
+    // Epilogue of tile t from TMEM set st: own 8-column chunks -> global.
+    auto epilogue = [&](long t, int st, float rs_out, const float *cs_out) {
+        const long gg = t * kRows + row;
+        const bool act = gg < rows;
+        const int pp = act ? int(gg / a.R) : 0;
+        const int rr = act ? int(gg - long(pp) * a.R) : 0;
+        float *out = a.out + size_t(pp) * a.N;
+        for (int cc = q; cc < Np / 8; cc += TPR) {
+            float v[8], vlo[8];
+            read8<MODE, NACC, HL>(set_tmem(st) + lane_q, Np, cc * 8, rs_out, cs_out, v, vlo);
+            if (!act) continue;
+            const int c0 = cc * 8;
+            if (STORE == STORE_NFAST && vec16 && c0 + 8 <= a.K) {
+                float4 *o = reinterpret_cast<float4 *>(out + size_t(rr) * a.K + c0);
+                o[0] = make_float4(v[0], v[1], v[2], v[3]);
+                o[1] = make_float4(v[4], v[5], v[6], v[7]);
+                if (HL) {
+                    float4 *ol = reinterpret_cast<float4 *>(out + a.lo_off + size_t(rr) * a.K + c0);
+                    ol[0] = make_float4(vlo[0], vlo[1], vlo[2], vlo[3]);
+                    ol[1] = make_float4(vlo[4], vlo[5], vlo[6], vlo[7]);
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int col = c0 + e;
+                    if (col < a.K) {
+                        const size_t idx = (STORE == STORE_NSLOW) ? size_t(col) * a.R + rr : size_t(rr) * a.K + col;
+                        out[idx] = v[e];
+                        if (HL) out[a.lo_off + idx] = vlo[e];
+                    }
+                }
+            }
+        }
+        tc::tc_fence_before();   // these TMEM reads precede the next thread sync
+    };
+
+    // Software pipeline over this CTA's tiles: the GEMM(s) of tile t run on the tensor
+    // core while the threads finish tile t-1 (epilogue) and slice tile t+1.
 #pragma unroll
     for (int j = 0; j < NBUF; ++j) prefetch(blockIdx.x + long(j) * gridDim.x, stg0 + j * buf_len);
+    long prev_tile = -1;
+    int prev_set = 0;
+    float prev_rs = 1.f;
+    const float *prev_cs = cs1;
     long it = 0;
     for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int st = int(it & 1);
         const long g = tile * kRows + row;
         const bool active = g < rows;
         const int p = active ? int(g / a.R) : 0;
         const int r = active ? int(g - long(p) * a.R) : 0;
         float *stg = stg0 + (it % NBUF) * buf_len;
-        float *mid_hi = stg;                  // pass 3: f(Lambda) D1 reuses the consumed buffer
-        float *mid_lo = stg + Np * kRows;
-        // ---- prologue: staged row -> row maximum -> pieces in SMEM ----
+        uint8_t *sA = set_A(st);
+        // ---- slice tile -> A[st] (A[st] was last read by the GEMMs of tile it-2,
+        //      which completed before that tile's epilogue) ----
         tc::cp_async_wait_group<NBUF - 1>();  // this tile's copies (one group per tile) landed
         float mx = 0.f;
         for (int c = q; c < nchunk; c += TPR) {
@@ -444,22 +520,32 @@ __global__ void __launch_bounds__(kRows * TPR, 1) tc_pass_kernel(TcPassArgs a)
                 if (MODE == MODE_FLOAT_TF32) split_tf32(hi[e], lo[e], qv);
                 else slice_fixed<S>(hi[e], lo[e], s_in, qv);
 #pragma unroll
-                for (int t = 0; t < 4; ++t) vals[t][e] = qv[t];
+                for (int t2 = 0; t2 < 4; ++t2) vals[t2][e] = qv[t2];
             }
             store_chunk<ES, S>(sA, a_piece, row, c, sbo, vals);
         }
-        // own chunks of this buffer consumed: fetch the tile NBUF steps ahead into it
+        // own chunks of this staging buffer consumed: fetch the tile NBUF steps ahead
         if (!DOUBLE) prefetch(tile + long(NBUF) * gridDim.x, stg);
-        if (!issue_and_wait(sB1_addr)) break;
+        // ---- first GEMM of this tile; TMEM set st was last read by the epilogue of
+        //      tile it-2, which every thread finished before this hand-off ----
+        if (handoff()) break;
+        // ---- epilogue of the previous tile, overlapping this tile's GEMM ----
+        if (prev_tile >= 0) {
+            if (DOUBLE) wait_bar(bar2 + prev_set, ph2, prev_set);
+            else wait_bar(bar1 + prev_set, ph1, prev_set);
+            epilogue(prev_tile, prev_set, prev_rs, prev_cs);
+        }
         float rs_out = rs1;
         const float *cs_out = cs1;
         if (DOUBLE) {
-            // D1 * f(Lambda) -> staging ([col][row], own columns) -> pieces of A (same rows,
-            // K = modes) -> second GEMM into the same TMEM columns
+            // D1 * f(Lambda) -> staging ([col][row], own columns) -> A[st] (its first GEMM
+            // is complete) -> second GEMM into the same TMEM set
+            wait_bar(bar1 + st, ph1, st);
+            float *mid_hi = stg, *mid_lo = stg + Np * kRows;
             float mx2 = 0.f;
             for (int cc = q; cc < Np / 8; cc += TPR) {
                 float v[8], vlo[8], fh[8], fl[8];
-                read8<MODE, NACC, HL>(dacc, Np, cc * 8, rs1, cs1, v, vlo);
+                read8<MODE, NACC, HL>(set_tmem(st) + lane_q, Np, cc * 8, rs1, cs1, v, vlo);
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     const int col = cc * 8 + e;
@@ -485,7 +571,8 @@ __global__ void __launch_bounds__(kRows * TPR, 1) tc_pass_kernel(TcPassArgs a)
                     mid_lo[(cc * 8 + e) * kRows + row] = xl;
                 }
             }
-            mx2 = row_max(mx2);
+            tc::tc_fence_before();
+            mx2 = row_max(mx2);   // (its sync also orders these TMEM reads before GEMM 2)
             float s2, rs2;
             scales(mx2, s2, rs2);
             for (int cc = q; cc < Np / 8; cc += TPR) {
@@ -500,53 +587,31 @@ __global__ void __launch_bounds__(kRows * TPR, 1) tc_pass_kernel(TcPassArgs a)
                         if (MODE == MODE_FLOAT_TF32) split_tf32(mid_hi[k * kRows + row], 0.f, qv);
                         else slice_fixed<S>(mid_hi[k * kRows + row], mid_lo[k * kRows + row], s2, qv);
 #pragma unroll
-                        for (int t = 0; t < 4; ++t) vals[t][e] = qv[t];
+                        for (int t2 = 0; t2 < 4; ++t2) vals[t2][e] = qv[t2];
                     }
                     store_chunk<ES, S>(sA, a_piece, row, c, sbo, vals);
                 }
             }
-            tc::fence_proxy_async_smem();
-            tc::tc_fence_before();
-            __syncthreads();
+            const bool stop = handoff();
             // every thread is past the middle step, whose staging ([col][row]) overlaps
             // other threads' input rows: only now refill this buffer
-            prefetch(tile + long(NBUF) * gridDim.x, stg);
-            if (!issue_and_wait(sB2_addr)) break;
+            if (!stop) prefetch(tile + long(NBUF) * gridDim.x, stg);
+            if (stop) break;
             rs_out = rs2;
             cs_out = cs2;
         }
-        // ---- epilogue: TMEM -> registers -> global (own 8-column chunks) ----
-        float *out = a.out + size_t(p) * a.N;
-        for (int cc = q; cc < Np / 8; cc += TPR) {
-            float v[8], vlo[8];
-            read8<MODE, NACC, HL>(dacc, Np, cc * 8, rs_out, cs_out, v, vlo);
-            if (!active) continue;
-            const int c0 = cc * 8;
-            if (STORE == STORE_NFAST && vec16 && c0 + 8 <= a.K) {
-                float4 *o = reinterpret_cast<float4 *>(out + size_t(r) * a.K + c0);
-                o[0] = make_float4(v[0], v[1], v[2], v[3]);
-                o[1] = make_float4(v[4], v[5], v[6], v[7]);
-                if (HL) {
-                    float4 *ol = reinterpret_cast<float4 *>(out + a.lo_off + size_t(r) * a.K + c0);
-                    ol[0] = make_float4(vlo[0], vlo[1], vlo[2], vlo[3]);
-                    ol[1] = make_float4(vlo[4], vlo[5], vlo[6], vlo[7]);
-                }
-            } else {
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int col = c0 + e;
-                    if (col < a.K) {
-                        const size_t idx = (STORE == STORE_NSLOW) ? size_t(col) * a.R + r : size_t(r) * a.K + col;
-                        out[idx] = v[e];
-                        if (HL) out[a.lo_off + idx] = vlo[e];
-                    }
-                }
-            }
-        }
-        tc::tc_fence_before();
-        __syncthreads();   // TMEM reads done before the next tile's MMA overwrites it
+        prev_tile = tile;
+        prev_set = st;
+        prev_rs = rs_out;
+        prev_cs = cs_out;
+    }
+    if (prev_tile >= 0 && *sflag == 0) {
+        if (DOUBLE) wait_bar(bar2 + prev_set, ph2, prev_set);
+        else wait_bar(bar1 + prev_set, ph1, prev_set);
+        epilogue(prev_tile, prev_set, prev_rs, prev_cs);
     }
     tc::cp_async_wait_all();   // no copy may still target shared memory at exit
+    }   // compute threads
     if (tid == 0 && *sflag) atomicExch(a.err, 1);
     tc::tc_fence_before();
     __syncthreads();
@@ -721,7 +786,7 @@ __global__ void tc_finalize_kernel(long N, int n_in, const float *acc_hi, const 
 size_t pass_smem(int prec, int Np, bool dbl, int load, int nbuf = 1)
 {
     const PrecInfo pi = prec_info(prec);
-    size_t a = size_t(pi.S) * kRows * Np * pi.es;
+    size_t a = 2 * size_t(pi.S) * kRows * Np * pi.es;   // two A buffers
     size_t staging = size_t(load == LOAD_PAIR ? 4 : (pi.hl ? 2 : 1)) * kRows * (Np + 4) * sizeof(float);
     if (dbl) staging = std::max(staging, size_t(2) * kRows * Np * sizeof(float));
     staging *= size_t(nbuf);                                   // staging buffers in flight
@@ -729,7 +794,7 @@ size_t pass_smem(int prec, int Np, bool dbl, int load, int nbuf = 1)
     return (dbl ? 2 : 1) * image_bytes(prec, Np) + a + staging + maxbuf + 64;
 }
 
-int tmem_cols(int prec, int Np) { return pow2_cols(prec_info(prec).nacc * Np); }
+int tmem_cols(int prec, int Np) { return pow2_cols(2 * prec_info(prec).nacc * Np); }   // two sets
 
 constexpr int kTPR = 4;   // threads per tile row
 
@@ -751,13 +816,13 @@ int launch_tc_pass_nb(Plan &P, int kind, int prec, const TcPassArgs &a, cudaStre
     }
     EXX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     int per_sm = 0;
-    EXX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRows * kTPR, smem));
+    EXX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRows * kTPR + 32, smem));
     per_sm = std::max(1, std::min(per_sm, max_ctas));
     const long rows = long(a.nfields) * a.R;
     const long ntiles = (rows + kRows - 1) / kRows;
     const int grid = int(std::min<long>(ntiles, long(P.num_sms) * per_sm));
     int tb = timing_begin(P, kind, s);
-    kern<<<grid, kRows * kTPR, smem, s>>>(a);
+    kern<<<grid, kRows * kTPR + 32, smem, s>>>(a);
     timing_end(P, tb, s);
     EXX_LAUNCH("tc_pass_kernel");
     P.launches++;

@@ -134,6 +134,37 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// tcgen05.ld without the wait: the registers are valid only after tmem_wait_ld(), and
+// every use must be ordered after it with order_after_wait().
+__device__ __forceinline__ void tmem_ld8_issue(uint32_t taddr, uint32_t (&r)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// An empty volatile asm that reads and writes r: volatile asm statements keep their order,
+// so uses of r cannot move above the preceding tcgen05.wait::ld.
+__device__ __forceinline__ void order_after_wait(uint32_t &r) { asm volatile("" : "+r"(r)); }
+
+// Named barriers (barrier 0 is __syncthreads): `count` threads, a multiple of 32.
+__device__ __forceinline__ void bar_sync(int id, int count)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+// Barrier that also returns the OR of every participating thread's flag.
+__device__ __forceinline__ bool bar_red_or(int id, int count, bool flag)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\t"
+        "bar.red.or.pred po, %2, %3, pi;\n\tselp.u32 %0, 1, 0, po;\n\t}"
+        : "=r"(r)
+        : "r"(uint32_t(flag)), "r"(id), "r"(count)
+        : "memory");
+    return r != 0;
+}
+
 // Asynchronous global -> shared copies (the copying thread waits for its own copies).
 __device__ __forceinline__ void cp_async4(void *dst_smem, const void *src)
 {
