@@ -291,38 +291,60 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# bytes per grid element a pass must read and write (its input and output planes); pass 1
+# reads the FP32 hi/lo planes of both orbitals, pass 3 also reads f(Lambda) (hi/lo) once
+# per launch.  BF16X10 keeps hi+lo intermediates (8 B), the other split modes FP32 (4 B).
+def pass_bytes(prec, kind):
+    inter = 8 if prec in ("bf16x10", "fp64") else 4
+    if prec == "fp64":
+        return {"pass1": 16 + 8, "pass2": 16, "pass3": 32, "pass4": 16, "pass5": 16}[kind]
+    return {"pass1": 16 + inter, "pass2": 2 * inter, "pass3": 2 * inter, "pass4": 2 * inter, "pass5": 2 * inter}[kind]
+
+
 def roofline(exx, plan, s, prec, kind, ms, nlaunch, K, peaks, clk):
     """Achieved throughput of the dominant kernel class from its live CUDA-event time."""
     n = s.n
     N = s.N
     unique = s.unique_pairs()
-    per_step = {}
-    # algorithmic flops of the mode products: 2 N n_d per field per contraction
+    fields_per_launch = unique * K / max(1, nlaunch) * (2 if (prec == "fp64" and kind == "pass3") else 1)
     axis_K = {"pass1": n[2], "pass2": n[0], "pass3": n[1], "pass4": n[0], "pass5": n[2]}
-    if kind in axis_K:
+    avg_s = ms / max(1, nlaunch) / 1e3
+    out = {}
+    if kind in axis_K and prec == "fp64":
+        contractions = 1   # FP64 pass 3 is two launches, one contraction each
+        flops = 2.0 * N * axis_K[kind] * contractions * fields_per_launch
+        achieved = flops / avg_s / 1e12
+        peak = 152 * 2 * 2 * 2.07e9 / 1e12
+        out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+               "kernel": f"fp64_pass_kernel ({kind})",
+               "peak_source": FP64_PEAK_NOTE + " (derived from unit counts and clock, not measured)",
+               "algorithmic_flops_per_launch": flops}
+    elif kind in axis_K:
+        byt = pass_bytes(prec, kind) * N * fields_per_launch + (8 * N if kind == "pass3" else 0)
+        achieved = byt / avg_s / 1e9
+        pk = peaks.get("hbm_gbs", 6800.0)
         contractions = 2 if kind == "pass3" else 1
-        flops = 2.0 * N * axis_K[kind] * contractions * unique * K
-        achieved = flops / (ms / 1e3) / 1e12
-        if prec == "fp64":
-            peak = 152 * 2 * 2 * 2.07e9 / 1e12
-            out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                   "frac": achieved / peak, "kernel": f"fp64_pass_kernel ({kind})",
-                   "peak_source": FP64_PEAK_NOTE + " (derived, not measured)"}
-        else:
-            pk = peaks.get("bf16_tflops_sustained", 1700.0)
-            out = {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
-                   "frac": achieved / pk, "kernel": f"tc_pass_kernel ({kind})",
-                   "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"}
-    elif kind == "accum":
-        bytes_ = 0.0
-        out = {"bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s", "frac": None,
-               "kernel": "accumulate"}
+        nprod = {"bf16x10": 10, "bf16x6": 7, "bf16x3": 3, "tf32x3": 3}.get(prec, 1)
+        flops = 2.0 * N * axis_K[kind] * contractions * fields_per_launch
+        out = {"bound": "hbm", "achieved": achieved, "peak": pk, "unit": "GB/s", "frac": achieved / pk,
+               "kernel": f"tc_pass_kernel ({kind})",
+               "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback 6800 GB/s",
+               "algorithmic_bytes_per_launch": byt,
+               "fields_per_launch": fields_per_launch,
+               "algorithmic_tflops": flops / avg_s / 1e12,
+               "tensor_executed_tflops": nprod * flops / avg_s / 1e12,
+               "tensor_executed_frac_of_bf16": nprod * flops / avg_s / 1e12 / peaks.get("bf16_tflops_sustained", 1751.7)}
     else:
         out = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None, "kernel": kind}
     out["launches"] = nlaunch
     out["avg_launch_ms"] = ms / max(1, nlaunch)
-    tr = traffic_for(out["kernel"].split(" ")[0] + ":" + kind)
-    out["traffic"] = tr["bytes_per_launch"] if tr else None
+    tr = traffic_for(out["kernel"].split(" ")[0] + ":" + kind + ":" + prec)
+    if tr:
+        # DRAM bytes per launch from the committed ncu capture, scaled to this launch size
+        out["traffic"] = tr["bytes_per_field"] * fields_per_launch
+        out["traffic_source"] = tr["source"]
+    else:
+        out["traffic"] = None
     return out
 
 
