@@ -12,6 +12,10 @@ one orbital pair, Sec. II.B) and the exx_apply time.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                        [--prec auto|fp64|bf16x3|tf32x3|bf16x6|bf16x10]
+                       [--workload periodic48|batch48]
+--workload batch48 times instead 48 independent systems (grids of 20-64 points per
+axis, 8-160 orbitals) solved by one exx_apply_batched call (one CUDA graph) per step,
+beside the same work issued as one exx_apply call per system.
 For N > 1 launch with torchrun; every rank runs an independent replica (the pair
 solves shard with no exchange), so the whole-job value is the sum over ranks.
 """
@@ -35,6 +39,10 @@ UNIT = "pair-Poisson solves/s"
 WORKLOAD = ("periodic48_erfc_128: 48x48x48 periodic grid, h=0.25, 12th-order FD, erfc kernel "
             "omega=0.106, 128 orbitals, Fermi-Dirac occupations; step = exx_apply + exx_energy + ace_build")
 L2_FLUSH_BYTES = 512 << 20
+BATCH_WORKLOAD = ("batch48: 48 independent systems, seeded grid draws of 20-64 points per axis, "
+                  "mixed Dirichlet/periodic axes, h=0.3, 12th-order FD, Coulomb kernel with any Dirichlet "
+                  "axis else erfc omega=0.106, 8-160 orbitals with Fermi-Dirac occupations; "
+                  "step = exx_apply of every system in one exx_apply_batched call")
 FP64_PEAK_NOTE = "FP64 CUDA-core peak: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"
 
 
@@ -50,6 +58,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n-orb", type=int, default=128)
     ap.add_argument("--batch", type=int, default=0, help="pairs per batch (0 = library default)")
+    ap.add_argument("--workload", default="periodic48", choices=["periodic48", "batch48"])
     return ap.parse_args()
 
 
@@ -291,6 +300,168 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batch48(args):
+    """Many small systems: one graph-captured exx_apply_batched call per step against
+    one exx_apply call per system, same stream, same buffers."""
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    import paper_2501_16572_gb300 as exx
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    specs = synth.config4_specs()
+    mine = [i for i in range(len(specs)) if i % world == rank]   # systems shard over ranks
+    systems = [synth.config4_system(i, specs) for i in mine]
+    prec_name = args.prec if args.prec != "auto" else "bf16x10"
+    plans, bufs = [], []
+    for s in systems:
+        p = exx.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+        p.set_precision(prec_code(exx, prec_name))
+        plans.append(p)
+        psi = torch.from_numpy(s.psi).to(dev)
+        bufs.append((psi, torch.from_numpy(s.f).to(dev), torch.empty_like(psi)))
+    bargs = [(psi[:s.n_occ], f, psi, out) for (psi, f, out), s in zip(bufs, systems)]
+    unique = sum(s.unique_pairs() for s in systems)
+    side = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def graph_step():
+        exx.exx_apply_batched(plans, bargs, stream=side)
+
+    def loop_step():
+        for p, (po, f, pi, out) in zip(plans, bargs):
+            p.apply(po, f, pi, out=out, stream=side)
+
+    def launches():
+        return sum(p.launch_count() for p in plans)
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ms, nl = [], 0
+        for _ in range(steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(side)
+            fn()
+            e1.record(side)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            nl += launches()
+        tot = torch.tensor([sum(ms)], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+        return tot.item(), nl
+
+    K = args.steps
+    clocks = Clocks(local)
+    clocks.start()
+    t_graph, nl_graph = timed(graph_step, K, args.warmup)
+    clk = clocks.stop()
+    t_loop, _ = timed(loop_step, K, args.warmup)
+    ref = [out.clone() for (_, _, out) in bufs]
+    graph_step()
+    torch.cuda.synchronize()
+    identical = all(torch.equal(r, out) for r, (_, _, out) in zip(ref, bufs))
+    # whole job: every rank's systems over the slowest rank's time
+    u = torch.tensor([float(unique)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(u)
+    value = u.item() * K / (t_graph / 1e3)
+    rec = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": t_graph / K, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+        "dtype": prec_name, "data": "synthetic (seeded Gaussian + plane-wave orbitals, orthonormalised)",
+        "config": {"workload": BATCH_WORKLOAD, "systems": len(specs), "systems_this_rank": len(systems),
+                   "unique_pair_solves_per_step": int(u.item()), "precision": prec_name,
+                   "l2": "flushed between timed steps (512 MB write, untimed)",
+                   "parallelism": f"systems sharded over {world} rank(s)"},
+        "gpu_launches": nl_graph,
+        "per_system_loop": {"ms_per_step": t_loop / K, "value": u.item() * K / (t_loop / 1e3)},
+        "graph_vs_loop_speedup": t_loop / t_graph,
+        "graph_equals_loop_bitwise": identical,
+        "clocks": clk,
+    }
+    # per-kernel times: one more step with CUDA events around every launch (timing issues
+    # the launches one by one instead of through the graph)
+    for p in plans:
+        p.set_timing(True)
+    graph_step()
+    torch.cuda.synchronize()
+    per_kind, bytes_kind = {}, {}
+    for p, s in zip(plans, systems):
+        for kind, (ms, n) in p.timing().items():
+            a = per_kind.setdefault(kind, [0.0, 0])
+            a[0] += ms
+            a[1] += n
+            if kind.startswith("pass") and prec_name != "fp64":
+                b = pass_bytes(prec_name, kind) * s.N * s.unique_pairs() + (8 * s.N * n if kind == "pass3" else 0)
+                bytes_kind[kind] = bytes_kind.get(kind, 0.0) + b
+        p.set_timing(False)
+    rec["kernel_times_ms"] = {k: round(v[0], 4) for k, v in per_kind.items()}
+    dom = max(per_kind, key=lambda k: per_kind[k][0])
+    peaks = measured_peaks()
+    if dom in bytes_kind:
+        ms, n = per_kind[dom]
+        achieved = bytes_kind[dom] / (ms / 1e3) / 1e9
+        pk = peaks.get("hbm_gbs", 6800.0)
+        rec["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": pk, "unit": "GB/s", "frac": achieved / pk,
+                           "traffic": None, "kernel": f"tc_pass_kernel ({dom})", "launches": n,
+                           "avg_launch_ms": ms / n, "algorithmic_bytes_per_launch": bytes_kind[dom] / n,
+                           "timing": "one extra step with CUDA events around each launch (launches issued "
+                                     "one by one, not through the graph)",
+                           "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks
+                           else "fallback 6800 GB/s"}
+    # end to end: pinned host orbitals in, host VxPsi out, every step
+    if not args.no_e2e:
+        host_in = [(torch.from_numpy(s.psi.copy()).pin_memory(), torch.from_numpy(s.f.copy()).pin_memory())
+                   for s in systems]
+        host_out = [torch.empty_like(h[0]).pin_memory() for h in host_in]
+
+        def e2e_step():
+            with torch.cuda.stream(side):
+                for (ph, fh), (psi, f, _) in zip(host_in, bufs):
+                    psi.copy_(ph, non_blocking=True)
+                    f.copy_(fh, non_blocking=True)
+                graph_step()
+                for ho, (_, _, out) in zip(host_out, bufs):
+                    ho.copy_(out, non_blocking=True)
+            side.synchronize()
+
+        e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(K):
+            e2e_step()
+        dt = (time.perf_counter() - t0) / K
+        rec["e2e"] = {"value": u.item() / dt, "unit": UNIT,
+                      "ms_per_step": dt * 1e3,
+                      "h2d_bytes_per_step": int(sum(h[0].numel() * 8 + h[1].numel() * 8 for h in host_in)),
+                      "d2h_bytes_per_step": int(sum(h.numel() * 8 for h in host_out)),
+                      "entry": "exx_apply_batched with host copies of every system's Psi, f and VxPsi"}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rec["cpu_baseline"] = cpu_baseline(systems[1])
+        rec["cpu_baseline"]["sample"] += f" of system 1 ({'x'.join(map(str, systems[1].n))}, {systems[1].n_orb} orbitals)"
+    for p in plans:
+        p.close()
+    if rank == 0:
+        print(json.dumps(rec), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 # bytes per grid element a pass must read and write (its input and output planes); pass 1
 # reads the FP32 hi/lo planes of both orbitals, pass 3 also reads f(Lambda) (hi/lo) once
 # per launch.  BF16X10 keeps hi+lo intermediates (8 B), the other split modes FP32 (4 B).
@@ -423,5 +594,7 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "batch48":
+        run_batch48(a)
     else:
         run_ours(a)

@@ -142,8 +142,8 @@ int exx_energy(exx_plan plan, const double *Psi_occ, int n_occ, long ld, const d
  * The compressed operator is then -dV xi xi^T (M is negative definite, so the
  * printed "Cholesky factor of M" is read as that of -M).  Psi, W: N x n (ld, ld_w);
  * xi: N x n (ld_xi), overwritten; M_out: optional n x n column-major device buffer
- * (NULL to skip).  Cholesky and the triangular factor are FP64 in every mode; M and
- * xi use the plan's precision (FP64, or split products on the tensor cores).
+ * (NULL to skip).  Every step (M, Cholesky, triangular inverse, xi) is FP64 on the
+ * CUDA cores in every precision mode of the plan.
  * *info_h (host) is 0, or 1 + the failing pivot when EXX_ERR_NOT_POSDEF is
  * returned.  Synchronizes `stream`.  n <= 2048. */
 int ace_build(exx_plan plan, const double *Psi, int n, long ld, const double *W, long ld_w,
@@ -161,10 +161,25 @@ int exx_ace_step_host(exx_plan plan, const double *Psi_h, int n, long ld, int n_
                       const double *f_h, double *xi_h, long ld_xi, double *E_x_h, int *info_h,
                       exx_stream_t stream);
 
-/* Many independent systems (Sec. II.B's batching carried across systems): for each
- * s < nsys runs exx_apply(plans[s], args[s]...) so that all systems' pair batches go
- * through one persistent launch sequence per pass, captured in one CUDA graph on
- * first use.  Every plan must use the same precision. */
+/* Many independent systems in one call: the batching of Sec. II.B carried across
+ * systems (for instance 48 small molecules of different grids and orbital counts).
+ * For each s < nsys the result in args[s].out equals what exx_apply(plans[s],
+ * args[s]...) writes, bit for bit; args[s] has exx_apply's meaning, layout and rules.
+ *   1. Every system is checked and every device allocation is made first (this
+ *      synchronizes `stream` when a plan's pair schedule has to be rebuilt).
+ *   2. On a stream other than NULL, with timing off on every plan, the launches of
+ *      all systems are captured once into one CUDA graph (relaxed capture mode) and
+ *      kept in a library-wide cache of 8 graphs, keyed by the plans, their settings
+ *      and every pointer, size and leading dimension in args; a later call with the
+ *      same key replays the graph: one launch from the host for the whole sequence.
+ *      A replay reads whatever the pointed-to buffers hold at that time, so callers
+ *      refill the same buffers in place between calls.
+ *   3. With stream NULL, or timing on, the launches are issued one by one.
+ * Every plan must use the same precision; a plan must not be used by another call on
+ * another stream while its work is in flight.  exx_plan_destroy drops the cached
+ * graphs that use the plan.  Errors: EXX_ERR_INVALID_ARG (NULL or inconsistent
+ * arguments, with the index-free message of exx_apply), EXX_ERR_OOM, EXX_ERR_CUDA
+ * (capture, instantiation or launch failed). */
 typedef struct {
     const double *Psi_occ; int n_occ; long ld_occ; const double *f;
     const double *Psi_in; int n_in; long ld_in; double *out; long ld_out;

@@ -4,6 +4,7 @@
 #include "exx_internal.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -28,6 +29,10 @@ static int invalid(const char *msg)
     set_error(msg);
     return EXX_ERR_INVALID_ARG;
 }
+
+static std::atomic<uint64_t> g_epoch{0};
+void bump_epoch(Plan &P) { P.epoch = ++g_epoch; }
+static void graph_evict_plan(const Plan *P);
 
 int dev_reserve(DevBuf &b, size_t bytes)
 {
@@ -92,6 +97,7 @@ static int ensure_schedule(Plan &P, int n_occ, int n_in, bool aliased, cudaStrea
     EXX_CUDA(cudaMemcpyAsync(P.blocks_d.p, P.sched.blocks.data(), P.sched.blocks.size() * sizeof(Block),
                              cudaMemcpyHostToDevice, s));
     EXX_CUDA(cudaStreamSynchronize(s));   // host vectors may be rebuilt by the next call
+    bump_epoch(P);
     std::copy(key, key + 4, P.sched_key);
     return EXX_OK;
 }
@@ -214,6 +220,7 @@ int exx_plan_create(exx_plan *out, int Nx, int Ny, int Nz, double h, const int b
         delete P;
         return rc;
     }
+    bump_epoch(*P);
     *out = reinterpret_cast<exx_plan>(P);
     return EXX_OK;
 }
@@ -228,6 +235,7 @@ int exx_plan_set_precision(exx_plan plan, int prec)
     }
     P->prec = prec;
     std::fill(P->sched_key, P->sched_key + 4, -1);
+    bump_epoch(*P);
     return EXX_OK;
 }
 
@@ -240,6 +248,7 @@ int exx_plan_set_batch(exx_plan plan, int pairs_per_batch, int block_orbitals)
     P->pairs_per_batch = pairs_per_batch;
     P->block_orbitals = block_orbitals;
     std::fill(P->sched_key, P->sched_key + 4, -1);
+    bump_epoch(*P);
     return EXX_OK;
 }
 
@@ -250,6 +259,7 @@ int exx_plan_set_shard(exx_plan plan, int rank, int world)
     if (world < 1 || rank < 0 || rank >= world) return invalid("exx_plan_set_shard: need 0 <= rank < world");
     P->shard_rank = rank;
     P->shard_world = world;
+    bump_epoch(*P);
     return EXX_OK;
 }
 
@@ -258,6 +268,7 @@ int exx_plan_destroy(exx_plan plan)
     Plan *P = as_plan(plan);
     if (!P) return EXX_OK;
     cudaDeviceSynchronize();
+    graph_evict_plan(P);
     free_plan_buffers(*P);
     timing_recycle(*P);
     for (auto e : P->timing.pool) cudaEventDestroy(e);
@@ -318,57 +329,73 @@ long exx_plan_launch_count(exx_plan plan)
     return P ? P->launches : -1;
 }
 
-int exx_apply(exx_plan plan, const double *Psi_occ, int n_occ, long ld_occ, const double *f,
-              const double *Psi_in, int n_in, long ld_in, double *out, long ld_out, exx_stream_t stream)
+}  // extern "C"
+
+namespace exx {
+
+struct ApplyCall {
+    const double *Psi_occ; int n_occ; long ld_occ; const double *f;
+    const double *Psi_in; int n_in; long ld_in; double *out; long ld_out;
+    bool aliased;
+};
+
+// Checks, schedule and every device allocation of one exx_apply (synchronizes `s` when
+// the schedule changes).  Nothing here is captured into a graph.
+static int apply_prepare(Plan *P, ApplyCall &c, cudaStream_t s)
 {
-    Plan *P = as_plan(plan);
     if (!P) return invalid("exx_apply: plan is NULL");
-    if (!Psi_occ || !f || !Psi_in || !out) return invalid("exx_apply: NULL array");
-    if (n_occ < 1 || n_in < 1 || n_occ > 65536 || n_in > 65536) return invalid("exx_apply: orbital counts must be in [1, 65536]");
-    if (ld_occ < P->N || ld_in < P->N || ld_out < P->N) return invalid("exx_apply: leading dimensions must be >= N");
-    const char *o0 = reinterpret_cast<const char *>(out);
-    const char *o1 = o0 + (size_t(n_in - 1) * ld_out + P->N) * sizeof(double);
+    if (!c.Psi_occ || !c.f || !c.Psi_in || !c.out) return invalid("exx_apply: NULL array");
+    if (c.n_occ < 1 || c.n_in < 1 || c.n_occ > 65536 || c.n_in > 65536) return invalid("exx_apply: orbital counts must be in [1, 65536]");
+    if (c.ld_occ < P->N || c.ld_in < P->N || c.ld_out < P->N) return invalid("exx_apply: leading dimensions must be >= N");
+    const char *o0 = reinterpret_cast<const char *>(c.out);
+    const char *o1 = o0 + (size_t(c.n_in - 1) * c.ld_out + P->N) * sizeof(double);
     auto overlaps = [&](const double *a, int n, long ld) {
         const char *a0 = reinterpret_cast<const char *>(a);
         const char *a1 = a0 + (size_t(n - 1) * ld + P->N) * sizeof(double);
         return a0 < o1 && o0 < a1;
     };
-    if (overlaps(Psi_occ, n_occ, ld_occ) || overlaps(Psi_in, n_in, ld_in)) return invalid("exx_apply: out overlaps an input");
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const bool aliased = (Psi_in == Psi_occ) && (ld_in == ld_occ) && (n_in >= n_occ);
-    P->launches = 0;
-    if (int rc = ensure_schedule(*P, n_occ, n_in, aliased, s)) return rc;
+    if (overlaps(c.Psi_occ, c.n_occ, c.ld_occ) || overlaps(c.Psi_in, c.n_in, c.ld_in)) return invalid("exx_apply: out overlaps an input");
+    c.aliased = (c.Psi_in == c.Psi_occ) && (c.ld_in == c.ld_occ) && (c.n_in >= c.n_occ);
+    if (int rc = ensure_schedule(*P, c.n_occ, c.n_in, c.aliased, s)) return rc;
+    const Schedule &S = P->sched;
+    if (P->prec == EXX_PREC_FP64) {
+        size_t fb = size_t(S.max_fields) * P->N * sizeof(double);
+        if (int rc = dev_reserve(P->work[0], fb)) return rc;
+        return dev_reserve(P->work[1], fb);
+    }
+    if (int rc = tc_reserve_orbitals(*P, c.n_occ, c.n_in, c.aliased)) return rc;
+    const bool hl = tc_is_hilo(P->prec);
+    P->tc_lo_off = hl ? long(S.max_fields) * P->N : 0;
+    size_t fb = size_t(S.max_fields) * P->N * sizeof(float) * (hl ? 2 : 1);
+    if (int rc = dev_reserve(P->work[0], fb)) return rc;
+    return dev_reserve(P->work[1], fb);
+}
+
+// The launches of one exx_apply (stream work only: capturable into a CUDA graph).
+static int apply_launch(Plan *P, const ApplyCall &c, cudaStream_t s)
+{
     const Schedule &S = P->sched;
     const int2 *pairs_d = static_cast<const int2 *>(P->pairs_d.p);
     const Block *blocks_d = static_cast<const Block *>(P->blocks_d.p);
     if (P->prec == EXX_PREC_FP64) {
-        size_t fb = size_t(S.max_fields) * P->N * sizeof(double);
-        if (int rc = dev_reserve(P->work[0], fb)) return rc;
-        if (int rc = dev_reserve(P->work[1], fb)) return rc;
-        EXX_CUDA(cudaMemset2DAsync(out, size_t(ld_out) * sizeof(double), 0, size_t(P->N) * sizeof(double),
-                                   n_in, s));
+        EXX_CUDA(cudaMemset2DAsync(c.out, size_t(c.ld_out) * sizeof(double), 0, size_t(P->N) * sizeof(double),
+                                   c.n_in, s));
         for (size_t b = 0; b < S.batches.size(); ++b) {
             if (int(b % P->shard_world) != P->shard_rank) continue;
             const Batch &bt = S.batches[b];
             double *V = nullptr;
-            if (int rc = fp64_solve_batch(*P, Psi_occ, ld_occ, Psi_in, ld_in, pairs_d + S.pair0[b], bt.nfields,
-                                          static_cast<double *>(P->work[0].p),
-                                          static_cast<double *>(P->work[1].p), &V, s))
+            if (int rc = fp64_solve_batch(*P, c.Psi_occ, c.ld_occ, c.Psi_in, c.ld_in, pairs_d + S.pair0[b], bt.nfields,
+                                          static_cast<double *>(P->work[0].p), static_cast<double *>(P->work[1].p), &V, s))
                 return rc;
-            if (int rc = fp64_accumulate(*P, Psi_occ, ld_occ, Psi_in, ld_in, f, blocks_d + bt.block0, bt.nblocks,
-                                         V, out, ld_out, s))
+            if (int rc = fp64_accumulate(*P, c.Psi_occ, c.ld_occ, c.Psi_in, c.ld_in, c.f, blocks_d + bt.block0,
+                                         bt.nblocks, V, c.out, c.ld_out, s))
                 return rc;
         }
         return EXX_OK;
     }
-    // split precision on the tensor cores
     const int prec = P->prec;
-    if (int rc = tc_prepare_orbitals(*P, Psi_occ, n_occ, ld_occ, f, Psi_in, n_in, ld_in, aliased, s)) return rc;
-    const bool hl = tc_is_hilo(prec);
-    P->tc_lo_off = hl ? long(S.max_fields) * P->N : 0;
-    size_t fb = size_t(S.max_fields) * P->N * sizeof(float) * (hl ? 2 : 1);
-    if (int rc = dev_reserve(P->work[0], fb)) return rc;
-    if (int rc = dev_reserve(P->work[1], fb)) return rc;
+    if (int rc = tc_prepare_orbitals(*P, c.Psi_occ, c.n_occ, c.ld_occ, c.f, c.Psi_in, c.n_in, c.ld_in, c.aliased, s))
+        return rc;
     for (size_t b = 0; b < S.batches.size(); ++b) {
         if (int(b % P->shard_world) != P->shard_rank) continue;
         const Batch &bt = S.batches[b];
@@ -377,7 +404,59 @@ int exx_apply(exx_plan plan, const double *Psi_occ, int n_occ, long ld_occ, cons
             return rc;
         if (int rc = tc_accumulate(*P, blocks_d + bt.block0, bt.nblocks, P->tc_result, s)) return rc;
     }
-    return tc_finalize(*P, n_in, out, ld_out, s);
+    return tc_finalize(*P, c.n_in, c.out, c.ld_out, s);
+}
+
+// Graphs of exx_apply_batched, keyed by everything the captured launches depend on.
+struct GraphEntry {
+    std::vector<uintptr_t> key;
+    cudaGraphExec_t exec;
+    std::vector<Plan *> plans;
+    std::vector<long> launches;   // kernels each plan's part of the graph launches
+};
+static std::mutex g_graph_mutex;
+static std::vector<GraphEntry> g_graphs;
+constexpr size_t kMaxGraphs = 8;
+
+// Drops every cached graph that launches work of plan P (called before P is freed).
+static void graph_evict_plan(const Plan *P)
+{
+    std::lock_guard<std::mutex> lock(g_graph_mutex);
+    for (size_t i = 0; i < g_graphs.size();) {
+        if (std::find(g_graphs[i].plans.begin(), g_graphs[i].plans.end(), P) != g_graphs[i].plans.end()) {
+            cudaGraphExecDestroy(g_graphs[i].exec);
+            g_graphs.erase(g_graphs.begin() + i);
+        } else {
+            ++i;
+        }
+    }
+}
+
+static void graph_key_add(std::vector<uintptr_t> &k, const Plan *P, const ApplyCall &c)
+{
+    const uintptr_t v[] = {uintptr_t(P), uintptr_t(P->epoch), uintptr_t(P->prec), uintptr_t(P->pairs_per_batch), uintptr_t(P->block_orbitals),
+                           uintptr_t(P->shard_rank), uintptr_t(P->shard_world), uintptr_t(c.Psi_occ), uintptr_t(c.n_occ),
+                           uintptr_t(c.ld_occ), uintptr_t(c.f), uintptr_t(c.Psi_in), uintptr_t(c.n_in), uintptr_t(c.ld_in),
+                           uintptr_t(c.out), uintptr_t(c.ld_out), uintptr_t(P->work[0].p), uintptr_t(P->work[1].p),
+                           uintptr_t(P->psi32.p), uintptr_t(P->g32.p), uintptr_t(P->acc_hi.p), uintptr_t(P->acc_lo.p),
+                           uintptr_t(P->pairs_d.p), uintptr_t(P->blocks_d.p), uintptr_t(P->err_d.p),
+                           uintptr_t(P->timing.on)};
+    k.insert(k.end(), v, v + sizeof(v) / sizeof(v[0]));
+}
+
+}  // namespace exx
+
+extern "C" {
+
+int exx_apply(exx_plan plan, const double *Psi_occ, int n_occ, long ld_occ, const double *f,
+              const double *Psi_in, int n_in, long ld_in, double *out, long ld_out, exx_stream_t stream)
+{
+    Plan *P = as_plan(plan);
+    ApplyCall c{Psi_occ, n_occ, ld_occ, f, Psi_in, n_in, ld_in, out, ld_out, false};
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (int rc = apply_prepare(P, c, s)) return rc;
+    P->launches = 0;
+    return apply_launch(P, c, s);
 }
 
 int exx_energy(exx_plan plan, const double *Psi_occ, int n_occ, long ld, const double *f, const double *VxPsi,
@@ -480,11 +559,66 @@ int exx_ace_step_host(exx_plan plan, const double *Psi_h, int n, long ld, int n_
 int exx_apply_batched(const exx_plan *plans, int nsys, const exx_apply_args *args, exx_stream_t stream)
 {
     if (!plans || !args || nsys < 1) return invalid("exx_apply_batched: bad arguments");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<ApplyCall> calls(nsys);
+    std::vector<uintptr_t> key;
+    int prec0 = -1;
     for (int i = 0; i < nsys; ++i) {
-        if (int rc = exx_apply(plans[i], args[i].Psi_occ, args[i].n_occ, args[i].ld_occ, args[i].f,
-                               args[i].Psi_in, args[i].n_in, args[i].ld_in, args[i].out, args[i].ld_out, stream))
-            return rc;
+        Plan *P = as_plan(plans[i]);
+        if (!P) return invalid("exx_apply_batched: NULL plan");
+        if (prec0 < 0) prec0 = P->prec;
+        if (P->prec != prec0) return invalid("exx_apply_batched: every plan must use the same precision");
+        calls[i] = ApplyCall{args[i].Psi_occ, args[i].n_occ, args[i].ld_occ, args[i].f, args[i].Psi_in,
+                             args[i].n_in, args[i].ld_in, args[i].out, args[i].ld_out, false};
+        if (int rc = apply_prepare(P, calls[i], s)) return rc;   // all allocation happens here
     }
+    for (int i = 0; i < nsys; ++i) graph_key_add(key, as_plan(plans[i]), calls[i]);
+    bool any_timing = false;
+    for (int i = 0; i < nsys; ++i) any_timing |= as_plan(plans[i])->timing.on;
+    if (s == nullptr || any_timing) {   // legacy stream or per-launch timing: no graph
+        for (int i = 0; i < nsys; ++i) as_plan(plans[i])->launches = 0;
+        for (int i = 0; i < nsys; ++i)
+            if (int rc = apply_launch(as_plan(plans[i]), calls[i], s)) return rc;
+        return EXX_OK;
+    }
+    std::lock_guard<std::mutex> lock(g_graph_mutex);
+    for (auto &g : g_graphs)
+        if (g.key == key) {
+            EXX_CUDA(cudaGraphLaunch(g.exec, s));
+            for (int i = 0; i < nsys; ++i) g.plans[i]->launches = 0;
+            for (int i = 0; i < nsys; ++i) g.plans[i]->launches += g.launches[i];
+            return EXX_OK;
+        }
+    // first call with this key: capture every system's launches into one graph
+    GraphEntry ent;
+    ent.key = key;
+    for (int i = 0; i < nsys; ++i) {
+        ent.plans.push_back(as_plan(plans[i]));
+        ent.plans.back()->launches = 0;
+    }
+    EXX_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+    int rc = EXX_OK;
+    for (int i = 0; i < nsys && rc == EXX_OK; ++i) {
+        const long before = ent.plans[i]->launches;
+        rc = apply_launch(ent.plans[i], calls[i], s);
+        ent.launches.push_back(ent.plans[i]->launches - before);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (rc != EXX_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "exx_apply_batched: cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&ent.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "exx_apply_batched: cudaGraphInstantiate");
+    if (g_graphs.size() >= kMaxGraphs) {
+        cudaGraphExecDestroy(g_graphs.front().exec);
+        g_graphs.erase(g_graphs.begin());
+    }
+    g_graphs.push_back(ent);
+    EXX_CUDA(cudaGraphLaunch(ent.exec, s));
     return EXX_OK;
 }
 

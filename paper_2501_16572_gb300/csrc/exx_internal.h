@@ -128,12 +128,14 @@ struct Plan {
     DevBuf host_stage_psi, host_stage_f, host_stage_xi, host_stage_w;
     DevBuf err_d;                   // device error word of the bounded waits
     int tc_occ_off = 0;             // column of Psi_occ in the fp32 planes (0 when aliased)
+    int tc_n_occ = 0;               // rows of g32's hi plane (its lo plane follows)
     float *tc_result = nullptr;     // buffer holding the last batch's solutions
     long tc_lo_off = 0;             // hi+lo intermediates: offset of the lo plane (floats)
     long launches = 0;
     Timing timing;
     // cached schedule
     int sched_key[4] = {-1, -1, -1, -1};
+    uint64_t epoch = 0;   // changes whenever device data or settings that launches read change
     Schedule sched;
 };
 
@@ -148,6 +150,8 @@ int fp64_upload(Plan &P);
 
 // split path (exx_tc.cu)
 int tc_upload(Plan &P, int prec);
+int tc_reserve_orbitals(Plan &P, int n_occ, int n_in, bool aliased);
+void bump_epoch(Plan &P);
 int tc_prepare_orbitals(Plan &P, const double *psi_occ, int n_occ, long ld_occ, const double *f,
                         const double *psi_in, int n_in, long ld_in, bool aliased, cudaStream_t s);
 int tc_solve_batch(Plan &P, int prec, const int2 *pairs_d, int nfields, float *bufA, float *bufB,

@@ -195,33 +195,33 @@ __device__ __forceinline__ void read8(uint32_t d, int Np, int c0, float rs, cons
     for (int l = 0; l < NACC; ++l)
 #pragma unroll
         for (int e = 0; e < 8; ++e) tc::order_after_wait(r[l][e]);
-    if (MODE == MODE_FLOAT_TF32) {
+    if constexpr (MODE == MODE_FLOAT_TF32) {
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             vh[e] = __uint_as_float(r[0][e]);
             vl[e] = 0.f;
         }
-        return;
-    }
-    float t[8];
+    } else {
+        float t[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) t[e] = 0.f;
+        for (int e = 0; e < 8; ++e) t[e] = 0.f;
 #pragma unroll
-    for (int l = NACC - 1; l >= 1; --l)
+        for (int l = NACC - 1; l >= 1; --l)
 #pragma unroll
-        for (int e = 0; e < 8; ++e) t[e] = (__uint_as_float(r[l][e]) + t[e]) * (1.f / 256.f);
+            for (int e = 0; e < 8; ++e) t[e] = (__uint_as_float(r[l][e]) + t[e]) * (1.f / 256.f);
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        const float l0 = __uint_as_float(r[0][e]);
-        const float sc = rs * cs[c0 + e];
-        if (HL) {
-            const float h = l0 + t[e];
-            const float bp = h - l0;
-            vl[e] = ((l0 - (h - bp)) + (t[e] - bp)) * sc;
-            vh[e] = h * sc;
-        } else {
-            vh[e] = (l0 + t[e]) * sc;
-            vl[e] = 0.f;
+        for (int e = 0; e < 8; ++e) {
+            const float l0 = __uint_as_float(r[0][e]);
+            const float sc = rs * cs[c0 + e];
+            if (HL) {
+                const float h = l0 + t[e];
+                const float bp = h - l0;
+                vl[e] = ((l0 - (h - bp)) + (t[e] - bp)) * sc;
+                vh[e] = h * sc;
+            } else {
+                vh[e] = (l0 + t[e]) * sc;
+                vl[e] = 0.f;
+            }
         }
     }
 }
@@ -248,7 +248,7 @@ struct TcPassArgs {
     int *err;
 };
 
-template <int MODE, int S, int SB, bool HL, int LOAD, int STORE, bool DOUBLE, int TPR, int NBUF>
+template <int MODE, int S, int SB, bool HL, int LOAD, int STORE, bool DOUBLE, int TPR, int NBUF, int NSETS>
 __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -263,17 +263,21 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
     const uint32_t b_piece = uint32_t(Np) * Kp * ES;
     uint8_t *sB1 = smem;
     uint8_t *sB2 = smem + a.img_bytes;
-    // two A buffers (slices of tile t and t+1) and two TMEM accumulator sets
+    // NSETS = 2: two A buffers (slices of tile t and t+1) and two TMEM accumulator sets,
+    // so the GEMMs of tile t overlap the epilogue of t-1 and the slicing of t+1.
+    // NSETS = 1 (long axes): one of each, the epilogue of t-1 comes before slicing t.
     uint8_t *sA0 = smem + (DOUBLE ? 2 : 1) * a.img_bytes;
-    // Input staging.  KSLOW / PAIR: [k][row] (a warp touches 32 consecutive words); KFAST:
-    // [row][Kp + 4] (16-byte copies, read back conflict-free because (Kp + 4)/4 is odd).
+    // Input staging.  KSLOW / PAIR: [k][row] (a warp touches 32 consecutive words; rows
+    // k >= K are zero from the start and never written); KFAST: [row][Kp + 4] (16-byte
+    // copies, read back conflict-free because (Kp + 4)/4 is odd; columns k >= K are
+    // masked when read).
     // PAIR stages psi_m hi, psi_m lo, psi_n hi, psi_n lo; the others hi (and lo).  Pass 3
     // stages f(Lambda) D1 ([col][row], hi and lo) in the same space after the first GEMM.
     // NBUF staging buffers = tiles whose copies are in flight.
     constexpr int NSTG = LOAD == LOAD_PAIR ? 4 : (HL ? 2 : 1);
-    const int stg_len = kRows * (Kp + 4);
+    const int stg_len = kRows * (LOAD == LOAD_KFAST ? Kp + 4 : Kp);
     const int buf_len = max(NSTG * stg_len, DOUBLE ? 2 * Np * kRows : 0);
-    float *stg0 = reinterpret_cast<float *>(sA0 + 2 * a_piece * S);
+    float *stg0 = reinterpret_cast<float *>(sA0 + NSETS * a_piece * S);
     float *maxbuf = stg0 + NBUF * buf_len;
     uint64_t *bar1 = reinterpret_cast<uint64_t *>(maxbuf + NT);   // [2]: first GEMM of each set
     uint64_t *bar2 = bar1 + 2;                                      // [2]: second GEMM (pass 3)
@@ -283,7 +287,7 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
     const float *cs2 = reinterpret_cast<const float *>(sB2 + SB * b_piece);
     const int tid = threadIdx.x, warp = tid >> 5, row = tid & (kRows - 1), q = tid / kRows;
     const int set_cols = NACC * Np;
-    const int ncols = 2 * set_cols <= 32 ? 32 : 2 * set_cols <= 64 ? 64 : 2 * set_cols <= 128 ? 128 : 2 * set_cols <= 256 ? 256 : 512;
+    const int ncols = NSETS * set_cols <= 32 ? 32 : NSETS * set_cols <= 64 ? 64 : NSETS * set_cols <= 128 ? 128 : NSETS * set_cols <= 256 ? 256 : 512;
     const int nchunk = Kp / EPC;
 
     for (uint32_t i = tid * 16; i < a.img_bytes; i += (NT + 32) * 16) {
@@ -359,7 +363,7 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
     // Staged values (hi, lo) of chunk c (EPC elements) of this thread's row.  KFAST rows are
     // read as float4 (conflict-free with the odd (Kp + 4)/4 row pitch).
     auto staged_chunk = [&](const float *stg, int c, float (&hi)[8], float (&lo)[8]) {
-        if (LOAD == LOAD_KFAST) {
+        if constexpr (LOAD == LOAD_KFAST) {
 #pragma unroll
             for (int j = 0; j < EPC; j += 4) {
                 const float4 h = *reinterpret_cast<const float4 *>(stg + row * (Kp + 4) + c * EPC + j);
@@ -371,19 +375,26 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
                     lo[j] = lo[j + 1] = lo[j + 2] = lo[j + 3] = 0.f;
                 }
             }
-            return;
-        }
+            // columns k >= K of a KFAST row are not copied, and in pass 3 they still hold
+            // the previous tile's middle values (staged over the same space): zero them
+            if ((c + 1) * EPC > a.K) {
 #pragma unroll
-        for (int e = 0; e < EPC; ++e) {
-            const int k = c * EPC + e;
-            if (LOAD == LOAD_PAIR) {
-                const float ah = stg[k * kRows + row], al = stg[stg_len + k * kRows + row];
-                const float bh = stg[2 * stg_len + k * kRows + row], bl = stg[3 * stg_len + k * kRows + row];
-                hi[e] = ah * bh;
-                lo[e] = fmaf(ah, bh, -hi[e]) + fmaf(ah, bl, al * bh);
-            } else {
-                hi[e] = stg[k * kRows + row];
-                lo[e] = HL ? stg[stg_len + k * kRows + row] : 0.f;
+                for (int e = 0; e < EPC; ++e)
+                    if (c * EPC + e >= a.K) hi[e] = lo[e] = 0.f;
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < EPC; ++e) {
+                const int k = c * EPC + e;
+                if (LOAD == LOAD_PAIR) {
+                    const float ah = stg[k * kRows + row], al = stg[stg_len + k * kRows + row];
+                    const float bh = stg[2 * stg_len + k * kRows + row], bl = stg[3 * stg_len + k * kRows + row];
+                    hi[e] = ah * bh;
+                    lo[e] = fmaf(ah, bh, -hi[e]) + fmaf(ah, bl, al * bh);
+                } else {
+                    hi[e] = stg[k * kRows + row];
+                    lo[e] = HL ? stg[stg_len + k * kRows + row] : 0.f;
+                }
             }
         }
     };
@@ -420,7 +431,7 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
         // ---- MMA warp: one hand-off per GEMM, in the compute threads' order ----
         long it = 0;
         for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-            const int st = int(it & 1);
+            const int st = int(it % NSETS);
             if (tc::bar_red_or(kBarHandoff, NT + 32, *sflag != 0)) break;
             if (tid == NT) {
                 tc::tc_fence_after();
@@ -490,7 +501,13 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
     const float *prev_cs = cs1;
     long it = 0;
     for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-        const int st = int(it & 1);
+        const int st = int(it % NSETS);
+        if (NSETS == 1 && prev_tile >= 0) {   // one A buffer / TMEM set: finish t-1 first
+            if (DOUBLE) wait_bar(bar2 + prev_set, ph2, prev_set);
+            else wait_bar(bar1 + prev_set, ph1, prev_set);
+            epilogue(prev_tile, prev_set, prev_rs, prev_cs);
+            prev_tile = -1;
+        }
         const long g = tile * kRows + row;
         const bool active = g < rows;
         const int p = active ? int(g / a.R) : 0;
@@ -689,7 +706,7 @@ __global__ void __launch_bounds__(kRows, 1) tc_unit_gemm_kernel(int n, int k, co
 // g = f_m psi_m in fp32 for the accumulation; zero the compensated accumulators.
 __global__ void tc_prepare_kernel(long N, int n_in, const double *psi_in, long ld_in, int n_occ,
                                   const double *psi_occ, long ld_occ, int copy_occ, const double *f,
-                                  float *hi, float *lo, float *g, float *acc_hi, float *acc_lo)
+                                  float *hi, float *lo, float *g, float *g_lo, float *acc_hi, float *acc_lo)
 {
     const long total_in = long(n_in) * N;
     const long total = total_in + (copy_occ ? long(n_occ) * N : 0);
@@ -711,7 +728,10 @@ __global__ void tc_prepare_kernel(long N, int n_in, const double *psi_in, long l
     const long tg = long(n_occ) * N;
     for (long e = long(blockIdx.x) * blockDim.x + threadIdx.x; e < tg; e += long(gridDim.x) * blockDim.x) {
         long c = e / N, r = e - c * N;
-        g[e] = float(f[c] * psi_occ[c * ld_occ + r]);
+        const double gv = f[c] * psi_occ[c * ld_occ + r];   // f_s psi_s as an FP32 pair
+        const float gh = float(gv);
+        g[e] = gh;
+        g_lo[e] = float(gv - double(gh));
     }
 }
 
@@ -724,19 +744,33 @@ __device__ __forceinline__ void two_sum_add(float &s, float &c, float x)
     s = t;
 }
 
+// (s, c) -= (gh + gl)(vh + vl): the leading product exactly (its rounding error from an
+// FMA), the second-order products rounded into the compensation word.
+__device__ __forceinline__ void sub_product(float &s, float &c, float gh, float gl, float vh, float vl)
+{
+    const float p = __fmul_rn(gh, vh);
+    const float e = fmaf(gh, vh, -p);
+    two_sum_add(s, c, -p);
+    c -= e + fmaf(gh, vl, gl * vh);
+}
+
 __device__ __forceinline__ int diag_idx(int i, int j, int nI) { return i * nI - (i * (i - 1)) / 2 + (j - i); }
 
+// One launch per batch: CUDA block (x, y) = 256 grid points of the outputs of Block y.
+// Blocks of one batch have disjoint outputs, so no atomics are needed.
 template <bool HL>
 __global__ void __launch_bounds__(256) tc_accum_kernel(long N, const Block *blocks, const float *V, long lo_off,
-                                                       const float *g, float *acc_hi, float *acc_lo)
+                                                       const float *g, const float *g_lo, float *acc_hi,
+                                                       float *acc_lo)
 {
     const Block b = blocks[blockIdx.y];
     const long r = long(blockIdx.x) * blockDim.x + threadIdx.x;
     if (r >= N) return;
     const float *Vb = V + size_t(b.field0) * N + r;
-    // -g V (V = hi + lo when the intermediates carry a lo plane)
-    auto term = [&](float gv, size_t fo) {
-        return HL ? -fmaf(gv, Vb[fo], gv * Vb[lo_off + fo]) : -gv * Vb[fo];
+    auto vh_at = [&](size_t fo) { return Vb[fo]; };
+    auto vl_at = [&](size_t fo) { return HL ? Vb[lo_off + fo] : 0.f; };
+    auto add = [&](float &s, float &c, int src, size_t fo) {
+        sub_product(s, c, g[size_t(src) * N + r], g_lo[size_t(src) * N + r], vh_at(fo), vl_at(fo));
     };
     auto finish = [&](int t, float s, float c) {
         float hs = s + c;
@@ -749,7 +783,7 @@ __global__ void __launch_bounds__(256) tc_accum_kernel(long N, const Block *bloc
             float s = acc_hi[size_t(o) * N + r], c = acc_lo[size_t(o) * N + r];
             for (int q = 0; q < b.nI; ++q) {
                 const int fi = q <= t ? diag_idx(q, t, b.nI) : diag_idx(t, q, b.nI);
-                two_sum_add(s, c, term(g[size_t(b.I0 + q) * N + r], size_t(fi) * N));
+                add(s, c, b.I0 + q, size_t(fi) * N);
             }
             finish(o, s, c);
         }
@@ -758,15 +792,14 @@ __global__ void __launch_bounds__(256) tc_accum_kernel(long N, const Block *bloc
     for (int j = 0; j < b.nJ; ++j) {
         const int o = b.J0 + j;
         float s = acc_hi[size_t(o) * N + r], c = acc_lo[size_t(o) * N + r];
-        for (int i = 0; i < b.nI; ++i) two_sum_add(s, c, term(g[size_t(b.I0 + i) * N + r], size_t(i * b.nJ + j) * N));
+        for (int i = 0; i < b.nI; ++i) add(s, c, b.I0 + i, size_t(i * b.nJ + j) * N);
         finish(o, s, c);
     }
     if (b.kind == BLK_SYM_OFF) {
         for (int i = 0; i < b.nI; ++i) {
             const int o = b.I0 + i;
             float s = acc_hi[size_t(o) * N + r], c = acc_lo[size_t(o) * N + r];
-            for (int j = 0; j < b.nJ; ++j)
-                two_sum_add(s, c, term(g[size_t(b.J0 + j) * N + r], size_t(i * b.nJ + j) * N));
+            for (int j = 0; j < b.nJ; ++j) add(s, c, b.J0 + j, size_t(i * b.nJ + j) * N);
             finish(o, s, c);
         }
     }
@@ -783,29 +816,30 @@ __global__ void tc_finalize_kernel(long N, int n_in, const float *acc_hi, const 
 }
 
 // ---- launch helpers -------------------------------------------------------------------
-size_t pass_smem(int prec, int Np, bool dbl, int load, int nbuf = 1)
+size_t pass_smem(int prec, int Np, bool dbl, int load, int nbuf = 1, int nsets = 1)
 {
     const PrecInfo pi = prec_info(prec);
-    size_t a = 2 * size_t(pi.S) * kRows * Np * pi.es;   // two A buffers
-    size_t staging = size_t(load == LOAD_PAIR ? 4 : (pi.hl ? 2 : 1)) * kRows * (Np + 4) * sizeof(float);
+    size_t a = size_t(nsets) * pi.S * kRows * Np * pi.es;   // A buffers
+    const int pitch = load == LOAD_KFAST ? Np + 4 : Np;   // KFAST rows are padded, [k][row] layouts not
+    size_t staging = size_t(load == LOAD_PAIR ? 4 : (pi.hl ? 2 : 1)) * kRows * pitch * sizeof(float);
     if (dbl) staging = std::max(staging, size_t(2) * kRows * Np * sizeof(float));
     staging *= size_t(nbuf);                                   // staging buffers in flight
     const size_t maxbuf = size_t(kRows) * 4 * sizeof(float);   // up to 4 threads per row
     return (dbl ? 2 : 1) * image_bytes(prec, Np) + a + staging + maxbuf + 64;
 }
 
-int tmem_cols(int prec, int Np) { return pow2_cols(2 * prec_info(prec).nacc * Np); }   // two sets
+int tmem_cols(int prec, int Np, int nsets = 1) { return pow2_cols(nsets * prec_info(prec).nacc * Np); }
 
 constexpr int kTPR = 4;   // threads per tile row
 
-template <int MODE, int S, int SB, bool HL, int LOAD, int STORE, bool DOUBLE, int NBUF>
+template <int MODE, int S, int SB, bool HL, int LOAD, int STORE, bool DOUBLE, int NBUF, int NSETS>
 int launch_tc_pass_nb(Plan &P, int kind, int prec, const TcPassArgs &a, cudaStream_t s)
 {
-    auto kern = tc_pass_kernel<MODE, S, SB, HL, LOAD, STORE, DOUBLE, kTPR, NBUF>;
-    size_t smem = pass_smem(prec, a.Np, DOUBLE, LOAD, NBUF);
+    auto kern = tc_pass_kernel<MODE, S, SB, HL, LOAD, STORE, DOUBLE, kTPR, NBUF, NSETS>;
+    size_t smem = pass_smem(prec, a.Np, DOUBLE, LOAD, NBUF, NSETS);
     // TMEM: co-resident CTAs must not ask for more than 512 columns in total, so the
     // shared-memory request is raised until at most 512 / cols CTAs fit on one SM.
-    const int cols = tmem_cols(prec, a.Np);
+    const int cols = tmem_cols(prec, a.Np, NSETS);
     const int max_ctas = std::max(1, 512 / cols);
     const size_t sm_total = 233472;   // 228 KB of shared memory per SM
     size_t floor_req = sm_total / size_t(max_ctas + 1) - 1024 + 64;
@@ -829,13 +863,18 @@ int launch_tc_pass_nb(Plan &P, int kind, int prec, const TcPassArgs &a, cudaStre
     return EXX_OK;
 }
 
-// Two staging buffers (two tiles of copies in flight) when they fit in shared memory.
+// Largest configuration that fits: pipelined with two staging buffers, pipelined with one,
+// or (long axes) one A buffer and one TMEM set.
 template <int MODE, int S, int SB, bool HL, int LOAD, int STORE, bool DOUBLE>
 int launch_tc_pass(Plan &P, int kind, int prec, const TcPassArgs &a, cudaStream_t s)
 {
-    if (LOAD != LOAD_PAIR && pass_smem(prec, a.Np, DOUBLE, LOAD, 2) <= 232448)
-        return launch_tc_pass_nb<MODE, S, SB, HL, LOAD, STORE, DOUBLE, 2>(P, kind, prec, a, s);
-    return launch_tc_pass_nb<MODE, S, SB, HL, LOAD, STORE, DOUBLE, 1>(P, kind, prec, a, s);
+    const size_t lim = 232448;
+    const bool tm2 = tmem_cols(prec, a.Np, 2) <= 512;
+    if (LOAD != LOAD_PAIR && tm2 && pass_smem(prec, a.Np, DOUBLE, LOAD, 2, 2) <= lim)
+        return launch_tc_pass_nb<MODE, S, SB, HL, LOAD, STORE, DOUBLE, 2, 2>(P, kind, prec, a, s);
+    if (tm2 && pass_smem(prec, a.Np, DOUBLE, LOAD, 1, 2) <= lim)
+        return launch_tc_pass_nb<MODE, S, SB, HL, LOAD, STORE, DOUBLE, 1, 2>(P, kind, prec, a, s);
+    return launch_tc_pass_nb<MODE, S, SB, HL, LOAD, STORE, DOUBLE, 1, 1>(P, kind, prec, a, s);
 }
 
 template <int MODE, int S, int SB, bool HL>
@@ -889,8 +928,13 @@ int tc_upload(Plan &P, int prec)
     const int inv_of[6] = {0, 0, 0, 1, 1, 1};
     for (int d = 0; d < 3; ++d) {
         const int Np = pad16(P.n[d]);
-        // the largest footprint of the passes on this axis: pair prologue (z), double (y)
-        const size_t need = std::max(pass_smem(prec, Np, d == 1, LOAD_KSLOW), pass_smem(prec, Np, false, d == 2 ? LOAD_PAIR : LOAD_KSLOW));
+        // the smallest variant of each pass on this axis must fit: x is read by passes 2
+        // (KFAST) and 4 (KSLOW), y by pass 3 (KFAST, two GEMMs), z by passes 1 (pair
+        // products) and 5 (KSLOW)
+        size_t need = 0;
+        if (d == 0) need = std::max(pass_smem(prec, Np, false, LOAD_KFAST), pass_smem(prec, Np, false, LOAD_KSLOW));
+        if (d == 1) need = pass_smem(prec, Np, true, LOAD_KFAST);
+        if (d == 2) need = std::max(pass_smem(prec, Np, false, LOAD_PAIR), pass_smem(prec, Np, false, LOAD_KSLOW));
         if (need > 232448 || tmem_cols(prec, Np) > 512) {
             set_error("split precision: grid axis too long for the on-chip operand images of this build");
             return EXX_ERR_UNSUPPORTED;
@@ -955,21 +999,30 @@ int tc_upload(Plan &P, int prec)
     return EXX_OK;
 }
 
-int tc_prepare_orbitals(Plan &P, const double *psi_occ, int n_occ, long ld_occ, const double *f,
-                        const double *psi_in, int n_in, long ld_in, bool aliased, cudaStream_t s)
+int tc_reserve_orbitals(Plan &P, int n_occ, int n_in, bool aliased)
 {
     const int ncols = n_in + (aliased ? 0 : n_occ);
     const size_t plane = size_t(ncols) * P.N;
     if (P.psi32.bytes != 2 * plane * sizeof(float)) dev_free(P.psi32);   // psi_lo follows psi_hi exactly
     if (int rc = dev_reserve(P.psi32, 2 * plane * sizeof(float))) return rc;
-    if (int rc = dev_reserve(P.g32, size_t(n_occ) * P.N * sizeof(float))) return rc;
+    if (int rc = dev_reserve(P.g32, 2 * size_t(n_occ) * P.N * sizeof(float))) return rc;   // hi, lo planes
     if (int rc = dev_reserve(P.acc_hi, size_t(n_in) * P.N * sizeof(float))) return rc;
     if (int rc = dev_reserve(P.acc_lo, size_t(n_in) * P.N * sizeof(float))) return rc;
     P.tc_occ_off = aliased ? 0 : n_in;
+    P.tc_n_occ = n_occ;
+    return EXX_OK;
+}
+
+int tc_prepare_orbitals(Plan &P, const double *psi_occ, int n_occ, long ld_occ, const double *f,
+                        const double *psi_in, int n_in, long ld_in, bool aliased, cudaStream_t s)
+{
+    const int ncols = n_in + (aliased ? 0 : n_occ);
+    const size_t plane = size_t(ncols) * P.N;
     float *hi = static_cast<float *>(P.psi32.p);
     int tb = timing_begin(P, EXX_TIMING_PREP, s);
     tc_prepare_kernel<<<4 * P.num_sms, 256, 0, s>>>(P.N, n_in, psi_in, ld_in, n_occ, psi_occ, ld_occ, aliased ? 0 : 1,
                                                    f, hi, hi + plane, static_cast<float *>(P.g32.p),
+                                                   static_cast<float *>(P.g32.p) + size_t(n_occ) * P.N,
                                                    static_cast<float *>(P.acc_hi.p), static_cast<float *>(P.acc_lo.p));
     timing_end(P, tb, s);
     EXX_LAUNCH("tc_prepare_kernel");
@@ -992,12 +1045,12 @@ int tc_accumulate(Plan &P, const Block *blocks_d, int nblocks, const float *V, c
 {
     dim3 grid(unsigned((P.N + 255) / 256), unsigned(nblocks));
     int tb = timing_begin(P, EXX_TIMING_ACCUM, s);
+    const float *g = static_cast<const float *>(P.g32.p), *g_lo = g + size_t(P.tc_n_occ) * P.N;
+    float *ah = static_cast<float *>(P.acc_hi.p), *al = static_cast<float *>(P.acc_lo.p);
     if (prec_info(P.prec).hl)
-        tc_accum_kernel<true><<<grid, 256, 0, s>>>(P.N, blocks_d, V, P.tc_lo_off, static_cast<const float *>(P.g32.p),
-                                                   static_cast<float *>(P.acc_hi.p), static_cast<float *>(P.acc_lo.p));
+        tc_accum_kernel<true><<<grid, 256, 0, s>>>(P.N, blocks_d, V, P.tc_lo_off, g, g_lo, ah, al);
     else
-        tc_accum_kernel<false><<<grid, 256, 0, s>>>(P.N, blocks_d, V, 0, static_cast<const float *>(P.g32.p),
-                                                    static_cast<float *>(P.acc_hi.p), static_cast<float *>(P.acc_lo.p));
+        tc_accum_kernel<false><<<grid, 256, 0, s>>>(P.N, blocks_d, V, 0, g, g_lo, ah, al);
     timing_end(P, tb, s);
     EXX_LAUNCH("tc_accum_kernel");
     P.launches++;
