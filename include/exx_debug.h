@@ -33,6 +33,10 @@ int exx_debug_schedule(int n_occ, int n_in, int aliased, int block, int max_pair
  * device.  Checks the operand layout and descriptors of the split-precision path. */
 int exx_debug_tc_gemm(int tf32, int n, int k, const float *A, const float *B, float *D, int *err);
 
+/* Quotients n[i] / d by the multiply-shift division the pass kernels use for row ->
+ * (field, row in field) (Granlund & Montgomery 1994, Fig. 4.1), host-side.  d >= 1. */
+int exx_debug_fastdiv(unsigned d, int count, const unsigned *n, unsigned *q);
+
 #ifdef __cplusplus
 }
 #endif

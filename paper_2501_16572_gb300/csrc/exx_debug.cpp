@@ -61,4 +61,12 @@ int exx_debug_tc_gemm(int tf32, int n, int k, const float *A, const float *B, fl
     return exx::tc_unit_gemm(tf32, n, k, A, B, D, err);
 }
 
+int exx_debug_fastdiv(unsigned d, int count, const unsigned *n, unsigned *q)
+{
+    if (d < 1 || count < 0 || (count > 0 && (!n || !q))) return EXX_ERR_INVALID_ARG;
+    const exx::FastDiv f = exx::make_fastdiv(d);
+    for (int i = 0; i < count; ++i) q[i] = exx::fast_div(n[i], f);
+    return EXX_OK;
+}
+
 }  // extern "C"

@@ -25,6 +25,36 @@ int cuda_fail(cudaError_t e, const char *what);
         if (_e != cudaSuccess) return ::exx::cuda_fail(_e, what);          \
     } while (0)
 
+// ---- division by an invariant 32-bit divisor ------------------------------------------
+// Granlund & Montgomery, "Division by invariant integers using multiplication" (PLDI
+// 1994), Fig. 4.1: with l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1,
+//   t = mulhi(m, n),  n / d = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0)
+// exactly for every 32-bit n.  Used for row -> (field, row in field) in the pass kernels.
+#ifdef __CUDACC__
+#define EXX_HD __host__ __device__
+#else
+#define EXX_HD
+#endif
+struct FastDiv {
+    uint32_t d, m, s1, s2;
+};
+inline FastDiv make_fastdiv(uint32_t d)
+{
+    uint32_t l = 0;
+    while ((uint64_t(1) << l) < d) ++l;
+    const uint64_t m = ((uint64_t(1) << 32) * ((uint64_t(1) << l) - d)) / d + 1;
+    return {d, uint32_t(m), l < 1 ? l : 1u, l > 0 ? l - 1 : 0u};
+}
+EXX_HD inline uint32_t fast_div(uint32_t n, const FastDiv &f)
+{
+#ifdef __CUDA_ARCH__
+    const uint32_t t = __umulhi(f.m, n);
+#else
+    const uint32_t t = uint32_t((uint64_t(f.m) * n) >> 32);
+#endif
+    return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
 // ---- the five passes of one batched solve --------------------------------------------
 // A grid function batch is P fields of N values.  Each pass contracts one axis with
 // an n_d x n_d matrix; a pass sees a field as R = N / K rows of K values.
@@ -119,7 +149,10 @@ struct Plan {
     DevBuf F64;                     // F in the P3 layout [b][a][c]
     DevBuf F32;                     // same as two float planes, hi then lo
     // tensor path: per pass and precision the B operand pieces, canonical SMEM image
-    DevBuf Btc[5][6];               // [prec][pass slot]
+    DevBuf Btc[5][6];               // [prec][pass slot]: nblk^2 block images, (c, h) at (c nblk + h)
+    int tc_nblk[5][3] = {};         // [prec][axis]: blocks the axis is cut into (1 = whole axis)
+    int tc_bsz[5][3] = {};          // [prec][axis]: points per block (the last may be shorter)
+    int tc_ysplit[5] = {};          // [prec]: pass 3 as two kernels (forward, inverse)
     // workspace
     DevBuf work[3];                 // batch buffers (fields x N)
     DevBuf pairs_d, blocks_d;       // schedule on the device

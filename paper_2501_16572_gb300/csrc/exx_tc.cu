@@ -101,18 +101,25 @@ __device__ __forceinline__ void split_tf32(float hi, float lo, float (&p)[4])
     p[3] = 0.f;
 }
 
+// Round to the nearest integer (ties to even) for |x| < 2^22: adding 1.5 * 2^23 leaves no
+// fraction bits, so the FP32 addition itself rounds; both additions stay on the FMA pipe.
+__device__ __forceinline__ float round_int(float x)
+{
+    return __fadd_rn(__fadd_rn(x, 12582912.f), -12582912.f);
+}
+
 // Fixed-point slices of (hi + lo) * s, s = 2^(7 - e): integers of at most 8 bits.
 // Each residual (t_i - q_i) is exact; only the first one absorbs lo.
 template <int S>
 __device__ __forceinline__ void slice_fixed(float hi, float lo, float s, float (&q)[4])
 {
     const float t = hi * s;
-    q[0] = rintf(t);
+    q[0] = round_int(t);
     const float t1 = ((t - q[0]) + lo * s) * 256.f;
-    q[1] = (S >= 2) ? rintf(t1) : 0.f;
+    q[1] = (S >= 2) ? round_int(t1) : 0.f;
     const float t2 = (t1 - q[1]) * 256.f;
-    q[2] = (S >= 3) ? rintf(t2) : 0.f;
-    q[3] = (S >= 4) ? rintf((t2 - q[2]) * 256.f) : 0.f;
+    q[2] = (S >= 3) ? round_int(t2) : 0.f;
+    q[3] = (S >= 4) ? round_int((t2 - q[2]) * 256.f) : 0.f;
 }
 
 // Store one 16-byte chunk per piece: vals[q][e] for e < 16/ES elements of row `row`.
@@ -138,6 +145,29 @@ __device__ __forceinline__ void store_chunk(uint8_t *img, uint32_t piece_bytes, 
             v = make_uint4(w[0], w[1], w[2], w[3]);
         }
         *reinterpret_cast<uint4 *>(img + q * piece_bytes + off) = v;
+    }
+}
+
+// Store one 4-element unit per piece: vals[q][e], elements 4u..4u+3 of row `row` (half a
+// 16-byte core-matrix row for bf16, a whole one for tf32).
+template <int ES, int S>
+__device__ __forceinline__ void store_unit(uint8_t *img, uint32_t piece_bytes, int row, int u, uint32_t sbo,
+                                           const float (&vals)[4][4])
+{
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+        if (ES == 4) {
+            *reinterpret_cast<uint4 *>(img + q * piece_bytes + img_off(row, u, sbo)) =
+                make_uint4(__float_as_uint(vals[q][0]), __float_as_uint(vals[q][1]), __float_as_uint(vals[q][2]),
+                           __float_as_uint(vals[q][3]));
+        } else {
+            // the values are integers of at most 8 significant bits, so their bf16 form is
+            // the upper half of their FP32 bits: pack two with one byte permute
+            const uint32_t w0 = __byte_perm(__float_as_uint(vals[q][0]), __float_as_uint(vals[q][1]), 0x7632);
+            const uint32_t w1 = __byte_perm(__float_as_uint(vals[q][2]), __float_as_uint(vals[q][3]), 0x7632);
+            *reinterpret_cast<uint2 *>(img + q * piece_bytes + img_off(row, u >> 1, sbo) + (u & 1) * 8) =
+                make_uint2(w0, w1);
+        }
     }
 }
 
@@ -226,16 +256,69 @@ __device__ __forceinline__ void read8(uint32_t d, int Np, int c0, float rs, cons
     }
 }
 
+// As read8 for 4 columns [c0, c0+4).
+template <int MODE, int NACC, bool HL>
+__device__ __forceinline__ void read4(uint32_t d, int Np, int c0, float rs, const float *cs, float (&vh)[4],
+                                      float (&vl)[4])
+{
+    uint32_t r[NACC][4];
+#pragma unroll
+    for (int l = 0; l < NACC; ++l) tc::tmem_ld4_issue(d + uint32_t(l * Np + c0), r[l]);
+    tc::tmem_wait_ld();
+#pragma unroll
+    for (int l = 0; l < NACC; ++l)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) tc::order_after_wait(r[l][e]);
+    if constexpr (MODE == MODE_FLOAT_TF32) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            vh[e] = __uint_as_float(r[0][e]);
+            vl[e] = 0.f;
+        }
+    } else {
+        float t[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) t[e] = 0.f;
+#pragma unroll
+        for (int l = NACC - 1; l >= 1; --l)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) t[e] = (__uint_as_float(r[l][e]) + t[e]) * (1.f / 256.f);
+        const float4 c4 = *reinterpret_cast<const float4 *>(cs + c0);   // 16-byte aligned
+        const float csv[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float l0 = __uint_as_float(r[0][e]);
+            const float sc = rs * csv[e];
+            if (HL) {
+                const float h = l0 + t[e];
+                const float bp = h - l0;
+                vl[e] = ((l0 - (h - bp)) + (t[e] - bp)) * sc;
+                vh[e] = h * sc;
+            } else {
+                vh[e] = (l0 + t[e]) * sc;
+                vl[e] = 0.f;
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------------------
 // Pass kernel.  Rows of the batch are cut into tiles of 128 (= TMEM lanes); TPR threads
-// share a row, thread (q, row) = threadIdx.x = q*128 + row owning the 16-byte chunks
-// c = q, q+TPR, ... of the row (copy, slicing) and the 8-column chunks cc = q, q+TPR,
-// ... of the result (TMEM read, stores).  Warps w and w+4 see TMEM lane quarter w%4.
-// CTAs loop over tiles; the next tile's rows arrive by cp.async while the current
-// tile's MMAs and epilogue run.
+// share a row, thread (q, row) = threadIdx.x = q*128 + row owning the 4-element units
+// u = q, q+TPR, ... of the row (slicing) and the 4-column units of the result (TMEM read,
+// stores); Np is a multiple of 16, so every thread of a row gets the same number of units.
+// Warps w, w+4, ... see TMEM lane quarter w%4.  CTAs loop over tiles; the next tile's rows
+// arrive by cp.async while the current tile's MMAs and epilogue run.
 struct TcPassArgs {
-    int nfields, R, K, Np;          // K = n_d (contracted length), Np = K padded to 16
+    int nfields, R, K, Np;          // K = contracted length of this block, Np = padded block size
+    int Kout;                       // outputs of this block (K = Kout = n_d when not blocked)
+    int in_pitch, out_pitch;        // KFAST / NFAST row pitch (= n_d)
+    long in_off, out_off;           // block offsets: k0 (KFAST) or k0 * R (KSLOW, PAIR); same for n0
+    int acc;                        // add to out instead of overwriting it (K-blocks after the first)
+    const float *Fs, *Fs_lo;        // if set: scale the finished sums by f(Lambda) before storing
+    int f_noff;                     // first output mode of this block (index into Fs)
     long N;
+    FastDiv divR;                   // division by R (row of the batch -> field, row in field)
     const float *in;
     float *out;
     long lo_off;                    // hi + lo intermediates: offset of the lo plane (floats)
@@ -253,11 +336,11 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     constexpr int ES = MODE == MODE_FLOAT_TF32 ? 4 : 2;
-    constexpr int EPC = 16 / ES;                       // elements per 16-byte chunk
     constexpr int NACC = MODE == MODE_FLOAT_TF32 ? 1 : (SB > S ? S + 1 : S);
     constexpr int NT = kRows * TPR;          // compute threads; one more warp issues the MMAs
     constexpr int kBarHandoff = 1, kBarCompute = 2;
     const int Np = a.Np, Kp = a.Np;
+    const int nunit = Np / 4;                // 4-element units per row
     const uint32_t sbo = uint32_t(Kp) * ES * 8;          // bytes per 8-row group
     const uint32_t a_piece = uint32_t(kRows) * Kp * ES;
     const uint32_t b_piece = uint32_t(Np) * Kp * ES;
@@ -270,10 +353,9 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
     // Input staging.  KSLOW / PAIR: [k][row] (a warp touches 32 consecutive words; rows
     // k >= K are zero from the start and never written); KFAST: [row][Kp + 4] (16-byte
     // copies, read back conflict-free because (Kp + 4)/4 is odd; columns k >= K are
-    // masked when read).
-    // PAIR stages psi_m hi, psi_m lo, psi_n hi, psi_n lo; the others hi (and lo).  Pass 3
-    // stages f(Lambda) D1 ([col][row], hi and lo) in the same space after the first GEMM.
-    // NBUF staging buffers = tiles whose copies are in flight.
+    // masked when read).  PAIR stages psi_m hi, psi_m lo, psi_n hi, psi_n lo; the others
+    // hi (and lo).  Pass 3 stages f(Lambda) D1 ([col][row], hi and lo) in the same space
+    // after the first GEMM.  NBUF staging buffers = tiles whose copies are in flight.
     constexpr int NSTG = LOAD == LOAD_PAIR ? 4 : (HL ? 2 : 1);
     const int stg_len = kRows * (LOAD == LOAD_KFAST ? Kp + 4 : Kp);
     const int buf_len = max(NSTG * stg_len, DOUBLE ? 2 * Np * kRows : 0);
@@ -288,7 +370,6 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
     const int tid = threadIdx.x, warp = tid >> 5, row = tid & (kRows - 1), q = tid / kRows;
     const int set_cols = NACC * Np;
     const int ncols = NSETS * set_cols <= 32 ? 32 : NSETS * set_cols <= 64 ? 64 : NSETS * set_cols <= 128 ? 128 : NSETS * set_cols <= 256 ? 256 : 512;
-    const int nchunk = Kp / EPC;
 
     for (uint32_t i = tid * 16; i < a.img_bytes; i += (NT + 32) * 16) {
         *reinterpret_cast<uint4 *>(sB1 + i) = *reinterpret_cast<const uint4 *>(a.B1 + i);
@@ -312,80 +393,116 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
     auto set_tmem = [&](int st) { return tmem + uint32_t(st * set_cols); };
     auto set_A = [&](int st) { return sA0 + st * S * a_piece; };
 
-    const long rows = long(a.nfields) * a.R;
+    const long rows = long(a.nfields) * a.R;   // < 2^31 (checked on the host)
     const long ntiles = (rows + kRows - 1) / kRows;
-    const bool vec16 = ((a.K & 3) == 0) && ((a.N & 3) == 0) && ((a.lo_off & 3) == 0);
-    // Copy this thread's chunks of its row of tile t into staging buffer `stg` (rows past
-    // the end are skipped; the conversion treats them as zero).  Exactly one copy group is
-    // committed per call, empty or not, so that wait_group counts tiles.
+    const bool vec16 = ((a.K & 3) == 0) && ((a.in_pitch & 3) == 0) && ((a.in_off & 3) == 0) &&
+                       ((a.N & 3) == 0) && ((a.lo_off & 3) == 0);
+    const bool vec_out = ((a.out_pitch & 3) == 0) && ((a.out_off & 3) == 0) && ((a.N & 3) == 0) &&
+                         ((a.lo_off & 3) == 0);
+    // KSLOW / PAIR rows come 4 at a time (16-byte copies) when a field's rows are a
+    // multiple of 4: a group of 4 consecutive rows then never straddles two fields
+    const bool rvec = ((a.R & 3) == 0) && ((a.lo_off & 3) == 0);
+    // row `rl` of tile t -> (field pp, row rr of the field); false past the last row
+    auto locate = [&](long t, int rl, int &pp, int &rr) {
+        const long gg = t * kRows + rl;
+        if (t >= ntiles || gg >= rows) return false;
+        const uint32_t g = uint32_t(gg);
+        const uint32_t f = fast_div(g, a.divR);
+        pp = int(f);
+        rr = int(g - f * uint32_t(a.R));
+        return true;
+    };
+    // Copy tile t into staging buffer `stg` (rows past the end are skipped; the slicing
+    // treats them as zero).  Exactly one copy group is committed per call, empty or not,
+    // so that wait_group counts tiles.
     auto prefetch = [&](long t, float *stg) {
-        const long gg = t * kRows + row;
-        if (t >= ntiles || gg >= rows) {
-            tc::cp_async_commit();
-            return;
-        }
-        const int pp = int(gg / a.R), rr = int(gg - long(pp) * a.R);
-        if (LOAD == LOAD_PAIR) {
-            const int2 mn = a.pairs[pp];
-            const float *src[4] = {a.psi_hi + size_t(a.occ_off + mn.x) * a.N, a.psi_lo + size_t(a.occ_off + mn.x) * a.N,
-                                   a.psi_hi + size_t(mn.y) * a.N, a.psi_lo + size_t(mn.y) * a.N};
-            for (int c = q; c < nchunk; c += TPR)
-                for (int k = c * EPC; k < min(a.K, (c + 1) * EPC); ++k)
-#pragma unroll
-                    for (int w = 0; w < 4; ++w) tc::cp_async4(stg + w * stg_len + k * kRows + row, src[w] + size_t(k) * a.R + rr);
-        } else if (LOAD == LOAD_KSLOW) {
-            const float *src = a.in + size_t(pp) * a.N + rr;
-            for (int c = q; c < nchunk; c += TPR)
-                for (int k = c * EPC; k < min(a.K, (c + 1) * EPC); ++k) {
-                    tc::cp_async4(stg + k * kRows + row, src + size_t(k) * a.R);
-                    if (HL) tc::cp_async4(stg + stg_len + k * kRows + row, src + a.lo_off + size_t(k) * a.R);
-                }
-        } else {
-            const float *src = a.in + size_t(pp) * a.N + size_t(rr) * a.K;
-            float *dh = stg + row * (Kp + 4);
-            for (int c = q; c < nchunk; c += TPR) {
-                const int k1 = min(a.K, (c + 1) * EPC);
+        int pp, rr;
+        if (LOAD == LOAD_KFAST) {
+            if (locate(t, row, pp, rr)) {
+                const float *src = a.in + size_t(pp) * a.N + size_t(rr) * a.in_pitch + a.in_off;
+                float *dh = stg + row * (Kp + 4);
                 if (vec16) {
-                    for (int k = c * EPC; k < k1; k += 4) {
+                    for (int k = 4 * q; k < a.K; k += 4 * TPR) {
                         tc::cp_async16(dh + k, src + k);
                         if (HL) tc::cp_async16(dh + stg_len + k, src + a.lo_off + k);
                     }
+                } else {   // the thread copies the elements of its own units
+                    for (int u = q; 4 * u < a.K; u += TPR)
+                        for (int k = 4 * u; k < min(a.K, 4 * u + 4); ++k) {
+                            tc::cp_async4(dh + k, src + k);
+                            if (HL) tc::cp_async4(dh + stg_len + k, src + a.lo_off + k);
+                        }
+                }
+            }
+        } else if (rvec) {
+            // thread -> rows 4g..4g+3 (g = lane) and lines k = warp, warp + NT/32, ...:
+            // a warp copies 512 contiguous bytes per line
+            const int g4 = 4 * (tid & 31);
+            if (locate(t, g4, pp, rr)) {
+                if (LOAD == LOAD_PAIR) {
+                    const int2 mn = a.pairs[pp];
+                    const size_t o = size_t(rr) + a.in_off;
+                    const float *src[4] = {a.psi_hi + size_t(a.occ_off + mn.x) * a.N + o,
+                                           a.psi_lo + size_t(a.occ_off + mn.x) * a.N + o,
+                                           a.psi_hi + size_t(mn.y) * a.N + o, a.psi_lo + size_t(mn.y) * a.N + o};
+                    for (int k = warp; k < a.K; k += NT / 32)
+#pragma unroll
+                        for (int w = 0; w < 4; ++w)
+                            tc::cp_async16(stg + w * stg_len + k * kRows + g4, src[w] + size_t(k) * a.R);
                 } else {
-                    for (int k = c * EPC; k < k1; ++k) {
-                        tc::cp_async4(dh + k, src + k);
-                        if (HL) tc::cp_async4(dh + stg_len + k, src + a.lo_off + k);
+                    const float *src = a.in + size_t(pp) * a.N + a.in_off + rr;
+                    for (int k = warp; k < a.K; k += NT / 32) {
+                        tc::cp_async16(stg + k * kRows + g4, src + size_t(k) * a.R);
+                        if (HL) tc::cp_async16(stg + stg_len + k * kRows + g4, src + a.lo_off + size_t(k) * a.R);
                     }
                 }
+            }
+        } else if (locate(t, row, pp, rr)) {
+            if (LOAD == LOAD_PAIR) {
+                const int2 mn = a.pairs[pp];
+                const size_t o = size_t(rr) + a.in_off;
+                const float *src[4] = {a.psi_hi + size_t(a.occ_off + mn.x) * a.N + o,
+                                       a.psi_lo + size_t(a.occ_off + mn.x) * a.N + o,
+                                       a.psi_hi + size_t(mn.y) * a.N + o, a.psi_lo + size_t(mn.y) * a.N + o};
+                for (int u = q; 4 * u < a.K; u += TPR)   // the elements of its own units
+                    for (int k = 4 * u; k < min(a.K, 4 * u + 4); ++k)
+#pragma unroll
+                        for (int w = 0; w < 4; ++w)
+                            tc::cp_async4(stg + w * stg_len + k * kRows + row, src[w] + size_t(k) * a.R);
+            } else {
+                const float *src = a.in + size_t(pp) * a.N + a.in_off + rr;
+                for (int u = q; 4 * u < a.K; u += TPR)
+                    for (int k = 4 * u; k < min(a.K, 4 * u + 4); ++k) {
+                        tc::cp_async4(stg + k * kRows + row, src + size_t(k) * a.R);
+                        if (HL) tc::cp_async4(stg + stg_len + k * kRows + row, src + a.lo_off + size_t(k) * a.R);
+                    }
             }
         }
         tc::cp_async_commit();
     };
-    // Staged values (hi, lo) of chunk c (EPC elements) of this thread's row.  KFAST rows are
-    // read as float4 (conflict-free with the odd (Kp + 4)/4 row pitch).
-    auto staged_chunk = [&](const float *stg, int c, float (&hi)[8], float (&lo)[8]) {
+    // Staged values (hi, lo) of unit u (elements 4u..4u+3) of this thread's row.
+    auto staged_unit = [&](const float *stg, int u, float (&hi)[4], float (&lo)[4]) {
+        const int k0 = 4 * u;
         if constexpr (LOAD == LOAD_KFAST) {
-#pragma unroll
-            for (int j = 0; j < EPC; j += 4) {
-                const float4 h = *reinterpret_cast<const float4 *>(stg + row * (Kp + 4) + c * EPC + j);
-                hi[j] = h.x; hi[j + 1] = h.y; hi[j + 2] = h.z; hi[j + 3] = h.w;
-                if (HL) {
-                    const float4 l = *reinterpret_cast<const float4 *>(stg + stg_len + row * (Kp + 4) + c * EPC + j);
-                    lo[j] = l.x; lo[j + 1] = l.y; lo[j + 2] = l.z; lo[j + 3] = l.w;
-                } else {
-                    lo[j] = lo[j + 1] = lo[j + 2] = lo[j + 3] = 0.f;
-                }
+            const float4 h = *reinterpret_cast<const float4 *>(stg + row * (Kp + 4) + k0);
+            hi[0] = h.x; hi[1] = h.y; hi[2] = h.z; hi[3] = h.w;
+            if (HL) {
+                const float4 l = *reinterpret_cast<const float4 *>(stg + stg_len + row * (Kp + 4) + k0);
+                lo[0] = l.x; lo[1] = l.y; lo[2] = l.z; lo[3] = l.w;
+            } else {
+                lo[0] = lo[1] = lo[2] = lo[3] = 0.f;
             }
             // columns k >= K of a KFAST row are not copied, and in pass 3 they still hold
             // the previous tile's middle values (staged over the same space): zero them
-            if ((c + 1) * EPC > a.K) {
+            if (k0 + 4 > a.K) {
 #pragma unroll
-                for (int e = 0; e < EPC; ++e)
-                    if (c * EPC + e >= a.K) hi[e] = lo[e] = 0.f;
+                for (int e = 0; e < 4; ++e)
+                    if (k0 + e >= a.K) hi[e] = lo[e] = 0.f;
             }
         } else {
 #pragma unroll
-            for (int e = 0; e < EPC; ++e) {
-                const int k = c * EPC + e;
+            for (int e = 0; e < 4; ++e) {
+                const int k = k0 + e;
                 if (LOAD == LOAD_PAIR) {
                     const float ah = stg[k * kRows + row], al = stg[stg_len + k * kRows + row];
                     const float bh = stg[2 * stg_len + k * kRows + row], bl = stg[3 * stg_len + k * kRows + row];
@@ -397,6 +514,29 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
                 }
             }
         }
+    };
+    // Largest |hi| over this thread's units (the row scale needs only the leading parts).
+    auto staged_max = [&](const float *stg) {
+        float mx = 0.f;
+        for (int u = q; u < nunit; u += TPR) {
+            const int k0 = 4 * u;
+            if constexpr (LOAD == LOAD_KFAST) {
+                const float4 h = *reinterpret_cast<const float4 *>(stg + row * (Kp + 4) + k0);
+                const float v[4] = {h.x, h.y, h.z, h.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (k0 + e < a.K) mx = fmaxf(mx, fabsf(v[e]));
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int k = k0 + e;
+                    const float v = LOAD == LOAD_PAIR ? stg[k * kRows + row] * stg[2 * stg_len + k * kRows + row]
+                                                      : stg[k * kRows + row];
+                    mx = fmaxf(mx, fabsf(v));
+                }
+            }
+        }
+        return mx;
     };
     // Row maximum from the per-thread partial maxima of the TPR threads of a row.
     auto row_max = [&](float part) {
@@ -411,11 +551,11 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
         sc = 1.f;
         rs = 1.f;
         if (MODE == MODE_FIXED_BF16) {
-            int e = 0;
-            if (mx > 0.f) frexpf(mx, &e);
-            e = max(e, -100);   // rows below 2^-100 are flushed to zero slices
-            sc = ldexpf(1.f, 7 - e);
-            rs = ldexpf(1.f, e - 7);
+            // e with mx = f 2^e, f in [0.5, 1) (as frexp), from the biased exponent field
+            int e = int((__float_as_uint(mx) >> 23) & 0xffu) - 126;
+            e = max(e, -100);   // rows below 2^-100 (and zero rows) are flushed to zero slices
+            sc = __uint_as_float(uint32_t(127 + 7 - e) << 23);   // 2^(7 - e), a normal number
+            rs = __uint_as_float(uint32_t(127 - 7 + e) << 23);   // 2^(e - 7)
         }
     };
     // Compute threads: publish the A slices written so far to the tensor core and hand
@@ -455,35 +595,82 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
         ph ^= 1u << st;
         tc::tc_fence_after();
     };
-    // Epilogue of tile t from TMEM set st: own 8-column chunks -> global.
+    // Epilogue of tile t from TMEM set st: own 4-column units -> global (added to the
+    // stored partial sums for K-blocks after the first; scaled by f(Lambda) when Fs is set).
     auto epilogue = [&](long t, int st, float rs_out, const float *cs_out) {
-        const long gg = t * kRows + row;
-        const bool act = gg < rows;
-        const int pp = act ? int(gg / a.R) : 0;
-        const int rr = act ? int(gg - long(pp) * a.R) : 0;
-        float *out = a.out + size_t(pp) * a.N;
-        for (int cc = q; cc < Np / 8; cc += TPR) {
-            float v[8], vlo[8];
-            read8<MODE, NACC, HL>(set_tmem(st) + lane_q, Np, cc * 8, rs_out, cs_out, v, vlo);
+        int pp = 0, rr = 0;
+        const bool act = locate(t, row, pp, rr);
+        float *out = a.out + size_t(pp) * a.N + a.out_off;
+        for (int u = q; u < nunit; u += TPR) {
+            float v[4], vlo[4];
+            read4<MODE, NACC, HL>(set_tmem(st) + lane_q, Np, 4 * u, rs_out, cs_out, v, vlo);
             if (!act) continue;
-            const int c0 = cc * 8;
-            if (STORE == STORE_NFAST && vec16 && c0 + 8 <= a.K) {
-                float4 *o = reinterpret_cast<float4 *>(out + size_t(rr) * a.K + c0);
-                o[0] = make_float4(v[0], v[1], v[2], v[3]);
-                o[1] = make_float4(v[4], v[5], v[6], v[7]);
-                if (HL) {
-                    float4 *ol = reinterpret_cast<float4 *>(out + a.lo_off + size_t(rr) * a.K + c0);
-                    ol[0] = make_float4(vlo[0], vlo[1], vlo[2], vlo[3]);
-                    ol[1] = make_float4(vlo[4], vlo[5], vlo[6], vlo[7]);
+            const int c0 = 4 * u;
+            if (!a.acc && !a.Fs) {   // plain store of the unit
+                if (STORE == STORE_NFAST && vec_out && c0 + 4 <= a.Kout) {
+                    float *o = out + size_t(rr) * a.out_pitch + c0;
+                    *reinterpret_cast<float4 *>(o) = make_float4(v[0], v[1], v[2], v[3]);
+                    if (HL) *reinterpret_cast<float4 *>(o + a.lo_off) = make_float4(vlo[0], vlo[1], vlo[2], vlo[3]);
+                } else {
+                    const size_t step = STORE == STORE_NSLOW ? size_t(a.R) : 1;
+                    float *o = out + (STORE == STORE_NSLOW ? size_t(c0) * a.R + rr : size_t(rr) * a.out_pitch + c0);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        if (c0 + e < a.Kout) {
+                            o[0] = v[e];
+                            if (HL) o[a.lo_off] = vlo[e];
+                        }
+                        o += step;
+                    }
                 }
+                continue;
+            }
+            // element e of this unit: out[idx(e)] (hi) and out[lo_off + idx(e)] (lo)
+            auto idx = [&](int e) {
+                return STORE == STORE_NSLOW ? size_t(c0 + e) * a.R + rr : size_t(rr) * a.out_pitch + c0 + e;
+            };
+            if (a.acc) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    if (c0 + e >= a.Kout) continue;
+                    const float oh = out[idx(e)];
+                    if (HL) {   // (oh + ol) + (v + vlo), renormalised
+                        const float ol = out[a.lo_off + idx(e)];
+                        const float sh = oh + v[e], bp = sh - oh;
+                        const float err = (oh - (sh - bp)) + (v[e] - bp);
+                        const float sl = (ol + vlo[e]) + err;
+                        v[e] = sh + sl;
+                        vlo[e] = sl - (v[e] - sh);
+                    } else {
+                        v[e] += oh;
+                    }
+                }
+            }
+            if (a.Fs) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    if (c0 + e >= a.Kout) continue;
+                    const size_t fi = size_t(a.f_noff + c0 + e) * a.R + rr;
+                    const float fh = a.Fs[fi], fl = a.Fs_lo[fi];
+                    if (HL) {
+                        const float x = v[e] * fh;
+                        vlo[e] = fmaf(v[e], fh, -x) + fmaf(v[e], fl, vlo[e] * fh);
+                        v[e] = x;
+                    } else {
+                        v[e] = fmaf(v[e], fh, v[e] * fl);
+                    }
+                }
+            }
+            if (STORE == STORE_NFAST && vec_out && c0 + 4 <= a.Kout) {
+                *reinterpret_cast<float4 *>(out + idx(0)) = make_float4(v[0], v[1], v[2], v[3]);
+                if (HL)
+                    *reinterpret_cast<float4 *>(out + a.lo_off + idx(0)) = make_float4(vlo[0], vlo[1], vlo[2], vlo[3]);
             } else {
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int col = c0 + e;
-                    if (col < a.K) {
-                        const size_t idx = (STORE == STORE_NSLOW) ? size_t(col) * a.R + rr : size_t(rr) * a.K + col;
-                        out[idx] = v[e];
-                        if (HL) out[a.lo_off + idx] = vlo[e];
+                for (int e = 0; e < 4; ++e) {
+                    if (c0 + e < a.Kout) {
+                        out[idx(e)] = v[e];
+                        if (HL) out[a.lo_off + idx(e)] = vlo[e];
                     }
                 }
             }
@@ -508,30 +695,22 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
             epilogue(prev_tile, prev_set, prev_rs, prev_cs);
             prev_tile = -1;
         }
-        const long g = tile * kRows + row;
-        const bool active = g < rows;
-        const int p = active ? int(g / a.R) : 0;
-        const int r = active ? int(g - long(p) * a.R) : 0;
+        int p = 0, r = 0;
+        const bool active = locate(tile, row, p, r);
         float *stg = stg0 + (it % NBUF) * buf_len;
         uint8_t *sA = set_A(st);
         // ---- slice tile -> A[st] (A[st] was last read by the GEMMs of tile it-2,
         //      which completed before that tile's epilogue) ----
         tc::cp_async_wait_group<NBUF - 1>();  // this tile's copies (one group per tile) landed
-        float mx = 0.f;
-        for (int c = q; c < nchunk; c += TPR) {
-            float hi[8], lo[8];
-            staged_chunk(stg, c, hi, lo);
-#pragma unroll
-            for (int e = 0; e < EPC; ++e) mx = fmaxf(mx, fabsf(hi[e]));
-        }
-        mx = row_max(active ? mx : 0.f);
+        if (LOAD != LOAD_KFAST && rvec) tc::bar_sync(kBarCompute, NT);   // rows copied by other threads
+        const float mx = row_max(active ? staged_max(stg) : 0.f);
         float s_in, rs1;
         scales(mx, s_in, rs1);
-        for (int c = q; c < nchunk; c += TPR) {
-            float vals[4][8], hi[8], lo[8];
-            staged_chunk(stg, c, hi, lo);
+        for (int u = q; u < nunit; u += TPR) {
+            float vals[4][4], hi[4], lo[4];
+            staged_unit(stg, u, hi, lo);
 #pragma unroll
-            for (int e = 0; e < EPC; ++e) {
+            for (int e = 0; e < 4; ++e) {
                 float qv[4];
                 if (!active) hi[e] = lo[e] = 0.f;
                 if (MODE == MODE_FLOAT_TF32) split_tf32(hi[e], lo[e], qv);
@@ -539,13 +718,13 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
 #pragma unroll
                 for (int t2 = 0; t2 < 4; ++t2) vals[t2][e] = qv[t2];
             }
-            store_chunk<ES, S>(sA, a_piece, row, c, sbo, vals);
+            store_unit<ES, S>(sA, a_piece, row, u, sbo, vals);
         }
-        // own chunks of this staging buffer consumed: fetch the tile NBUF steps ahead
-        if (!DOUBLE) prefetch(tile + long(NBUF) * gridDim.x, stg);
         // ---- first GEMM of this tile; TMEM set st was last read by the epilogue of
         //      tile it-2, which every thread finished before this hand-off ----
         if (handoff()) break;
+        // every thread has consumed this staging buffer: fetch the tile NBUF steps ahead
+        if (!DOUBLE) prefetch(tile + long(NBUF) * gridDim.x, stg);
         // ---- epilogue of the previous tile, overlapping this tile's GEMM ----
         if (prev_tile >= 0) {
             if (DOUBLE) wait_bar(bar2 + prev_set, ph2, prev_set);
@@ -555,27 +734,27 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
         float rs_out = rs1;
         const float *cs_out = cs1;
         if (DOUBLE) {
-            // D1 * f(Lambda) -> staging ([col][row], own columns) -> A[st] (its first GEMM
+            // D1 * f(Lambda) -> staging ([col][row], own units) -> A[st] (its first GEMM
             // is complete) -> second GEMM into the same TMEM set
             wait_bar(bar1 + st, ph1, st);
             float *mid_hi = stg, *mid_lo = stg + Np * kRows;
             float mx2 = 0.f;
-            for (int cc = q; cc < Np / 8; cc += TPR) {
-                float v[8], vlo[8], fh[8], fl[8];
-                read8<MODE, NACC, HL>(set_tmem(st) + lane_q, Np, cc * 8, rs1, cs1, v, vlo);
+            for (int u = q; u < nunit; u += TPR) {
+                float v[4], vlo[4], fh[4], fl[4];
+                read4<MODE, NACC, HL>(set_tmem(st) + lane_q, Np, 4 * u, rs1, cs1, v, vlo);
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int col = cc * 8 + e;
+                for (int e = 0; e < 4; ++e) {
+                    const int col = 4 * u + e;
                     fh[e] = 0.f;
                     fl[e] = 0.f;
-                    if (active && col < a.K) {
+                    if (active && col < a.Kout) {
                         const size_t fi = size_t(col) * a.R + r;
                         fh[e] = a.F[fi];
                         fl[e] = a.Flo[fi];
                     }
                 }
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
+                for (int e = 0; e < 4; ++e) {
                     float x, xl = 0.f;
                     if (HL) {   // (v + vlo)(fh + fl) as x + xl
                         x = v[e] * fh[e];
@@ -584,30 +763,26 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
                         x = fmaf(v[e], fh[e], v[e] * fl[e]);
                     }
                     mx2 = fmaxf(mx2, fabsf(x));
-                    mid_hi[(cc * 8 + e) * kRows + row] = x;
-                    mid_lo[(cc * 8 + e) * kRows + row] = xl;
+                    mid_hi[(4 * u + e) * kRows + row] = x;
+                    mid_lo[(4 * u + e) * kRows + row] = xl;
                 }
             }
             tc::tc_fence_before();
             mx2 = row_max(mx2);   // (its sync also orders these TMEM reads before GEMM 2)
             float s2, rs2;
             scales(mx2, s2, rs2);
-            for (int cc = q; cc < Np / 8; cc += TPR) {
+            for (int u = q; u < nunit; u += TPR) {   // the same units: own values only
+                float vals[4][4];
 #pragma unroll
-                for (int h = 0; h < 8 / EPC; ++h) {
-                    const int c = cc * (8 / EPC) + h;
-                    float vals[4][8];
+                for (int e = 0; e < 4; ++e) {
+                    const int k = 4 * u + e;
+                    float qv[4];
+                    if (MODE == MODE_FLOAT_TF32) split_tf32(mid_hi[k * kRows + row], 0.f, qv);
+                    else slice_fixed<S>(mid_hi[k * kRows + row], mid_lo[k * kRows + row], s2, qv);
 #pragma unroll
-                    for (int e = 0; e < EPC; ++e) {
-                        const int k = c * EPC + e;
-                        float qv[4];
-                        if (MODE == MODE_FLOAT_TF32) split_tf32(mid_hi[k * kRows + row], 0.f, qv);
-                        else slice_fixed<S>(mid_hi[k * kRows + row], mid_lo[k * kRows + row], s2, qv);
-#pragma unroll
-                        for (int t2 = 0; t2 < 4; ++t2) vals[t2][e] = qv[t2];
-                    }
-                    store_chunk<ES, S>(sA, a_piece, row, c, sbo, vals);
+                    for (int t2 = 0; t2 < 4; ++t2) vals[t2][e] = qv[t2];
                 }
+                store_unit<ES, S>(sA, a_piece, row, u, sbo, vals);
             }
             const bool stop = handoff();
             // every thread is past the middle step, whose staging ([col][row]) overlaps
@@ -877,24 +1052,56 @@ int launch_tc_pass(Plan &P, int kind, int prec, const TcPassArgs &a, cudaStream_
     return launch_tc_pass_nb<MODE, S, SB, HL, LOAD, STORE, DOUBLE, 1, 1>(P, kind, prec, a, s);
 }
 
+// One launch of pass kernel `kind` (0..4 = P1..P5; 5 = P3's forward half alone, 6 = its
+// inverse half alone, used when the y axis is cut into blocks).
+template <int MODE, int S, int SB, bool HL>
+int launch_kind(Plan &P, int kind, int prec, const TcPassArgs &a, cudaStream_t s)
+{
+    switch (kind) {
+    case 0: return launch_tc_pass<MODE, S, SB, HL, LOAD_PAIR, STORE_NSLOW, false>(P, EXX_TIMING_PASS1, prec, a, s);
+    case 1: return launch_tc_pass<MODE, S, SB, HL, LOAD_KFAST, STORE_NSLOW, false>(P, EXX_TIMING_PASS2, prec, a, s);
+    case 2: return launch_tc_pass<MODE, S, SB, HL, LOAD_KFAST, STORE_NFAST, true>(P, EXX_TIMING_PASS3, prec, a, s);
+    case 3: return launch_tc_pass<MODE, S, SB, HL, LOAD_KSLOW, STORE_NFAST, false>(P, EXX_TIMING_PASS4, prec, a, s);
+    case 4: return launch_tc_pass<MODE, S, SB, HL, LOAD_KSLOW, STORE_NSLOW, false>(P, EXX_TIMING_PASS5, prec, a, s);
+    default: return launch_tc_pass<MODE, S, SB, HL, LOAD_KFAST, STORE_NFAST, false>(P, EXX_TIMING_PASS3, prec, a, s);
+    }
+}
+
 template <int MODE, int S, int SB, bool HL>
 int solve_batch_t(Plan &P, int prec, const int2 *pairs_d, int nfields, float *bufA, float *bufB, cudaStream_t s)
 {
     float *src = nullptr, *dst = bufA;
+    // passes as (kind, B slot): P3 is one kernel (two GEMMs) unless y is cut into blocks
+    const bool ycut = P.tc_ysplit[prec] != 0;
+    int kinds[6], slots[6], np = 0;
     for (int pass = 0; pass < 5; ++pass) {
-        PassGeom g = pass_geom(P.n, pass);
+        if (pass == 2 && ycut) {
+            kinds[np] = 5; slots[np++] = 2;
+            kinds[np] = 6; slots[np++] = 3;
+        } else {
+            kinds[np] = pass;
+            slots[np++] = pass <= 2 ? pass : pass + 1;   // fused P3 uses slots 2 (fwd) and 3 (inv)
+        }
+    }
+    const int axis_of[6] = {2, 0, 1, 1, 0, 2};
+    for (int i = 0; i < np; ++i) {
+        const int kind = kinds[i], slot = slots[i];
+        const PassGeom g = pass_geom(P.n, kind >= 5 ? 2 : kind);
+        const int d = axis_of[slot], nd = P.n[d], nb = P.tc_nblk[prec][d], bs = P.tc_bsz[prec][d];
         TcPassArgs a{};
         a.nfields = nfields;
         a.R = g.R;
-        a.K = g.K;
-        a.Np = pad16(g.K);
+        a.divR = make_fastdiv(uint32_t(g.R));
+        if (long(nfields) * g.R >= (1L << 31)) {
+            set_error("split-precision pass: more than 2^31 rows in one batch");
+            return EXX_ERR_UNSUPPORTED;
+        }
+        a.Np = pad16(bs);
         a.N = P.N;
         a.in = src;
         a.out = dst;
+        a.in_pitch = a.out_pitch = nd;
         a.lo_off = HL ? P.tc_lo_off : 0;
-        const int slot = pass <= 2 ? pass : pass + 1;  // P3 uses slots 2 (fwd) and 3 (inv)
-        a.B1 = static_cast<const uint8_t *>(P.Btc[prec][slot].p);
-        a.B2 = pass == 2 ? static_cast<const uint8_t *>(P.Btc[prec][3].p) : nullptr;
         a.img_bytes = uint32_t(image_bytes(prec, a.Np));
         a.F = static_cast<const float *>(P.F32.p);
         a.Flo = a.F + P.N;
@@ -903,15 +1110,23 @@ int solve_batch_t(Plan &P, int prec, const int2 *pairs_d, int nfields, float *bu
         a.occ_off = P.tc_occ_off;
         a.pairs = pairs_d;
         a.err = static_cast<int *>(P.err_d.p);
-        int rc;
-        switch (pass) {
-        case 0: rc = launch_tc_pass<MODE, S, SB, HL, LOAD_PAIR, STORE_NSLOW, false>(P, EXX_TIMING_PASS1, prec, a, s); break;
-        case 1: rc = launch_tc_pass<MODE, S, SB, HL, LOAD_KFAST, STORE_NSLOW, false>(P, EXX_TIMING_PASS2, prec, a, s); break;
-        case 2: rc = launch_tc_pass<MODE, S, SB, HL, LOAD_KFAST, STORE_NFAST, true>(P, EXX_TIMING_PASS3, prec, a, s); break;
-        case 3: rc = launch_tc_pass<MODE, S, SB, HL, LOAD_KSLOW, STORE_NFAST, false>(P, EXX_TIMING_PASS4, prec, a, s); break;
-        default: rc = launch_tc_pass<MODE, S, SB, HL, LOAD_KSLOW, STORE_NSLOW, false>(P, EXX_TIMING_PASS5, prec, a, s); break;
-        }
-        if (rc) return rc;
+        const uint8_t *img1 = static_cast<const uint8_t *>(P.Btc[prec][slot].p);
+        const bool kslow_in = g.load != LOAD_KFAST, nslow_out = g.store == STORE_NSLOW;
+        for (int h = 0; h < nb; ++h)
+            for (int c = 0; c < nb; ++c) {   // K-blocks in order: the first writes, the others add
+                a.K = std::min(bs, nd - c * bs);
+                a.Kout = std::min(bs, nd - h * bs);
+                a.in_off = kslow_in ? long(c) * bs * g.R : long(c) * bs;
+                a.out_off = nslow_out ? long(h) * bs * g.R : long(h) * bs;
+                a.acc = c > 0;
+                a.B1 = img1 + size_t(c * nb + h) * a.img_bytes;
+                a.B2 = kind == 2 ? static_cast<const uint8_t *>(P.Btc[prec][3].p) : nullptr;
+                const bool scale = kind == 5 && c == nb - 1;   // the sums of this block are complete
+                a.Fs = scale ? a.F : nullptr;
+                a.Fs_lo = scale ? a.Flo : nullptr;
+                a.f_noff = h * bs;
+                if (int rc = launch_kind<MODE, S, SB, HL>(P, kind, prec, a, s)) return rc;
+            }
         src = dst;
         dst = (dst == bufA) ? bufB : bufA;
     }
@@ -921,79 +1136,106 @@ int solve_batch_t(Plan &P, int prec, const int2 *pairs_d, int nfields, float *bu
 
 }  // namespace
 
+// Does every pass on axis d fit on chip with blocks of Np (padded) points?  x is read by
+// passes 2 (KFAST) and 4 (KSLOW), y by pass 3 (KFAST; two GEMMs in one kernel unless
+// split), z by passes 1 (pair products) and 5 (KSLOW).
+static bool axis_fits(int prec, int d, int Np, bool split)
+{
+    size_t need = 0;
+    if (d == 0) need = std::max(pass_smem(prec, Np, false, LOAD_KFAST), pass_smem(prec, Np, false, LOAD_KSLOW));
+    if (d == 1) need = pass_smem(prec, Np, !split, LOAD_KFAST);
+    if (d == 2) need = std::max(pass_smem(prec, Np, false, LOAD_PAIR), pass_smem(prec, Np, false, LOAD_KSLOW));
+    return need <= 232448 && tmem_cols(prec, Np) <= 512;
+}
+
 int tc_upload(Plan &P, int prec)
 {
     const PrecInfo pi = prec_info(prec);
     const int axis_of[6] = {2, 0, 1, 1, 0, 2};
     const int inv_of[6] = {0, 0, 0, 1, 1, 1};
+    // Long axes are cut into nb blocks of b = ceil(n / nb) points: a mode product then
+    // becomes nb x nb block products, out_h = sum_c in_c V_ch, summed in hi/lo FP32.
+    // Pass 3 runs its two GEMMs in one kernel when y fits whole with both images on chip,
+    // else as two kernels (forward with the f(Lambda) scaling, inverse).
+    int nblk[3], bsz[3];
+    const bool ysplit = !axis_fits(prec, 1, pad16(P.n[1]), false);
     for (int d = 0; d < 3; ++d) {
-        const int Np = pad16(P.n[d]);
-        // the smallest variant of each pass on this axis must fit: x is read by passes 2
-        // (KFAST) and 4 (KSLOW), y by pass 3 (KFAST, two GEMMs), z by passes 1 (pair
-        // products) and 5 (KSLOW)
-        size_t need = 0;
-        if (d == 0) need = std::max(pass_smem(prec, Np, false, LOAD_KFAST), pass_smem(prec, Np, false, LOAD_KSLOW));
-        if (d == 1) need = pass_smem(prec, Np, true, LOAD_KFAST);
-        if (d == 2) need = std::max(pass_smem(prec, Np, false, LOAD_PAIR), pass_smem(prec, Np, false, LOAD_KSLOW));
-        if (need > 232448 || tmem_cols(prec, Np) > 512) {
+        int nb = 1;
+        while (nb <= 16 && !axis_fits(prec, d, pad16((P.n[d] + nb - 1) / nb), d == 1 && ysplit)) ++nb;
+        if (nb > 16) {
             set_error("split precision: grid axis too long for the on-chip operand images of this build");
             return EXX_ERR_UNSUPPORTED;
         }
+        nblk[d] = nb;
+        bsz[d] = (P.n[d] + nb - 1) / nb;
     }
     for (int slot = 0; slot < 6; ++slot) {
-        const int d = axis_of[slot], nd = P.n[d], Np = pad16(nd);
+        const int d = axis_of[slot], nd = P.n[d], nb = nblk[d], bs = bsz[d], Np = pad16(bs);
         const uint32_t sbo = uint32_t(Np) * pi.es * 8;
         const size_t piece = size_t(Np) * Np * pi.es;
+        const size_t ib = image_bytes(prec, Np);
         const int epc = 16 / pi.es;
-        std::vector<uint8_t> img(image_bytes(prec, Np), 0);
-        // coefficient of output mode n from input k: forward V(k, n), inverse V(n, k)
-        auto coef = [&](int n, int k) {
-            if (n >= nd || k >= nd) return 0.0;
-            return inv_of[slot] ? P.V[d][n + size_t(nd) * k] : P.V[d][k + size_t(nd) * n];
-        };
-        auto put = [&](int q, int n, int k, float v) {
-            size_t off = piece * q + img_off(n, k / epc, sbo) + size_t(k % epc) * pi.es;
-            if (pi.es == 4) {
-                std::memcpy(&img[off], &v, 4);
-            } else {
-                uint32_t u;
-                std::memcpy(&u, &v, 4);
-                uint16_t h = uint16_t(u >> 16);   // v is bf16-exact (a small integer)
-                std::memcpy(&img[off], &h, 2);
-            }
-        };
-        std::vector<float> cs(Np, 1.0f);
-        for (int n = 0; n < Np; ++n) {
-            if (pi.mode == MODE_FIXED_BF16) {
-                double mx = 0.0;
-                for (int k = 0; k < Np; ++k) mx = std::max(mx, std::fabs(coef(n, k)));
-                int e = 0;
-                if (mx > 0.0) std::frexp(mx, &e);
-                const double sc = std::ldexp(1.0, 7 - e);
-                cs[n] = float(std::ldexp(1.0, e - 7));
-                for (int k = 0; k < Np; ++k) {
-                    double t = coef(n, k) * sc;
-                    for (int s = 0; s < pi.SB; ++s) {   // t = q0 + q1/2^8 + q2/2^16 + ...
-                        const double q = std::nearbyint(t);
-                        put(s, n, k, float(q));
-                        t = (t - q) * 256.0;
+        std::vector<uint8_t> all(ib * nb * nb, 0);
+        for (int c = 0; c < nb; ++c)
+            for (int h = 0; h < nb; ++h) {
+                uint8_t *img = all.data() + ib * size_t(c * nb + h);
+                // coefficient of output mode n0+n from input k0+k: forward V(k, n), inverse V(n, k)
+                const int k0 = c * bs, n0 = h * bs;
+                const int kl = std::min(bs, nd - k0), nl = std::min(bs, nd - n0);
+                auto coef = [&](int n, int k) {
+                    if (n >= nl || k >= kl) return 0.0;
+                    const size_t gn = size_t(n0 + n), gk = size_t(k0 + k);
+                    return inv_of[slot] ? P.V[d][gn + size_t(nd) * gk] : P.V[d][gk + size_t(nd) * gn];
+                };
+                auto put = [&](int q, int n, int k, float v) {
+                    size_t off = piece * q + img_off(n, k / epc, sbo) + size_t(k % epc) * pi.es;
+                    if (pi.es == 4) {
+                        std::memcpy(&img[off], &v, 4);
+                    } else {
+                        uint32_t u;
+                        std::memcpy(&u, &v, 4);
+                        uint16_t hb = uint16_t(u >> 16);   // v is bf16-exact (a small integer)
+                        std::memcpy(&img[off], &hb, 2);
+                    }
+                };
+                std::vector<float> cs(Np, 1.0f);
+                for (int n = 0; n < Np; ++n) {
+                    if (pi.mode == MODE_FIXED_BF16) {
+                        double mx = 0.0;
+                        for (int k = 0; k < Np; ++k) mx = std::max(mx, std::fabs(coef(n, k)));
+                        int e = 0;
+                        if (mx > 0.0) std::frexp(mx, &e);
+                        const double sc = std::ldexp(1.0, 7 - e);
+                        cs[n] = float(std::ldexp(1.0, e - 7));
+                        for (int k = 0; k < Np; ++k) {
+                            double t = coef(n, k) * sc;
+                            for (int q = 0; q < pi.SB; ++q) {   // t = q0 + q1/2^8 + q2/2^16 + ...
+                                const double qq = std::nearbyint(t);
+                                put(q, n, k, float(qq));
+                                t = (t - qq) * 256.0;
+                            }
+                        }
+                    } else {
+                        for (int k = 0; k < Np; ++k) {
+                            double rem = coef(n, k);
+                            for (int q = 0; q < pi.SB; ++q) {
+                                float pv = host_tf32(rem);
+                                rem -= double(pv);
+                                put(q, n, k, pv);
+                            }
+                        }
                     }
                 }
-            } else {
-                for (int k = 0; k < Np; ++k) {
-                    double rem = coef(n, k);
-                    for (int s = 0; s < pi.SB; ++s) {
-                        float pv = host_tf32(rem);
-                        rem -= double(pv);
-                        put(s, n, k, pv);
-                    }
-                }
+                if (pi.mode == MODE_FIXED_BF16) std::memcpy(&img[piece * pi.SB], cs.data(), size_t(Np) * 4);
             }
-        }
-        if (pi.mode == MODE_FIXED_BF16) std::memcpy(&img[piece * pi.SB], cs.data(), size_t(Np) * 4);
-        if (int rc = dev_reserve(P.Btc[prec][slot], img.size())) return rc;
-        EXX_CUDA(cudaMemcpy(P.Btc[prec][slot].p, img.data(), img.size(), cudaMemcpyHostToDevice));
+        if (int rc = dev_reserve(P.Btc[prec][slot], all.size())) return rc;
+        EXX_CUDA(cudaMemcpy(P.Btc[prec][slot].p, all.data(), all.size(), cudaMemcpyHostToDevice));
     }
+    for (int d = 0; d < 3; ++d) {
+        P.tc_nblk[prec][d] = nblk[d];
+        P.tc_bsz[prec][d] = bsz[d];
+    }
+    P.tc_ysplit[prec] = ysplit;
     if (int rc = dev_reserve(P.err_d, 16)) return rc;
     EXX_CUDA(cudaMemset(P.err_d.p, 0, 16));
     return EXX_OK;

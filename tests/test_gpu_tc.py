@@ -152,3 +152,40 @@ def test_split_config2_sampled_columns(exx, cfg2, name):
     assert err_cols < tol_v
     assert err_full < tol_v
     assert abs(e - e64) <= tol_e * abs(e64)
+
+
+LONG = [dict(n=(72, 20, 24), bc=(1, 0, 1)), dict(n=(20, 72, 16), bc=(0, 1, 1)), dict(n=(16, 20, 144), bc=(1, 1, 0)),
+        dict(n=(20, 100, 20), bc=(0, 0, 1)), dict(n=(130, 16, 12), bc=(1, 0, 0)), dict(n=(12, 16, 150), bc=(0, 1, 1))]
+
+
+@pytest.mark.parametrize("name", ["bf16x10", "bf16x6", "tf32x3"])
+@pytest.mark.parametrize("case", LONG, ids=lambda c: "x".join(map(str, c["n"])))
+def test_split_long_axes_match_oracle(exx, name, case):
+    """Axes longer than one on-chip operand image: cut into blocks whose products are
+    summed in hi/lo FP32 (y alone may also just split pass 3 into two kernels)."""
+    code, tol_v, tol_e = SPLIT[name]
+    s = synth.small_system(h=0.3, seed=33, n_orb=4, kernel=1, omega=0.106, **case)
+    plan, psi, f, vx, e = _apply(exx, s, code)
+    orc = oracle.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    ref = orc.exx_apply(s.psi[:s.n_occ], s.f, s.psi)
+    e_ref = orc.energy(s.psi[:s.n_occ], s.f, ref)
+    assert pm.rel(vx.cpu().numpy(), ref) < tol_v
+    assert abs(e - e_ref) < tol_e * abs(e_ref)
+
+
+@pytest.fixture(scope="module")
+def slab64():
+    # the slab grid (72 x 72 x 144, periodic x, y, vacuum along Dirichlet z) with 64 orbitals
+    return synth.make_system("slab72x72x144_erfc_64", (72, 72, 144), 0.2, (1, 1, 0), 64, synth.KERNEL_ERFC,
+                             synth.HSE_OMEGA, "fd", synth.SEED_BASE + 5, slab_axis=2, fermi_index=49)
+
+
+@pytest.mark.parametrize("name", ["bf16x10", "fp64"])
+def test_slab_grid_sampled_columns(exx, slab64, name):
+    s = slab64
+    code = 0 if name == "fp64" else SPLIT[name][0]
+    plan, psi, f, vx, e = _apply(exx, s, code)
+    cols = [5, 60]
+    orc = oracle.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    ref = orc.exx_apply(s.psi[:s.n_occ], s.f, s.psi, cols=cols)
+    assert pm.rel(vx.cpu().numpy()[cols], ref) < (1e-10 if name == "fp64" else 1e-6)

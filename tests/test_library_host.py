@@ -159,3 +159,22 @@ def test_schedule_covers_each_pair_once_with_disjoint_outputs(lib, n_occ, n_in, 
         assert field == nf
         p0 += nf
     assert p0 == len(pairs)
+
+
+def test_fast_division_matches_integer_division(lib):
+    """Row -> (field, row in field) in the pass kernels divides by multiply and shift;
+    every quotient must equal the integer one, at the divisor and quotient edges too."""
+    U = ctypes.POINTER(ctypes.c_uint)
+    lib.exx_debug_fastdiv.argtypes = [ctypes.c_uint, ctypes.c_int, U, U]
+    rng = np.random.Generator(np.random.PCG64(1994))
+    divisors = [1, 2, 3, 5, 7, 143, 2304, 4096, 5184, 746496, 2**31 - 1, 2**31, 2**31 + 1, 2**32 - 1]
+    divisors += [int(x) for x in rng.integers(1, 2**32, size=40)] + [int(x) for x in rng.integers(1, 5000, size=40)]
+    for d in divisors:
+        n = np.concatenate([rng.integers(0, 2**32, size=2000, dtype=np.uint64),
+                            np.array([0, 1, d - 1, d, d + 1, 2 * d - 1, 2 * d, 2**31 - 1, 2**31, 2**32 - 1],
+                                     dtype=np.uint64)])
+        n = (n % 2**32).astype(np.uint32)
+        q = np.zeros_like(n)
+        assert lib.exx_debug_fastdiv(d, len(n), n.ctypes.data_as(U), q.ctypes.data_as(U)) == 0
+        assert np.array_equal(q.astype(np.uint64), n.astype(np.uint64) // d), d
+    assert lib.exx_debug_fastdiv(0, 0, None, None) != 0
