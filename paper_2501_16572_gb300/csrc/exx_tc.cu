@@ -319,6 +319,8 @@ struct TcPassArgs {
     int f_noff;                     // first output mode of this block (index into Fs)
     long N;
     FastDiv divR;                   // division by R (row of the batch -> field, row in field)
+    FastDiv divK4;                  // division by K / 4 (contiguous KFAST tiles: chunk -> row)
+    FastDiv divKo4;                 // division by Kout / 4 (contiguous NFAST output tiles)
     const float *in;
     float *out;
     long lo_off;                    // hi + lo intermediates: offset of the lo plane (floats)
@@ -358,7 +360,10 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
     // after the first GEMM.  NBUF staging buffers = tiles whose copies are in flight.
     constexpr int NSTG = LOAD == LOAD_PAIR ? 4 : (HL ? 2 : 1);
     const int stg_len = kRows * (LOAD == LOAD_KFAST ? Kp + 4 : Kp);
-    const int buf_len = max(NSTG * stg_len, DOUBLE ? 2 * Np * kRows : 0);
+    // NFAST outputs are also staged here ([row][Kp + 4], hi then lo) to leave as
+    // contiguous runs (see the epilogue)
+    const int buf_len = max(max(NSTG * stg_len, DOUBLE ? 2 * Np * kRows : 0),
+                            STORE == STORE_NFAST ? (HL ? 2 : 1) * kRows * (Kp + 4) : 0);
     float *stg0 = reinterpret_cast<float *>(sA0 + NSETS * a_piece * S);
     float *maxbuf = stg0 + NBUF * buf_len;
     uint64_t *bar1 = reinterpret_cast<uint64_t *>(maxbuf + NT);   // [2]: first GEMM of each set
@@ -402,6 +407,13 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
     // KSLOW / PAIR rows come 4 at a time (16-byte copies) when a field's rows are a
     // multiple of 4: a group of 4 consecutive rows then never straddles two fields
     const bool rvec = ((a.R & 3) == 0) && ((a.lo_off & 3) == 0);
+    // KFAST rows of a whole (unblocked) axis are back to back across fields (N = R K), so a
+    // tile is one contiguous run of 128 K values: copied by consecutive lanes (coalesced)
+    const bool kcont = LOAD == LOAD_KFAST && vec16 && a.in_pitch == a.K && a.in_off == 0;
+    // the same holds for NFAST outputs of a whole axis: the epilogue stages the tile in
+    // shared memory and writes it back with consecutive lanes on consecutive 16 bytes
+    const bool ostage = STORE == STORE_NFAST && (NSETS == 2 || DOUBLE) && vec_out && a.out_pitch == a.Kout &&
+                        a.out_off == 0 && !a.acc && !a.Fs && (a.Kout & 3) == 0;
     // row `rl` of tile t -> (field pp, row rr of the field); false past the last row
     auto locate = [&](long t, int rl, int &pp, int &rr) {
         const long gg = t * kRows + rl;
@@ -417,7 +429,20 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
     // so that wait_group counts tiles.
     auto prefetch = [&](long t, float *stg) {
         int pp, rr;
-        if (LOAD == LOAD_KFAST) {
+        if (LOAD == LOAD_KFAST && kcont) {
+            if (t < ntiles) {
+                const long g0 = t * kRows;
+                const int nrow = int(min(long(kRows), rows - g0));
+                const int nchk = nrow * (a.K >> 2);   // 16-byte chunks of the tile
+                const float *src = a.in + size_t(g0) * a.K;
+                for (int c = tid; c < nchk; c += NT) {
+                    const int rw = int(fast_div(uint32_t(c), a.divK4));
+                    float *dh = stg + rw * (Kp + 4) + 4 * (c - rw * (a.K >> 2));
+                    tc::cp_async16(dh, src + 4 * c);
+                    if (HL) tc::cp_async16(dh + stg_len, src + a.lo_off + 4 * c);
+                }
+            }
+        } else if (LOAD == LOAD_KFAST) {
             if (locate(t, row, pp, rr)) {
                 const float *src = a.in + size_t(pp) * a.N + size_t(rr) * a.in_pitch + a.in_off;
                 float *dh = stg + row * (Kp + 4);
@@ -597,7 +622,35 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
     };
     // Epilogue of tile t from TMEM set st: own 4-column units -> global (added to the
     // stored partial sums for K-blocks after the first; scaled by f(Lambda) when Fs is set).
-    auto epilogue = [&](long t, int st, float rs_out, const float *cs_out) {
+    // With obuf (a free staging buffer) and ostage, through shared memory: every compute
+    // thread must call it then, as it contains two compute-thread barriers.
+    auto epilogue = [&](long t, int st, float rs_out, const float *cs_out, float *obuf) {
+        if (ostage && obuf != nullptr) {
+            const int opitch = Kp + 4;
+            float *oh = obuf, *ol = obuf + kRows * opitch;
+            for (int u = q; u < nunit; u += TPR) {
+                float v[4], vlo[4];
+                read4<MODE, NACC, HL>(set_tmem(st) + lane_q, Np, 4 * u, rs_out, cs_out, v, vlo);
+                *reinterpret_cast<float4 *>(oh + row * opitch + 4 * u) = make_float4(v[0], v[1], v[2], v[3]);
+                if (HL) *reinterpret_cast<float4 *>(ol + row * opitch + 4 * u) = make_float4(vlo[0], vlo[1], vlo[2], vlo[3]);
+            }
+            tc::tc_fence_before();
+            tc::bar_sync(kBarCompute, NT);
+            const long g0 = t * kRows;
+            const int nrow = int(min(long(kRows), rows - g0));
+            const int kq = a.Kout >> 2;
+            float *dst = a.out + size_t(g0) * a.Kout;
+            for (int c = tid; c < nrow * kq; c += NT) {
+                const int rw = int(fast_div(uint32_t(c), a.divKo4));
+                const int k = 4 * (c - rw * kq);
+                *reinterpret_cast<float4 *>(dst + 4 * c) = *reinterpret_cast<const float4 *>(oh + rw * opitch + k);
+                if (HL)
+                    *reinterpret_cast<float4 *>(dst + a.lo_off + 4 * c) =
+                        *reinterpret_cast<const float4 *>(ol + rw * opitch + k);
+            }
+            tc::bar_sync(kBarCompute, NT);   // obuf is free again
+            return;
+        }
         int pp = 0, rr = 0;
         const bool act = locate(t, row, pp, rr);
         float *out = a.out + size_t(pp) * a.N + a.out_off;
@@ -692,7 +745,7 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
         if (NSETS == 1 && prev_tile >= 0) {   // one A buffer / TMEM set: finish t-1 first
             if (DOUBLE) wait_bar(bar2 + prev_set, ph2, prev_set);
             else wait_bar(bar1 + prev_set, ph1, prev_set);
-            epilogue(prev_tile, prev_set, prev_rs, prev_cs);
+            epilogue(prev_tile, prev_set, prev_rs, prev_cs, nullptr);
             prev_tile = -1;
         }
         int p = 0, r = 0;
@@ -702,7 +755,7 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
         // ---- slice tile -> A[st] (A[st] was last read by the GEMMs of tile it-2,
         //      which completed before that tile's epilogue) ----
         tc::cp_async_wait_group<NBUF - 1>();  // this tile's copies (one group per tile) landed
-        if (LOAD != LOAD_KFAST && rvec) tc::bar_sync(kBarCompute, NT);   // rows copied by other threads
+        if ((LOAD != LOAD_KFAST && rvec) || kcont) tc::bar_sync(kBarCompute, NT);   // rows copied by other threads
         const float mx = row_max(active ? staged_max(stg) : 0.f);
         float s_in, rs1;
         scales(mx, s_in, rs1);
@@ -724,35 +777,46 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
         //      tile it-2, which every thread finished before this hand-off ----
         if (handoff()) break;
         // every thread has consumed this staging buffer: fetch the tile NBUF steps ahead
-        if (!DOUBLE) prefetch(tile + long(NBUF) * gridDim.x, stg);
+        // (after the epilogue when that stages its output here)
+        if (!DOUBLE && !ostage) prefetch(tile + long(NBUF) * gridDim.x, stg);
         // ---- epilogue of the previous tile, overlapping this tile's GEMM ----
         if (prev_tile >= 0) {
             if (DOUBLE) wait_bar(bar2 + prev_set, ph2, prev_set);
             else wait_bar(bar1 + prev_set, ph1, prev_set);
-            epilogue(prev_tile, prev_set, prev_rs, prev_cs);
+            epilogue(prev_tile, prev_set, prev_rs, prev_cs, stg);
         }
+        if (!DOUBLE && ostage) prefetch(tile + long(NBUF) * gridDim.x, stg);
         float rs_out = rs1;
         const float *cs_out = cs1;
         if (DOUBLE) {
             // D1 * f(Lambda) -> staging ([col][row], own units) -> A[st] (its first GEMM
             // is complete) -> second GEMM into the same TMEM set
+            // f(Lambda) of the next unit is loaded while the current one is processed (the
+            // first one while the GEMM finishes)
+            float fh_n[4], fl_n[4];
+            auto load_f = [&](int u) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int col = 4 * u + e;
+                    const bool ok = active && u < nunit && col < a.Kout;
+                    const size_t fi = size_t(col) * a.R + r;
+                    fh_n[e] = ok ? a.F[fi] : 0.f;
+                    fl_n[e] = ok ? a.Flo[fi] : 0.f;
+                }
+            };
+            load_f(q);
             wait_bar(bar1 + st, ph1, st);
             float *mid_hi = stg, *mid_lo = stg + Np * kRows;
             float mx2 = 0.f;
             for (int u = q; u < nunit; u += TPR) {
                 float v[4], vlo[4], fh[4], fl[4];
-                read4<MODE, NACC, HL>(set_tmem(st) + lane_q, Np, 4 * u, rs1, cs1, v, vlo);
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const int col = 4 * u + e;
-                    fh[e] = 0.f;
-                    fl[e] = 0.f;
-                    if (active && col < a.Kout) {
-                        const size_t fi = size_t(col) * a.R + r;
-                        fh[e] = a.F[fi];
-                        fl[e] = a.Flo[fi];
-                    }
+                    fh[e] = fh_n[e];
+                    fl[e] = fl_n[e];
                 }
+                load_f(u + TPR);
+                read4<MODE, NACC, HL>(set_tmem(st) + lane_q, Np, 4 * u, rs1, cs1, v, vlo);
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     float x, xl = 0.f;
@@ -797,10 +861,12 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
         prev_rs = rs_out;
         prev_cs = cs_out;
     }
-    if (prev_tile >= 0 && *sflag == 0) {
+    // last tile (every staging buffer is idle now); the decision is made uniform first,
+    // since the staged epilogue synchronizes the compute threads
+    if (prev_tile >= 0 && !tc::bar_red_or(kBarCompute, NT, *sflag != 0)) {
         if (DOUBLE) wait_bar(bar2 + prev_set, ph2, prev_set);
         else wait_bar(bar1 + prev_set, ph1, prev_set);
-        epilogue(prev_tile, prev_set, prev_rs, prev_cs);
+        epilogue(prev_tile, prev_set, prev_rs, prev_cs, stg0);
     }
     tc::cp_async_wait_all();   // no copy may still target shared memory at exit
     }   // compute threads
@@ -991,13 +1057,14 @@ __global__ void tc_finalize_kernel(long N, int n_in, const float *acc_hi, const 
 }
 
 // ---- launch helpers -------------------------------------------------------------------
-size_t pass_smem(int prec, int Np, bool dbl, int load, int nbuf = 1, int nsets = 1)
+size_t pass_smem(int prec, int Np, bool dbl, int load, int nbuf = 1, int nsets = 1, int store = STORE_NSLOW)
 {
     const PrecInfo pi = prec_info(prec);
     size_t a = size_t(nsets) * pi.S * kRows * Np * pi.es;   // A buffers
     const int pitch = load == LOAD_KFAST ? Np + 4 : Np;   // KFAST rows are padded, [k][row] layouts not
     size_t staging = size_t(load == LOAD_PAIR ? 4 : (pi.hl ? 2 : 1)) * kRows * pitch * sizeof(float);
     if (dbl) staging = std::max(staging, size_t(2) * kRows * Np * sizeof(float));
+    if (store == STORE_NFAST) staging = std::max(staging, size_t(pi.hl ? 2 : 1) * kRows * (Np + 4) * sizeof(float));
     staging *= size_t(nbuf);                                   // staging buffers in flight
     const size_t maxbuf = size_t(kRows) * 4 * sizeof(float);   // up to 4 threads per row
     return (dbl ? 2 : 1) * image_bytes(prec, Np) + a + staging + maxbuf + 64;
@@ -1011,7 +1078,7 @@ template <int MODE, int S, int SB, bool HL, int LOAD, int STORE, bool DOUBLE, in
 int launch_tc_pass_nb(Plan &P, int kind, int prec, const TcPassArgs &a, cudaStream_t s)
 {
     auto kern = tc_pass_kernel<MODE, S, SB, HL, LOAD, STORE, DOUBLE, kTPR, NBUF, NSETS>;
-    size_t smem = pass_smem(prec, a.Np, DOUBLE, LOAD, NBUF, NSETS);
+    size_t smem = pass_smem(prec, a.Np, DOUBLE, LOAD, NBUF, NSETS, STORE);
     // TMEM: co-resident CTAs must not ask for more than 512 columns in total, so the
     // shared-memory request is raised until at most 512 / cols CTAs fit on one SM.
     const int cols = tmem_cols(prec, a.Np, NSETS);
@@ -1045,9 +1112,9 @@ int launch_tc_pass(Plan &P, int kind, int prec, const TcPassArgs &a, cudaStream_
 {
     const size_t lim = 232448;
     const bool tm2 = tmem_cols(prec, a.Np, 2) <= 512;
-    if (LOAD != LOAD_PAIR && tm2 && pass_smem(prec, a.Np, DOUBLE, LOAD, 2, 2) <= lim)
+    if (LOAD != LOAD_PAIR && tm2 && pass_smem(prec, a.Np, DOUBLE, LOAD, 2, 2, STORE) <= lim)
         return launch_tc_pass_nb<MODE, S, SB, HL, LOAD, STORE, DOUBLE, 2, 2>(P, kind, prec, a, s);
-    if (tm2 && pass_smem(prec, a.Np, DOUBLE, LOAD, 1, 2) <= lim)
+    if (tm2 && pass_smem(prec, a.Np, DOUBLE, LOAD, 1, 2, STORE) <= lim)
         return launch_tc_pass_nb<MODE, S, SB, HL, LOAD, STORE, DOUBLE, 1, 2>(P, kind, prec, a, s);
     return launch_tc_pass_nb<MODE, S, SB, HL, LOAD, STORE, DOUBLE, 1, 1>(P, kind, prec, a, s);
 }
@@ -1116,6 +1183,8 @@ int solve_batch_t(Plan &P, int prec, const int2 *pairs_d, int nfields, float *bu
             for (int c = 0; c < nb; ++c) {   // K-blocks in order: the first writes, the others add
                 a.K = std::min(bs, nd - c * bs);
                 a.Kout = std::min(bs, nd - h * bs);
+                a.divK4 = make_fastdiv(uint32_t(std::max(1, a.K / 4)));
+                a.divKo4 = make_fastdiv(uint32_t(std::max(1, a.Kout / 4)));
                 a.in_off = kslow_in ? long(c) * bs * g.R : long(c) * bs;
                 a.out_off = nslow_out ? long(h) * bs * g.R : long(h) * bs;
                 a.acc = c > 0;
@@ -1142,8 +1211,10 @@ int solve_batch_t(Plan &P, int prec, const int2 *pairs_d, int nfields, float *bu
 static bool axis_fits(int prec, int d, int Np, bool split)
 {
     size_t need = 0;
-    if (d == 0) need = std::max(pass_smem(prec, Np, false, LOAD_KFAST), pass_smem(prec, Np, false, LOAD_KSLOW));
-    if (d == 1) need = pass_smem(prec, Np, !split, LOAD_KFAST);
+    if (d == 0)
+        need = std::max(pass_smem(prec, Np, false, LOAD_KFAST),
+                        pass_smem(prec, Np, false, LOAD_KSLOW, 1, 1, STORE_NFAST));
+    if (d == 1) need = pass_smem(prec, Np, !split, LOAD_KFAST, 1, 1, STORE_NFAST);
     if (d == 2) need = std::max(pass_smem(prec, Np, false, LOAD_PAIR), pass_smem(prec, Np, false, LOAD_KSLOW));
     return need <= 232448 && tmem_cols(prec, Np) <= 512;
 }
