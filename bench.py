@@ -12,10 +12,17 @@ one orbital pair, Sec. II.B) and the exx_apply time.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                        [--prec auto|fp64|bf16x3|tf32x3|bf16x6|bf16x10]
-                       [--workload periodic48|batch48]
---workload batch48 times instead 48 independent systems (grids of 20-64 points per
-axis, 8-160 orbitals) solved by one exx_apply_batched call (one CUDA graph) per step,
-beside the same work issued as one exx_apply call per system.
+                       [--workload periodic48|batch48|sweep|precision|slab]
+Other workloads (not the default line):
+  batch48   48 independent systems (grids of 20-64 points per axis, 8-160 orbitals) solved
+            by one exx_apply_batched call (one CUDA graph) per step, beside the same work
+            issued as one exx_apply call per system.
+  sweep     exx_apply of the 48^3 workload for pair batches n_c = 1 (one pair per solve
+            sequence, the unbatched Kronecker solver) up to 1024.
+  precision 48^3 grid with 256 orbitals: every precision mode against the FP64 path
+            (VxPsi, xi, E_x errors and times).
+  slab      72x72x144 slab (periodic x, y; Dirichlet z), 1024 orbitals, 800 occupied:
+            BF16X10 step timed, FP64 path on 16 sampled output orbitals for the error.
 For N > 1 launch with torchrun; every rank runs an independent replica (the pair
 solves shard with no exchange), so the whole-job value is the sum over ranks.
 """
@@ -58,7 +65,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n-orb", type=int, default=128)
     ap.add_argument("--batch", type=int, default=0, help="pairs per batch (0 = library default)")
-    ap.add_argument("--workload", default="periodic48", choices=["periodic48", "batch48"])
+    ap.add_argument("--workload", default="periodic48", choices=["periodic48", "batch48", "sweep", "precision", "slab"])
     return ap.parse_args()
 
 
@@ -462,6 +469,163 @@ def run_batch48(args):
         dist.destroy_process_group()
 
 
+def _apply_ms(exx, plan, psi_occ, f, psi_in, out, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        plan.apply(psi_occ, f, psi_in, out=out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        plan.apply(psi_occ, f, psi_in, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_sweep(args):
+    """exx_apply time of the 48^3 / 128-orbital workload against the pair batch size n_c."""
+    import torch
+    import synth
+    import paper_2501_16572_gb300 as exx
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    s = synth.config2(args.n_orb)
+    psi = torch.from_numpy(s.psi).cuda()
+    f = torch.from_numpy(s.f).cuda()
+    out = torch.empty_like(psi)
+    stream = torch.cuda.current_stream()
+    prec_name = args.prec if args.prec != "auto" else "bf16x10"
+    rows = []
+    for nc, blk in [(1, 1), (4, 2), (16, 4), (64, 8), (256, 8), (512, 8), (1024, 8)]:
+        p = exx.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+        p.set_precision(prec_code(exx, prec_name))
+        p.set_batch(nc, blk)
+        ms = _apply_ms(exx, p, psi, f, psi, out, max(1, args.steps), max(1, args.warmup if nc > 16 else 1), stream)
+        rows.append({"n_c": nc, "block_orbitals": blk, "exx_apply_ms": ms, "launches": p.launch_count(),
+                     "pair_solves_per_s": s.unique_pairs() / (ms / 1e3)})
+        p.close()
+    best = max(rows, key=lambda r: r["pair_solves_per_s"])
+    rec = {"metric": METRIC, "value": best["pair_solves_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": best["exx_apply_ms"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": prec_name, "data": "synthetic (seeded Gaussian + plane-wave orbitals, orthonormalised)",
+           "config": {"workload": "n_c sweep of exx_apply on " + WORKLOAD.split(";")[0], "n_orb": s.n_orb,
+                      "unique_pair_solves": s.unique_pairs(), "l2": "not flushed (back-to-back applies)"},
+           "sweep": rows}
+    print(json.dumps(rec), flush=True)
+
+
+def run_precision(args):
+    """Every precision mode on the 48^3 grid with 256 orbitals, against the FP64 path."""
+    import torch
+    import synth
+    import paper_2501_16572_gb300 as exx
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    s = synth.config3()
+    psi = torch.from_numpy(s.psi).cuda()
+    f = torch.from_numpy(s.f).cuda()
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name in ("fp64", "bf16x10", "bf16x6", "tf32x3", "bf16x3"):
+        p = exx.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+        p.set_precision(prec_code(exx, name))
+        W = torch.empty_like(psi)
+        ms = _apply_ms(exx, p, psi[:s.n_occ], f, psi, W, max(1, args.steps), 1, stream)
+        e = p.energy(psi[:s.n_occ], f, W)
+        xi = p.ace_build(psi, W)
+        res[name] = (ms, W, xi, e)
+        p.close()
+    ms64, W64, xi64, e64 = res["fp64"]
+    rel = lambda a, b: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+    table = []
+    for name, (ms, W, xi, e) in res.items():
+        table.append({"precision": name, "exx_apply_ms": ms, "pair_solves_per_s": s.unique_pairs() / (ms / 1e3),
+                      "vxpsi_rel_fro_vs_fp64": rel(W, W64), "xi_rel_fro_vs_fp64": rel(xi, xi64),
+                      "E_x_rel_vs_fp64": abs(e - e64) / abs(e64), "E_x": e})
+    b10 = [r for r in table if r["precision"] == "bf16x10"][0]
+    rec = {"metric": METRIC, "value": b10["pair_solves_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": 1, "ms_per_step": b10["exx_apply_ms"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "bf16x10", "data": "synthetic (seeded Gaussian + plane-wave orbitals, orthonormalised)",
+           "config": {"workload": "precision study: 48x48x48 periodic grid, erfc omega=0.106, 256 orbitals, "
+                                  "Fermi-Dirac occupations; exx_apply timed per precision",
+                      "unique_pair_solves": s.unique_pairs(), "l2": "not flushed (back-to-back applies)"},
+           "precisions": table}
+    print(json.dumps(rec), flush=True)
+
+
+def run_slab(args):
+    """72x72x144 slab, 1024 orbitals (800 occupied): BF16X10 step (exx_apply + energy +
+    ACE) timed; the FP64 path recomputes 16 sampled output orbitals for the error."""
+    import torch
+    import synth
+    import paper_2501_16572_gb300 as exx
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    t0 = time.perf_counter()
+    s = synth.config5()
+    t_synth = time.perf_counter() - t0
+    psi = torch.from_numpy(s.psi).cuda()
+    f = torch.from_numpy(s.f).cuda()
+    occ = s.n_occ
+    stream = torch.cuda.current_stream()
+    prec_name = args.prec if args.prec != "auto" else "bf16x10"
+    p = exx.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    p.set_precision(prec_code(exx, prec_name))
+    W = torch.empty_like(psi)
+    xi = torch.empty_like(psi)
+    for _ in range(args.warmup):
+        p.apply(psi[:occ], f, psi, out=W)
+    torch.cuda.synchronize()
+    ms, apply_ms, e = [], [], 0.0
+    clocks = Clocks(local)
+    clocks.start()
+    for _ in range(args.steps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        p.apply(psi[:occ], f, psi, out=W)
+        ev[1].record(stream)
+        e = p.energy(psi[:occ], f, W)
+        p.ace_build(psi, W, xi=xi)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        ms.append(ev[0].elapsed_time(ev[2]))
+        apply_ms.append(ev[0].elapsed_time(ev[1]))
+    clk = clocks.stop()
+    cols = list(range(0, s.n_orb, s.n_orb // 16))[:16]
+    p64 = exx.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    sub = psi[cols].contiguous()
+    ref = torch.empty_like(sub)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    p64.apply(psi[:occ], f, sub, out=ref)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    rel = float(torch.linalg.norm(W[cols] - ref) / torch.linalg.norm(ref))
+    unique = s.unique_pairs()
+    K = args.steps
+    rec = {"metric": METRIC, "value": unique * K / (sum(ms) / 1e3), "unit": UNIT, "n_gpus": 1, "steps": K,
+           "warmup": args.warmup, "ms_per_step": sum(ms) / K, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": prec_name, "data": "synthetic (seeded Gaussian orbitals in the bottom 70% of z, orthonormalised)",
+           "config": {"workload": "slab 72x72x144, periodic x,y, Dirichlet z, h=0.2, erfc omega=0.106, 1024 orbitals, "
+                                  "800 occupied; step = exx_apply + exx_energy + ace_build",
+                      "unique_pair_solves_per_step": unique, "ordered_pairs_per_step": s.ordered_pairs(),
+                      "l2": "inputs (6.1 GB) larger than L2"},
+           "exx_apply_ms": sum(apply_ms) / K, "E_x": e, "clocks": clk,
+           "fp64_sampled": {"output_orbitals": cols, "pair_solves": occ * len(cols), "exx_apply_ms": ms64,
+                            "pair_solves_per_s": occ * len(cols) / (ms64 / 1e3),
+                            "vxpsi_rel_fro_of_sampled_vs_fp64": rel},
+           "input_generation_s": t_synth}
+    print(json.dumps(rec), flush=True)
+
+
 # bytes per grid element a pass must read and write (its input and output planes); pass 1
 # reads the FP32 hi/lo planes of both orbitals, pass 3 also reads f(Lambda) (hi/lo) once
 # per launch.  BF16X10 keeps hi+lo intermediates (8 B), the other split modes FP32 (4 B).
@@ -596,5 +760,11 @@ if __name__ == "__main__":
         run_reference(a)
     elif a.workload == "batch48":
         run_batch48(a)
+    elif a.workload == "sweep":
+        run_sweep(a)
+    elif a.workload == "precision":
+        run_precision(a)
+    elif a.workload == "slab":
+        run_slab(a)
     else:
         run_ours(a)

@@ -98,8 +98,10 @@ int exx_plan_create(exx_plan *out, int Nx, int Ny, int Nz, double h, const int b
 /* Select the mode-product arithmetic (EXX_PREC_*); default EXX_PREC_FP64. */
 int exx_plan_set_precision(exx_plan plan, int prec);
 
-/* Tuning: pairs per batch (the paper's n_c, Sec. II.B; 0 = autotuned default) and
- * orbitals per pair block (0 = default).  Results do not depend on either. */
+/* Tuning: pairs per batch (the paper's n_c, Sec. II.B) and orbitals per pair block.
+ * 0 = defaults: blocks of 8 orbitals, and as many pairs per batch as fit two plan-owned
+ * work buffers of at most 2 GiB each, at most 1024, a multiple of block^2.  Results do
+ * not depend on either (up to the order of the compensated sums). */
 int exx_plan_set_batch(exx_plan plan, int pairs_per_batch, int block_orbitals);
 
 /* Shard the pair solves of exx_apply over `world` processes (one GPU each): this plan then

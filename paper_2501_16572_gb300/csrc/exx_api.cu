@@ -77,7 +77,7 @@ static void free_plan_buffers(Plan &P)
 static int default_pairs(const Plan &P, int block)
 {
     long per_field = long(P.N) * (P.prec == EXX_PREC_FP64 || P.prec == EXX_PREC_BF16X10 ? 8 : 4);
-    long budget = 512L << 20;
+    long budget = 2048L << 20;   // per work buffer (two of them)
     long pairs = std::max<long>(block * block, budget / per_field);
     pairs = std::min<long>(pairs, 1024);
     return int((pairs / (block * block)) * (block * block));
