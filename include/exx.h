@@ -144,14 +144,19 @@ int exx_energy(exx_plan plan, const double *Psi_occ, int n_occ, long ld, const d
  * The compressed operator is then -dV xi xi^T (M is negative definite, so the
  * printed "Cholesky factor of M" is read as that of -M).  Psi, W: N x n (ld, ld_w);
  * xi: N x n (ld_xi), overwritten; M_out: optional n x n column-major device buffer
- * (NULL to skip).  Every step (M, Cholesky, triangular inverse, xi) is FP64 on the
- * CUDA cores in every precision mode of the plan.
+ * (NULL to skip).  FP64 plans compute every step on the CUDA cores in FP64.  Split
+ * plans compute the products M and xi on the tensor cores: fixed-point digits of 31
+ * bits per 320-long chunk of the contraction (rows scaled by their largest entry),
+ * exact integer sums per chunk, FP64 across chunks (relative error ~1e-9..1e-8).  The
+ * Cholesky factor and its inverse are FP64 in every mode.
  * *info_h (host) is 0, or 1 + the failing pivot when EXX_ERR_NOT_POSDEF is
  * returned.  Synchronizes `stream`.  n <= 2048. */
 int ace_build(exx_plan plan, const double *Psi, int n, long ld, const double *W, long ld_w,
               double *xi, long ld_xi, double *M_out, int *info_h, exx_stream_t stream);
 
-/* ACE application, Sec. III.B: out = -dV xi (xi^T Phi); xi: N x n, Phi, out: N x nphi. */
+/* ACE application, Sec. III.B: out = -dV xi (xi^T Phi); xi: N x n, Phi, out: N x nphi.
+ * Both products run as in ace_build: FP64 for FP64 plans, tensor-core digits for split
+ * plans. */
 int ace_apply(exx_plan plan, const double *xi, int n, long ld_xi, const double *Phi, int nphi,
               long ld_phi, double *out, long ld_out, exx_stream_t stream);
 

@@ -32,7 +32,7 @@ def sources():
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     srcs = sources()
-    deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     deps.append(os.path.join(ROOT, "include", "exx.h"))
     if not force and os.path.exists(LIB):
         newest = max(os.path.getmtime(p) for p in deps)

@@ -488,7 +488,14 @@ int ace_build(exx_plan plan, const double *Psi, int n, long ld, const double *W,
     double *M = M_out ? M_out : static_cast<double *>(P->info_d.p);
     double *Linv = static_cast<double *>(P->info_d.p) + nn;
     int *info_d = reinterpret_cast<int *>(static_cast<double *>(P->info_d.p) + 2 * nn);
-    if (int rc = gemm_fp64_tn_splitk(*P, n, n, P->N, Psi, ld, W, ld_w, P->dV, M, n, s)) return rc;
+    // split-precision plans take the ACE products on the tensor cores, FP64 plans on the
+    // CUDA cores; the Cholesky factor and its inverse are FP64 in both
+    const bool tcg = P->prec != EXX_PREC_FP64;
+    if (tcg) {
+        if (int rc = tc_gemm(*P, n, n, P->N, Psi, ld, 1, W, ld_w, 1, P->dV, M, 1, n, s)) return rc;
+    } else if (int rc = gemm_fp64_tn_splitk(*P, n, n, P->N, Psi, ld, W, ld_w, P->dV, M, n, s)) {
+        return rc;
+    }
     if (int rc = cholesky_neg_sym_and_inverse(*P, n, M, Linv, info_d, s)) return rc;
     int info = 0;
     EXX_CUDA(cudaMemcpyAsync(&info, info_d, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -499,8 +506,13 @@ int ace_build(exx_plan plan, const double *Psi, int n, long ld, const double *W,
         return EXX_ERR_NOT_POSDEF;
     }
     // xi = W Linv^T
-    if (int rc = gemm_fp64_nt(*P, P->N, n, n, W, ld_w, Linv, n, 1.0, xi, ld_xi, s)) return rc;
+    if (tcg) {
+        if (int rc = tc_gemm(*P, P->N, n, n, W, 1, ld_w, Linv, 1, n, 1.0, xi, 1, ld_xi, s)) return rc;
+    } else if (int rc = gemm_fp64_nt(*P, P->N, n, n, W, ld_w, Linv, n, 1.0, xi, ld_xi, s)) {
+        return rc;
+    }
     EXX_CUDA(cudaStreamSynchronize(s));
+    if (tcg) return tc_check_error(*P, s);
     return EXX_OK;
 }
 
@@ -517,6 +529,10 @@ int ace_apply(exx_plan plan, const double *xi, int n, long ld_xi, const double *
     if (int rc = dev_reserve(P->small_ws, need)) return rc;
     double *chi = static_cast<double *>(P->small_ws.p);
     // chi = xi^T Phi (n x nphi), out = -dV xi chi
+    if (P->prec != EXX_PREC_FP64) {   // the two products on the tensor cores
+        if (int rc = tc_gemm(*P, n, nphi, P->N, xi, ld_xi, 1, Phi, ld_phi, 1, 1.0, chi, 1, n, s)) return rc;
+        return tc_gemm(*P, P->N, nphi, n, xi, 1, ld_xi, chi, n, 1, -P->dV, out, 1, ld_out, s);
+    }
     if (int rc = gemm_fp64_tn_splitk(*P, n, nphi, P->N, xi, ld_xi, Phi, ld_phi, 1.0, chi, n, s)) return rc;
     return gemm_fp64_nn(*P, P->N, nphi, n, xi, ld_xi, chi, n, -P->dV, out, ld_out, s);
 }

@@ -198,6 +198,10 @@ int tc_unit_gemm(int tf32, int n, int k, const float *A, const float *B, float *
 // reductions, GEMM, Cholesky (exx_linalg.cu)
 int energy_fp64(Plan &P, const double *psi, int n, long ld, const double *f, const double *v,
                 long ld_v, double *E_h, cudaStream_t s);
+// D(i, j) = alpha sum_k A(i, k) B(j, k) on the tensor cores (fixed-point digits, exact
+// 320-long chunks summed in FP64); A(i, k) = A[i as_i + k as_k], same for B and D.
+int tc_gemm(Plan &P, int m, int n, long K, const double *A, long as_i, long as_k, const double *B, long bs_j,
+            long bs_k, double alpha, double *D, long ds_i, long ds_j, cudaStream_t s);
 int gemm_fp64_tn_splitk(Plan &P, int n_a, int n_b, int K, const double *A, long lda,
                         const double *B, long ldb, double alpha, double *C, int ldc, cudaStream_t s);
 int gemm_fp64_nt(Plan &P, int M, int Ncols, int K, const double *A, long lda, const double *B,

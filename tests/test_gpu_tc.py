@@ -189,3 +189,42 @@ def test_slab_grid_sampled_columns(exx, slab64, name):
     orc = oracle.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
     ref = orc.exx_apply(s.psi[:s.n_occ], s.f, s.psi, cols=cols)
     assert pm.rel(vx.cpu().numpy()[cols], ref) < (1e-10 if name == "fp64" else 1e-6)
+
+
+ACE_CASES = [dict(n=(13, 11, 12), bc=(0, 0, 1), n_orb=10, kernel=0),      # N = 1716: 6 k chunks, split k
+             dict(n=(8, 7, 9), bc=(1, 0, 0), n_orb=150, kernel=0),         # n = 150: 2 x 2 output tiles
+             dict(n=(24, 20, 22), bc=(1, 1, 1), n_orb=40, kernel=1, omega=0.106)]
+
+
+@pytest.mark.parametrize("case", ACE_CASES, ids=lambda c: f"{'x'.join(map(str, c['n']))}_{c['n_orb']}")
+def test_split_ace_on_tensor_cores_matches_oracle(exx, case):
+    """ACE products in a split plan (fixed-point digits on the tensor cores) against the
+    FP64 oracle of Sec. III, for an exact W (taken from the FP64 path)."""
+    s = synth.small_system(h=0.4, seed=41, **case)
+    n = s.n_orb
+    p64 = exx.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    psi = torch.from_numpy(s.psi).cuda()
+    f = torch.from_numpy(s.f).cuda()
+    W = p64.apply(psi[:s.n_occ], f, psi)
+    Wh = W.cpu().numpy()
+    M_ref, L_ref, xi_ref = oracle.ace(s.psi, Wh, s.dV)
+    p = exx.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    p.set_precision(SPLIT["bf16x10"][0])
+    Md = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+    # strided operands: rows of Psi and W padded past N
+    pad = torch.zeros((n, s.N + 9), dtype=torch.float64, device="cuda")
+    pad[:, :s.N] = psi
+    wpad = torch.zeros((n, s.N + 5), dtype=torch.float64, device="cuda")
+    wpad[:, :s.N] = W
+    xi = p.ace_build(pad[:, :s.N], wpad[:, :s.N], M=Md)
+    assert pm.rel(Md.cpu().numpy().T, M_ref) < 1e-8
+    assert pm.rel(xi.cpu().numpy(), xi_ref) < 1e-8
+    back = p.ace_apply(xi, psi)
+    assert pm.rel(back.cpu().numpy(), Wh) < 1e-8
+    # a block of 3 vectors that are not orbitals: -dV xi (xi^T Phi) against numpy
+    rng = np.random.Generator(np.random.PCG64(7))
+    phi = rng.normal(size=(3, s.N))
+    got = p.ace_apply(xi, torch.from_numpy(phi).cuda()).cpu().numpy()
+    X = xi.cpu().numpy()
+    want = -s.dV * (X.T @ (X @ phi.T)).T
+    assert pm.rel(got, want) < 1e-8
