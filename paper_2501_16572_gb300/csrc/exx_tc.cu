@@ -334,13 +334,15 @@ struct TcPassArgs {
 };
 
 template <int MODE, int S, int SB, bool HL, int LOAD, int STORE, bool DOUBLE, int TPR, int NBUF, int NSETS>
-__global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs a)
+__global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(TcPassArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     constexpr int ES = MODE == MODE_FLOAT_TF32 ? 4 : 2;
     constexpr int NACC = MODE == MODE_FLOAT_TF32 ? 1 : (SB > S ? S + 1 : S);
-    constexpr int NT = kRows * TPR;          // compute threads; one more warp issues the MMAs
-    constexpr int kBarHandoff = 1, kBarCompute = 2;
+    // compute threads, then one warp that issues the MMAs and one that issues the input
+    // copies of the coalesced layouts (the producer)
+    constexpr int NT = kRows * TPR;
+    constexpr int kBarHandoff = 1, kBarCompute = 2, kBarEpi = 3;
     const int Np = a.Np, Kp = a.Np;
     const int nunit = Np / 4;                // 4-element units per row
     const uint32_t sbo = uint32_t(Kp) * ES * 8;          // bytes per 8-row group
@@ -368,7 +370,8 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
     float *maxbuf = stg0 + NBUF * buf_len;
     uint64_t *bar1 = reinterpret_cast<uint64_t *>(maxbuf + NT);   // [2]: first GEMM of each set
     uint64_t *bar2 = bar1 + 2;                                      // [2]: second GEMM (pass 3)
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar2 + 2);
+    uint64_t *full = bar2 + 2;                                      // [2]: staging buffer filled
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(full + 2);
     int *sflag = reinterpret_cast<int *>(tslot + 1);
     const float *cs1 = reinterpret_cast<const float *>(sB1 + SB * b_piece);
     const float *cs2 = reinterpret_cast<const float *>(sB2 + SB * b_piece);
@@ -376,13 +379,15 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
     const int set_cols = NACC * Np;
     const int ncols = NSETS * set_cols <= 32 ? 32 : NSETS * set_cols <= 64 ? 64 : NSETS * set_cols <= 128 ? 128 : NSETS * set_cols <= 256 ? 256 : 512;
 
-    for (uint32_t i = tid * 16; i < a.img_bytes; i += (NT + 32) * 16) {
+    for (uint32_t i = tid * 16; i < a.img_bytes; i += (NT + 64) * 16) {
         *reinterpret_cast<uint4 *>(sB1 + i) = *reinterpret_cast<const uint4 *>(a.B1 + i);
         if (DOUBLE) *reinterpret_cast<uint4 *>(sB2 + i) = *reinterpret_cast<const uint4 *>(a.B2 + i);
     }
-    for (int i = tid; i < NBUF * buf_len; i += NT + 32) stg0[i] = 0.f;   // padding k >= K stays zero
+    for (int i = tid; i < NBUF * buf_len; i += NT + 64) stg0[i] = 0.f;   // padding k >= K stays zero
+    tc::fence_proxy_async_smem();
     if (tid == 0) {
         for (int i = 0; i < 4; ++i) tc::mbar_init(bar1 + i, 1);
+        for (int i = 0; i < 2; ++i) tc::mbar_init(full + i, 32);   // the producer's 32 lanes
         *sflag = 0;
     }
     if (warp == 0) tc::tmem_alloc(tslot, ncols);
@@ -424,45 +429,32 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
         rr = int(g - f * uint32_t(a.R));
         return true;
     };
-    // Copy tile t into staging buffer `stg` (rows past the end are skipped; the slicing
-    // treats them as zero).  Exactly one copy group is committed per call, empty or not,
-    // so that wait_group counts tiles.
-    auto prefetch = [&](long t, float *stg) {
+    // The coalesced layouts (contiguous KFAST tiles, 4-row groups of [k][row] tiles) put
+    // a thread's copies into other threads' staging rows.  KSLOW tiles (two staging
+    // buffers) are copied by the producer warp, whose `full` mbarrier tells the compute
+    // threads when a tile is in; KFAST and pair tiles (measured faster that way: pass 3
+    // and the pair pass have one buffer, and the next tile must be requested at once
+    // by many threads) are copied by the compute threads, with a barrier after the wait.
+    const bool use_prod = LOAD == LOAD_KSLOW && rvec;
+    const bool coal = !use_prod && (kcont || (LOAD == LOAD_PAIR && rvec));
+    // Copies of tile t into `stg` by issuer x of nx (nx a multiple of 32).
+    auto copy_coalesced = [&](long t, float *stg, int x, int nx) {
         int pp, rr;
-        if (LOAD == LOAD_KFAST && kcont) {
-            if (t < ntiles) {
-                const long g0 = t * kRows;
-                const int nrow = int(min(long(kRows), rows - g0));
-                const int nchk = nrow * (a.K >> 2);   // 16-byte chunks of the tile
-                const float *src = a.in + size_t(g0) * a.K;
-                for (int c = tid; c < nchk; c += NT) {
-                    const int rw = int(fast_div(uint32_t(c), a.divK4));
-                    float *dh = stg + rw * (Kp + 4) + 4 * (c - rw * (a.K >> 2));
-                    tc::cp_async16(dh, src + 4 * c);
-                    if (HL) tc::cp_async16(dh + stg_len, src + a.lo_off + 4 * c);
-                }
+        if (LOAD == LOAD_KFAST) {
+            const long g0 = t * kRows;
+            const int nrow = int(min(long(kRows), rows - g0));
+            const int nchk = nrow * (a.K >> 2);   // 16-byte chunks of the tile
+            const float *src = a.in + size_t(g0) * a.K;
+            for (int c = x; c < nchk; c += nx) {
+                const int rw = int(fast_div(uint32_t(c), a.divK4));
+                float *dh = stg + rw * (Kp + 4) + 4 * (c - rw * (a.K >> 2));
+                tc::cp_async16(dh, src + 4 * c);
+                if (HL) tc::cp_async16(dh + stg_len, src + a.lo_off + 4 * c);
             }
-        } else if (LOAD == LOAD_KFAST) {
-            if (locate(t, row, pp, rr)) {
-                const float *src = a.in + size_t(pp) * a.N + size_t(rr) * a.in_pitch + a.in_off;
-                float *dh = stg + row * (Kp + 4);
-                if (vec16) {
-                    for (int k = 4 * q; k < a.K; k += 4 * TPR) {
-                        tc::cp_async16(dh + k, src + k);
-                        if (HL) tc::cp_async16(dh + stg_len + k, src + a.lo_off + k);
-                    }
-                } else {   // the thread copies the elements of its own units
-                    for (int u = q; 4 * u < a.K; u += TPR)
-                        for (int k = 4 * u; k < min(a.K, 4 * u + 4); ++k) {
-                            tc::cp_async4(dh + k, src + k);
-                            if (HL) tc::cp_async4(dh + stg_len + k, src + a.lo_off + k);
-                        }
-                }
-            }
-        } else if (rvec) {
-            // thread -> rows 4g..4g+3 (g = lane) and lines k = warp, warp + NT/32, ...:
-            // a warp copies 512 contiguous bytes per line
-            const int g4 = 4 * (tid & 31);
+        } else {
+            // issuer -> rows 4g..4g+3 (g = x mod 32) and lines k = x / 32, + nx / 32, ...:
+            // 32 consecutive issuers copy 512 contiguous bytes per line
+            const int g4 = 4 * (x & 31);
             if (locate(t, g4, pp, rr)) {
                 if (LOAD == LOAD_PAIR) {
                     const int2 mn = a.pairs[pp];
@@ -470,26 +462,51 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
                     const float *src[4] = {a.psi_hi + size_t(a.occ_off + mn.x) * a.N + o,
                                            a.psi_lo + size_t(a.occ_off + mn.x) * a.N + o,
                                            a.psi_hi + size_t(mn.y) * a.N + o, a.psi_lo + size_t(mn.y) * a.N + o};
-                    for (int k = warp; k < a.K; k += NT / 32)
+                    for (int k = x >> 5; k < a.K; k += nx >> 5)
 #pragma unroll
                         for (int w = 0; w < 4; ++w)
                             tc::cp_async16(stg + w * stg_len + k * kRows + g4, src[w] + size_t(k) * a.R);
                 } else {
                     const float *src = a.in + size_t(pp) * a.N + a.in_off + rr;
-                    for (int k = warp; k < a.K; k += NT / 32) {
+                    for (int k = x >> 5; k < a.K; k += nx >> 5) {
                         tc::cp_async16(stg + k * kRows + g4, src + size_t(k) * a.R);
                         if (HL) tc::cp_async16(stg + stg_len + k * kRows + g4, src + a.lo_off + size_t(k) * a.R);
                     }
                 }
             }
-        } else if (locate(t, row, pp, rr)) {
-            if (LOAD == LOAD_PAIR) {
+        }
+    };
+    // Copies of tile t by the compute threads: coalesced (see above), or for ragged
+    // layouts each thread the elements of its own units of its own row (rows past the end
+    // are skipped; the slicing treats them as zero).  Exactly one copy group is committed
+    // per call, empty or not, so that wait_group counts tiles.
+    auto prefetch = [&](long t, float *stg) {
+        int pp, rr;
+        if (coal) {
+            if (t < ntiles) copy_coalesced(t, stg, tid, NT);
+        } else if (!use_prod && locate(t, row, pp, rr)) {
+            if (LOAD == LOAD_KFAST) {
+                const float *src = a.in + size_t(pp) * a.N + size_t(rr) * a.in_pitch + a.in_off;
+                float *dh = stg + row * (Kp + 4);
+                if (vec16) {
+                    for (int k = 4 * q; k < a.K; k += 4 * TPR) {
+                        tc::cp_async16(dh + k, src + k);
+                        if (HL) tc::cp_async16(dh + stg_len + k, src + a.lo_off + k);
+                    }
+                } else {
+                    for (int u = q; 4 * u < a.K; u += TPR)
+                        for (int k = 4 * u; k < min(a.K, 4 * u + 4); ++k) {
+                            tc::cp_async4(dh + k, src + k);
+                            if (HL) tc::cp_async4(dh + stg_len + k, src + a.lo_off + k);
+                        }
+                }
+            } else if (LOAD == LOAD_PAIR) {
                 const int2 mn = a.pairs[pp];
                 const size_t o = size_t(rr) + a.in_off;
                 const float *src[4] = {a.psi_hi + size_t(a.occ_off + mn.x) * a.N + o,
                                        a.psi_lo + size_t(a.occ_off + mn.x) * a.N + o,
                                        a.psi_hi + size_t(mn.y) * a.N + o, a.psi_lo + size_t(mn.y) * a.N + o};
-                for (int u = q; 4 * u < a.K; u += TPR)   // the elements of its own units
+                for (int u = q; 4 * u < a.K; u += TPR)
                     for (int k = 4 * u; k < min(a.K, 4 * u + 4); ++k)
 #pragma unroll
                         for (int w = 0; w < 4; ++w)
@@ -589,15 +606,40 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
     auto handoff = [&]() {
         tc::fence_proxy_async_smem();
         tc::tc_fence_before();
-        return tc::bar_red_or(kBarHandoff, NT + 32, *sflag != 0);
+        return tc::bar_red_or(kBarHandoff, NT + 64, *sflag != 0);
     };
 
-    if (tid >= NT) {
+    if (tid >= NT + 32) {
+        // ---- producer warp: the copies of tile t + NBUF go out once every compute thread
+        //      is done with its buffer (after the last hand-off of tile t, and after the
+        //      epilogue of tile t - 1 when that stages its output there) ----
+        const int lane = tid - NT - 32;
+        if (use_prod)
+            for (int jb = 0; jb < NBUF; ++jb) {
+                const long t0 = blockIdx.x + long(jb) * gridDim.x;
+                if (t0 < ntiles) {
+                    copy_coalesced(t0, stg0 + jb * buf_len, lane, 32);
+                    tc::cp_async_mbar_arrive_noinc(full + jb);
+                }
+            }
+        long it = 0;
+        for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+            if (tc::bar_red_or(kBarHandoff, NT + 64, false)) break;
+            if (DOUBLE && tc::bar_red_or(kBarHandoff, NT + 64, false)) break;
+            if (use_prod && ostage && !DOUBLE && it > 0) tc::bar_sync(kBarEpi, NT + 32);
+            const long tn = tile + long(NBUF) * gridDim.x;
+            if (use_prod && tn < ntiles) {
+                copy_coalesced(tn, stg0 + (it % NBUF) * buf_len, lane, 32);
+                tc::cp_async_mbar_arrive_noinc(full + it % NBUF);
+            }
+        }
+        tc::cp_async_wait_all();   // no copy may still target shared memory at exit
+    } else if (tid >= NT) {
         // ---- MMA warp: one hand-off per GEMM, in the compute threads' order ----
         long it = 0;
         for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
             const int st = int(it % NSETS);
-            if (tc::bar_red_or(kBarHandoff, NT + 32, *sflag != 0)) break;
+            if (tc::bar_red_or(kBarHandoff, NT + 64, *sflag != 0)) break;
             if (tid == NT) {
                 tc::tc_fence_after();
                 issue_gemm<MODE, S, SB>(set_tmem(st), Np, tc::smem_addr(set_A(st)), a_piece, sB1_addr, b_piece, sbo,
@@ -605,7 +647,7 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
                 tc::mma_commit(bar1 + st);
             }
             if (DOUBLE) {
-                if (tc::bar_red_or(kBarHandoff, NT + 32, *sflag != 0)) break;
+                if (tc::bar_red_or(kBarHandoff, NT + 64, *sflag != 0)) break;
                 if (tid == NT) {
                     tc::tc_fence_after();
                     issue_gemm<MODE, S, SB>(set_tmem(st), Np, tc::smem_addr(set_A(st)), a_piece, sB2_addr, b_piece, sbo,
@@ -624,7 +666,7 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
     // stored partial sums for K-blocks after the first; scaled by f(Lambda) when Fs is set).
     // With obuf (a free staging buffer) and ostage, through shared memory: every compute
     // thread must call it then, as it contains two compute-thread barriers.
-    auto epilogue = [&](long t, int st, float rs_out, const float *cs_out, float *obuf) {
+    auto epilogue = [&](long t, int st, float rs_out, const float *cs_out, float *obuf, bool to_producer) {
         if (ostage && obuf != nullptr) {
             const int opitch = Kp + 4;
             float *oh = obuf, *ol = obuf + kRows * opitch;
@@ -648,7 +690,8 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
                     *reinterpret_cast<float4 *>(dst + a.lo_off + 4 * c) =
                         *reinterpret_cast<const float4 *>(ol + rw * opitch + k);
             }
-            tc::bar_sync(kBarCompute, NT);   // obuf is free again
+            if (to_producer) tc::bar_sync(kBarEpi, NT + 32);   // obuf is free again (the producer refills it)
+            else tc::bar_sync(kBarCompute, NT);
             return;
         }
         int pp = 0, rr = 0;
@@ -745,7 +788,7 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
         if (NSETS == 1 && prev_tile >= 0) {   // one A buffer / TMEM set: finish t-1 first
             if (DOUBLE) wait_bar(bar2 + prev_set, ph2, prev_set);
             else wait_bar(bar1 + prev_set, ph1, prev_set);
-            epilogue(prev_tile, prev_set, prev_rs, prev_cs, nullptr);
+            epilogue(prev_tile, prev_set, prev_rs, prev_cs, nullptr, false);
             prev_tile = -1;
         }
         int p = 0, r = 0;
@@ -754,8 +797,12 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
         uint8_t *sA = set_A(st);
         // ---- slice tile -> A[st] (A[st] was last read by the GEMMs of tile it-2,
         //      which completed before that tile's epilogue) ----
-        tc::cp_async_wait_group<NBUF - 1>();  // this tile's copies (one group per tile) landed
-        if ((LOAD != LOAD_KFAST && rvec) || kcont) tc::bar_sync(kBarCompute, NT);   // rows copied by other threads
+        if (use_prod) {   // the producer's copies of this tile landed
+            if (!tc::mbar_wait_bounded(full + it % NBUF, uint32_t((it / NBUF) & 1), kWaitLimit)) atomicExch(sflag, 1);
+        } else {
+            tc::cp_async_wait_group<NBUF - 1>();   // own copies (one group per tile) landed
+            if (coal) tc::bar_sync(kBarCompute, NT);   // and every other thread's
+        }
         const float mx = row_max(active ? staged_max(stg) : 0.f);
         float s_in, rs1;
         scales(mx, s_in, rs1);
@@ -783,7 +830,7 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
         if (prev_tile >= 0) {
             if (DOUBLE) wait_bar(bar2 + prev_set, ph2, prev_set);
             else wait_bar(bar1 + prev_set, ph1, prev_set);
-            epilogue(prev_tile, prev_set, prev_rs, prev_cs, stg);
+            epilogue(prev_tile, prev_set, prev_rs, prev_cs, stg, use_prod && !DOUBLE);
         }
         if (!DOUBLE && ostage) prefetch(tile + long(NBUF) * gridDim.x, stg);
         float rs_out = rs1;
@@ -866,7 +913,7 @@ __global__ void __launch_bounds__(kRows * TPR + 32, 1) tc_pass_kernel(TcPassArgs
     if (prev_tile >= 0 && !tc::bar_red_or(kBarCompute, NT, *sflag != 0)) {
         if (DOUBLE) wait_bar(bar2 + prev_set, ph2, prev_set);
         else wait_bar(bar1 + prev_set, ph1, prev_set);
-        epilogue(prev_tile, prev_set, prev_rs, prev_cs, stg0);
+        epilogue(prev_tile, prev_set, prev_rs, prev_cs, stg0, false);
     }
     tc::cp_async_wait_all();   // no copy may still target shared memory at exit
     }   // compute threads
@@ -1092,13 +1139,13 @@ int launch_tc_pass_nb(Plan &P, int kind, int prec, const TcPassArgs &a, cudaStre
     }
     EXX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     int per_sm = 0;
-    EXX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRows * kTPR + 32, smem));
+    EXX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRows * kTPR + 64, smem));
     per_sm = std::max(1, std::min(per_sm, max_ctas));
     const long rows = long(a.nfields) * a.R;
     const long ntiles = (rows + kRows - 1) / kRows;
     const int grid = int(std::min<long>(ntiles, long(P.num_sms) * per_sm));
     int tb = timing_begin(P, kind, s);
-    kern<<<grid, kRows * kTPR + 32, smem, s>>>(a);
+    kern<<<grid, kRows * kTPR + 64, smem, s>>>(a);
     timing_end(P, tb, s);
     EXX_LAUNCH("tc_pass_kernel");
     P.launches++;
