@@ -499,13 +499,18 @@ def run_sweep(args):
     stream = torch.cuda.current_stream()
     prec_name = args.prec if args.prec != "auto" else "bf16x10"
     rows = []
-    for nc, blk in [(1, 1), (4, 2), (16, 4), (64, 8), (256, 8), (512, 8), (1024, 8)]:
+    for nc, blk in [(1, 1), (4, 2), (16, 4), (64, 8), (256, 8), (512, 8), (1024, 8), (1024, 16), (1024, 32)]:
         p = exx.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
         p.set_precision(prec_code(exx, prec_name))
         p.set_batch(nc, blk)
         ms = _apply_ms(exx, p, psi, f, psi, out, max(1, args.steps), max(1, args.warmup if nc > 16 else 1), stream)
-        rows.append({"n_c": nc, "block_orbitals": blk, "exx_apply_ms": ms, "launches": p.launch_count(),
-                     "pair_solves_per_s": s.unique_pairs() / (ms / 1e3)})
+        launches = p.launch_count()
+        p.set_timing(True)
+        p.apply(psi, f, psi, out=out)
+        kt = {k: round(v[0], 3) for k, v in p.timing().items()}
+        p.set_timing(False)
+        rows.append({"n_c": nc, "block_orbitals": blk, "exx_apply_ms": ms, "launches": launches,
+                     "pair_solves_per_s": s.unique_pairs() / (ms / 1e3), "kernel_ms": kt})
         p.close()
     best = max(rows, key=lambda r: r["pair_solves_per_s"])
     rec = {"metric": METRIC, "value": best["pair_solves_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,

@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(TcPassArgs
     // the same holds for NFAST outputs of a whole axis: the epilogue stages the tile in
     // shared memory and writes it back with consecutive lanes on consecutive 16 bytes
     const bool ostage = STORE == STORE_NFAST && (NSETS == 2 || DOUBLE) && vec_out && a.out_pitch == a.Kout &&
-                        a.out_off == 0 && !a.acc && !a.Fs && (a.Kout & 3) == 0;
+                        a.out_off == 0 && !a.acc && (a.Kout & 3) == 0;
     // row `rl` of tile t -> (field pp, row rr of the field); false past the last row
     auto locate = [&](long t, int rl, int &pp, int &rr) {
         const long gg = t * kRows + rl;
@@ -670,9 +670,26 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(TcPassArgs
         if (ostage && obuf != nullptr) {
             const int opitch = Kp + 4;
             float *oh = obuf, *ol = obuf + kRows * opitch;
+            int fp = 0, fr = 0;
+            const bool fact = a.Fs != nullptr && locate(t, row, fp, fr);
             for (int u = q; u < nunit; u += TPR) {
                 float v[4], vlo[4];
                 read4<MODE, NACC, HL>(set_tmem(st) + lane_q, Np, 4 * u, rs_out, cs_out, v, vlo);
+                if (fact) {   // f(Lambda) scaling of a finished forward product
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int col = 4 * u + e;
+                        const size_t fi = size_t(a.f_noff + min(col, a.Kout - 1)) * a.R + fr;
+                        const float fh = a.Fs[fi], fl = a.Fs_lo[fi];
+                        if (HL) {
+                            const float x = v[e] * fh;
+                            vlo[e] = fmaf(v[e], fh, -x) + fmaf(v[e], fl, vlo[e] * fh);
+                            v[e] = x;
+                        } else {
+                            v[e] = fmaf(v[e], fh, v[e] * fl);
+                        }
+                    }
+                }
                 *reinterpret_cast<float4 *>(oh + row * opitch + 4 * u) = make_float4(v[0], v[1], v[2], v[3]);
                 if (HL) *reinterpret_cast<float4 *>(ol + row * opitch + 4 * u) = make_float4(vlo[0], vlo[1], vlo[2], vlo[3]);
             }
