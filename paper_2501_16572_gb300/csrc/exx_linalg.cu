@@ -30,20 +30,26 @@ __device__ __forceinline__ void kmerge(KSum &a, const KSum &b)
 constexpr int kRedThreads = 256;
 constexpr int kRedBlocks = 512;
 
-// E partial sums over a fixed grid: element e = n*N + r handled by thread (e mod T);
-// every thread adds its elements in increasing e, the block merges in a fixed tree.
+// E partial sums over a fixed grid: thread t of T sums (f_c dV / 4) psi_c(r) v_c(r) over
+// the columns c in order and its points r = t, t + T, ... in plain FP64 (n N / T terms,
+// about 10^2..10^4: relative rounding far below 1e-13); the threads' sums are merged with
+// Neumaier compensation in a fixed tree, then the blocks' (reduce_partials_kernel).
 __global__ void __launch_bounds__(kRedThreads)
 energy_partial_kernel(const double *psi, int n, long ld, const double *f, const double *v, long ldv,
                       long N, double dV, KSum *partials)
 {
     __shared__ KSum sh[kRedThreads];
     KSum acc{0.0, 0.0};
-    const long total = long(n) * N;
     const long T = long(gridDim.x) * blockDim.x;
-    for (long e = long(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += T) {
-        long col = e / N, r = e - col * N;
-        double w = 0.25 * f[col] * dV;
-        kadd(acc, w * psi[col * ld + r] * v[col * ldv + r]);
+    const long t0 = long(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t0 < N) {
+        double s = 0.0;
+        for (int c = 0; c < n; ++c) {
+            const double *pc = psi + long(c) * ld, *vc = v + long(c) * ldv;
+            const double w = 0.25 * f[c] * dV;
+            for (long r = t0; r < N; r += T) s = fma(w * pc[r], vc[r], s);
+        }
+        acc.s = s;
     }
     sh[threadIdx.x] = acc;
     __syncthreads();
@@ -54,12 +60,19 @@ energy_partial_kernel(const double *psi, int n, long ld, const double *f, const 
     if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
 }
 
-__global__ void reduce_partials_kernel(const KSum *partials, int np, double *out)
+// The block partials merged in a fixed tree by one block of kRedThreads threads.
+__global__ void __launch_bounds__(kRedThreads) reduce_partials_kernel(const KSum *partials, int np, double *out)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ KSum sh[kRedThreads];
     KSum acc{0.0, 0.0};
-    for (int i = 0; i < np; ++i) kmerge(acc, partials[i]);
-    out[0] = acc.s + acc.c;
+    for (int i = threadIdx.x; i < np; i += kRedThreads) kmerge(acc, partials[i]);
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int stride = kRedThreads / 2; stride > 0; stride >>= 1) {
+        if (threadIdx.x < stride) kmerge(sh[threadIdx.x], sh[threadIdx.x + stride]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = sh[0].s + sh[0].c;
 }
 
 // ---- FP64 GEMMs (DFMA; GB300's FP64 rate makes these compute-bound) -----------------
@@ -218,6 +231,78 @@ cholesky_inverse_kernel(int n, const double *M, double *L, double *Linv, int *in
     }
 }
 
+// The same for n <= kCholSmemMax with everything in shared memory (column-major n x n):
+// right-looking Cholesky (column j: pivot, scale, rank-1 update of the trailing lower
+// triangle), then the inverse in place, columns from the right (unblocked triangular
+// inverse): X_jj = 1 / L_jj and X(j+1:, j) = -X_jj X(j+1:, j+1:) L(j+1:, j), the
+// triangular product into a scratch column.
+constexpr int kCholSmemMax = 128;
+__global__ void __launch_bounds__(kCholThreads)
+cholesky_inverse_smem_kernel(int n, const double *M, double *Linv, int *info_d)
+{
+    extern __shared__ double S[];   // n x n, S[i + n j], then n scratch values
+    double *y = S + n * n;
+    __shared__ int failed;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < n * n; e += blockDim.x) {
+        const int i = e % n, j = e / n;
+        S[e] = (i >= j) ? -0.5 * (M[i + size_t(n) * j] + M[j + size_t(n) * i]) : 0.0;
+    }
+    if (tid == 0) {
+        failed = 0;
+        info_d[0] = 0;
+    }
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {
+        if (tid == 0) {
+            const double d = S[j + n * j];
+            if (!(d > 0.0)) {
+                failed = 1;
+                info_d[0] = j + 1;
+            } else {
+                S[j + n * j] = sqrt(d);
+            }
+        }
+        __syncthreads();
+        if (failed) return;   // uniform: read after the barrier
+        const double djj = S[j + n * j];
+        for (int i = j + 1 + tid; i < n; i += blockDim.x) S[i + n * j] /= djj;
+        __syncthreads();
+        // trailing lower triangle: warps over its columns k, lanes over consecutive rows i
+        for (int k = j + 1 + (tid >> 5); k < n; k += blockDim.x >> 5) {
+            const double lk = S[k + n * j];
+            for (int i = k + (tid & 31); i < n; i += 32) S[i + n * k] -= S[i + n * j] * lk;
+        }
+        __syncthreads();
+    }
+    for (int j = n - 1; j >= 0; --j) {
+        const double xjj = 1.0 / S[j + n * j];
+        // y_i = sum_{k = j+1..i} X(i, k) L(k, j), rows i > j (X(j+1:, j+1:) is final): a
+        // thread per row (consecutive lanes read consecutive rows of a column), four
+        // partial sums against the FMA latency
+        for (int i = j + 1 + tid; i < n; i += blockDim.x) {
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            int k = j + 1;
+            for (; k + 3 <= i; k += 4) {
+                s0 = fma(S[i + n * k], S[k + n * j], s0);
+                s1 = fma(S[i + n * (k + 1)], S[k + 1 + n * j], s1);
+                s2 = fma(S[i + n * (k + 2)], S[k + 2 + n * j], s2);
+                s3 = fma(S[i + n * (k + 3)], S[k + 3 + n * j], s3);
+            }
+            for (; k <= i; ++k) s0 = fma(S[i + n * k], S[k + n * j], s0);
+            y[i] = (s0 + s1) + (s2 + s3);
+        }
+        __syncthreads();
+        for (int i = j + 1 + tid; i < n; i += blockDim.x) S[i + n * j] = -xjj * y[i];
+        if (tid == 0) S[j + n * j] = xjj;
+        __syncthreads();
+    }
+    for (int e = tid; e < n * n; e += blockDim.x) {
+        const int i = e % n, j = e / n;
+        Linv[e] = (i >= j) ? S[e] : 0.0;
+    }
+}
+
 }  // namespace
 
 int energy_fp64(Plan &P, const double *psi, int n, long ld, const double *f, const double *v, long ld_v,
@@ -230,7 +315,7 @@ int energy_fp64(Plan &P, const double *psi, int n, long ld, const double *f, con
     int tb = timing_begin(P, EXX_TIMING_ENERGY, s);
     energy_partial_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(psi, n, ld, f, v, ld_v, P.N, P.dV, parts);
     EXX_LAUNCH("energy_partial_kernel");
-    reduce_partials_kernel<<<1, 32, 0, s>>>(parts, kRedBlocks, res);
+    reduce_partials_kernel<<<1, kRedThreads, 0, s>>>(parts, kRedBlocks, res);
     timing_end(P, tb, s);
     EXX_LAUNCH("reduce_partials_kernel");
     P.launches += 2;
@@ -292,12 +377,23 @@ int gemm_fp64_nn(Plan &P, int M, int Nc, int K, const double *A, long lda, const
 int cholesky_neg_sym_and_inverse(Plan &P, int n, const double *M, double *Linv, int *info_d,
                                  cudaStream_t s)
 {
-    if (int rc = dev_reserve(P.small_ws, size_t(n) * n * sizeof(double))) return rc;
-    double *L = static_cast<double *>(P.small_ws.p);
+    if (n > kCholSmemMax) {
+        if (int rc = dev_reserve(P.small_ws, size_t(n) * n * sizeof(double))) return rc;
+    }
     int tb = timing_begin(P, EXX_TIMING_CHOL, s);
-    cholesky_inverse_kernel<<<1, kCholThreads, 0, s>>>(n, M, L, Linv, info_d);
-    timing_end(P, tb, s);
-    EXX_LAUNCH("cholesky_inverse_kernel");
+    if (n <= kCholSmemMax) {
+        const size_t smem = (size_t(n) * n + n) * sizeof(double);
+        EXX_CUDA(cudaFuncSetAttribute(cholesky_inverse_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      int(smem)));
+        cholesky_inverse_smem_kernel<<<1, kCholThreads, smem, s>>>(n, M, Linv, info_d);
+        timing_end(P, tb, s);
+        EXX_LAUNCH("cholesky_inverse_smem_kernel");
+    } else {
+        double *L = static_cast<double *>(P.small_ws.p);
+        cholesky_inverse_kernel<<<1, kCholThreads, 0, s>>>(n, M, L, Linv, info_d);
+        timing_end(P, tb, s);
+        EXX_LAUNCH("cholesky_inverse_kernel");
+    }
     P.launches++;
     return EXX_OK;
 }

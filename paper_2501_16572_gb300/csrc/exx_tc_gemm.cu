@@ -25,7 +25,8 @@ namespace exx {
 
 namespace {
 
-constexpr int kT = 128;              // rows of A per tile (TMEM lanes, threads)
+constexpr int kT = 128;              // rows of A per tile (TMEM lanes)
+constexpr int kThreads = 4 * kT;     // 4 threads per row (slicing, drain by column groups)
 constexpr int kTN = 96;              // rows of B per tile (output columns)
 constexpr int kLev = 5;              // level accumulators: digit products with i + j <= 4
 constexpr int kSub = 64;             // k per operand image
@@ -85,18 +86,20 @@ __device__ __forceinline__ void store_digits(uint8_t *img, int row, int u, const
     }
 }
 
-__global__ void __launch_bounds__(kT, 1) tc_gemm_kernel(GemmArgs a)
+__global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(GemmArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     constexpr uint32_t piece = kT * kSub * 2;       // one A digit image: 128 rows x 64 k bf16
     constexpr uint32_t bpiece = kTN * kSub * 2;     // one B digit image: 96 rows
     constexpr uint32_t sbo = kSub * 2 * 8;          // bytes per 8-row group
     uint8_t *sA = smem, *sB = smem + 4 * piece;
-    int *sh_b = reinterpret_cast<int *>(sB + 4 * bpiece);   // per B row: its scale shift
+    int *sh_a = reinterpret_cast<int *>(sB + 4 * bpiece);   // per A row: its scale shift
+    int *sh_b = sh_a + kT;                                   // per B row
     uint64_t *bar = reinterpret_cast<uint64_t *>(sh_b + kTN);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
     int *sflag = reinterpret_cast<int *>(tslot + 1);
-    const int t = threadIdx.x, warp = t >> 5;
+    const int t = threadIdx.x, warp = t >> 5, row = t & (kT - 1), q = t / kT;
+    constexpr int kWarps = kThreads / 32;
     if (t == 0) {
         tc::mbar_init(bar, 1);
         *sflag = 0;
@@ -106,51 +109,85 @@ __global__ void __launch_bounds__(kT, 1) tc_gemm_kernel(GemmArgs a)
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tslot;
-    const uint32_t lane = uint32_t(warp * 32) << 16;
+    const uint32_t lane = uint32_t((warp & 3) * 32) << 16;   // this warp's TMEM lane quarter
     const uint32_t idesc = tc::instr_desc(false, kTN);
     const uint32_t a_addr = tc::smem_addr(sA), b_addr = tc::smem_addr(sB);
 
-    const int i = blockIdx.x * kT + t, j = blockIdx.y * kTN + t;   // this thread's A row, B row
-    const bool arow = i < a.m, brow = t < kTN && j < a.n;
-    const double *Ar = a.A + (arow ? long(i) * a.as_i : 0);
-    const double *Br = a.B + (brow ? long(j) * a.bs_j : 0);
+    const int i0 = blockIdx.x * kT, j0 = blockIdx.y * kTN;
+    const int i = i0 + row;              // this thread's output row (TMEM lane)
+    const bool arow = i < a.m;
     const long kbeg = long(blockIdx.z) * a.kper, kend = min(a.K, kbeg + a.kper);
     double *D = a.D + long(blockIdx.z) * a.dz;
     uint32_t phase = 0;
     bool first = true;
-    for (long c0 = kbeg; c0 < kend; c0 += kChunk) {
-        const long c1 = min(kend, c0 + kChunk);
-        // scales of this chunk: largest exponent field of the own A row and B row
-        int EA = 0, EB = 0;
-        for (long k = c0; k < c1; ++k) {
-            if (arow) EA = max(EA, exp_field(Ar[k * a.as_k]));
-            if (brow) EB = max(EB, exp_field(Br[k * a.bs_k]));
+    // Per-row shifts of a chunk [c0, c1) and digit images of a sub-step [k0, k0 + 64) for an
+    // operand X of R tile rows (global rows base + r < valid, element (row, k) at
+    // X[row sr + k sk]).  k-contiguous operands (sk = 1) are read a warp per row,
+    // consecutive lanes on consecutive k; the others by threads per row, consecutive lanes
+    // on consecutive rows: both coalesced.
+    auto shifts = [&](const double *X, long sr, long sk, int base, int valid, int R, int *sh, long c0, long c1) {
+        if (sk == 1) {
+            for (int r = warp; r < R; r += kWarps) {
+                int E = 0;
+                if (base + r < valid) {
+                    const double *xr = X + long(base + r) * sr;
+                    for (long k = c0 + (t & 31); k < c1; k += 32) E = max(E, exp_field(xr[k]));
+                }
+                for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
+                if ((t & 31) == 0) sh[r] = 1052 - max(E, 100);   // rows below 2^-922 are zero rows
+            }
+        } else if (t < R) {
+            int E = 0;
+            if (base + t < valid) {
+                const double *xr = X + long(base + t) * sr;
+                for (long k = c0; k < c1; ++k) E = max(E, exp_field(xr[k * sk]));
+            }
+            sh[t] = 1052 - max(E, 100);
         }
-        EA = max(EA, 100);   // rows below 2^-922 are zero rows
-        EB = max(EB, 100);
-        const int shA = 1052 - EA, shB = 1052 - EB;
-        if (t < kTN) sh_b[t] = shB;
-        for (int sub = 0; sub < kSubs; ++sub) {
-            const long k0 = c0 + long(sub) * kSub;
-            if (k0 >= c1) break;   // uniform
-            for (int u = 0; u < kSub / 4; ++u) {
-                float qa[4][4], qb[4][4];
+    };
+    auto digits_sub = [&](const double *X, long sr, long sk, int base, int valid, int R, const int *sh,
+                          uint8_t *img, uint32_t pc, long k0, long c1) {
+        if (sk == 1) {
+            const int l2 = 2 * (t & 31);   // this lane's k: k0 + l2, k0 + l2 + 1
+            for (int r = warp; r < R; r += kWarps) {
+                const bool ok = base + r < valid;
+                const double *xr = ok ? X + long(base + r) * sr : X;
+                const long k = k0 + l2;
+                float d0[4], d1[4];
+                digits4(ok && k < c1 ? xr[k] : 0.0, sh[r], d0);
+                digits4(ok && k + 1 < c1 ? xr[k + 1] : 0.0, sh[r], d1);
+#pragma unroll
+                for (int lv = 0; lv < 4; ++lv)
+                    *reinterpret_cast<uint32_t *>(img + lv * pc + gimg_off(r, l2 >> 3) + (l2 & 7) * 2) =
+                        __byte_perm(__float_as_uint(d0[lv]), __float_as_uint(d1[lv]), 0x7632);
+            }
+        } else if (row < R) {   // 4 threads per row, 4-k units u = q, q + 4, ...
+            const bool ok = base + row < valid;
+            const double *xr = ok ? X + long(base + row) * sr : X;
+            for (int u = q; u < kSub / 4; u += kThreads / kT) {
+                float dq[4][4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const long k = k0 + 4 * u + e;
-                    const bool in = k < c1;
-                    float da[4], db[4];
-                    digits4(arow && in ? Ar[k * a.as_k] : 0.0, shA, da);
-                    digits4(brow && in ? Br[k * a.bs_k] : 0.0, shB, db);
+                    float d[4];
+                    digits4(ok && k < c1 ? xr[k * sk] : 0.0, sh[row], d);
 #pragma unroll
-                    for (int l = 0; l < 4; ++l) {
-                        qa[l][e] = da[l];
-                        qb[l][e] = db[l];
-                    }
+                    for (int lv = 0; lv < 4; ++lv) dq[lv][e] = d[lv];
                 }
-                store_digits(sA, t, u, qa, piece);
-                if (t < kTN) store_digits(sB, t, u, qb, bpiece);
+                store_digits(img, row, u, dq, pc);
             }
+        }
+    };
+    for (long c0 = kbeg; c0 < kend; c0 += kChunk) {
+        const long c1 = min(kend, c0 + kChunk);
+        shifts(a.A, a.as_i, a.as_k, i0, a.m, kT, sh_a, c0, c1);
+        shifts(a.B, a.bs_j, a.bs_k, j0, a.n, kTN, sh_b, c0, c1);
+        __syncthreads();   // every row's shift is visible
+        for (int sub = 0; sub < kSubs; ++sub) {
+            const long k0 = c0 + long(sub) * kSub;
+            if (k0 >= c1) break;   // uniform
+            digits_sub(a.A, a.as_i, a.as_k, i0, a.m, kT, sh_a, sA, piece, k0, c1);
+            digits_sub(a.B, a.bs_j, a.bs_k, j0, a.n, kTN, sh_b, sB, bpiece, k0, c1);
             tc::fence_proxy_async_smem();
             tc::tc_fence_before();
             __syncthreads();
@@ -171,11 +208,14 @@ __global__ void __launch_bounds__(kT, 1) tc_gemm_kernel(GemmArgs a)
             if (!tc::mbar_wait_bounded(bar, phase, kGemmWait)) atomicExch(sflag, 1);
             phase ^= 1u;
             tc::tc_fence_after();
+            __syncthreads();   // the images may be rewritten
         }
-        __syncthreads();   // the shift of every B row is visible
-        if (*sflag) break;
-        // drain: D(i, j) (+)= alpha 2^(-shA - shB) sum_l L_l 2^(48 - 8 l)
-        for (int cg = 0; cg < kTN / 8; ++cg) {
+        if (*sflag) break;   // uniform: set before the last barrier
+        // drain: D(i, j) (+)= alpha 2^(48 - shA - shB) sum_l L_l 2^(-8 l).  The levels are
+        // combined in FP32 down to level 1 (rounding ~2^-32 of level 0's scale), level 0 is
+        // added with TwoSum, and the pair is scaled and accumulated in FP64.
+        const int shA = sh_a[row];
+        for (int cg = q; cg < kTN / 8; cg += kThreads / kT) {   // this thread's column groups
             uint32_t r[kLev][8];
 #pragma unroll
             for (int l = 0; l < kLev; ++l) tc::tmem_ld8_issue(tmem + lane + uint32_t(l * kTN + cg * 8), r[l]);
@@ -186,16 +226,20 @@ __global__ void __launch_bounds__(kT, 1) tc_gemm_kernel(GemmArgs a)
                 for (int e = 0; e < 8; ++e) tc::order_after_wait(r[l][e]);
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
-                const int col = blockIdx.y * kTN + cg * 8 + e;
+                const int col = j0 + cg * 8 + e;
                 if (!arow || col >= a.n) continue;
-                double v = double(__uint_as_float(r[4][e]));
-                v = v * (1.0 / 256.0) + double(__uint_as_float(r[3][e]));
-                v = v * (1.0 / 256.0) + double(__uint_as_float(r[2][e]));
-                v = v * (1.0 / 256.0) + double(__uint_as_float(r[1][e]));
-                v = v * (1.0 / 256.0) + double(__uint_as_float(r[0][e]));
+                float tl = __uint_as_float(r[4][e]);
+                tl = tl * (1.f / 256.f) + __uint_as_float(r[3][e]);
+                tl = tl * (1.f / 256.f) + __uint_as_float(r[2][e]);
+                tl = tl * (1.f / 256.f) + __uint_as_float(r[1][e]);
+                tl *= 1.f / 256.f;
+                const float l0 = __uint_as_float(r[0][e]);
+                const float h = l0 + tl, bp = h - l0;
+                const float lo = (l0 - (h - bp)) + (tl - bp);
                 // v 2^48 2^-shA 2^-shB alpha, the powers of two as one exponent (a product
                 // below the normal range is zero: both rows were below 2^-900)
                 const int sc = min(48 - shA - sh_b[cg * 8 + e], 1023);
+                double v = double(h) + double(lo);
                 v = sc < -1022 ? 0.0 : a.alpha * (v * __longlong_as_double(static_cast<long long>(sc + 1023) << 52));
                 double *dp = D + long(i) * a.ds_i + long(col) * a.ds_j;
                 *dp = first ? v : *dp + v;
@@ -205,9 +249,9 @@ __global__ void __launch_bounds__(kT, 1) tc_gemm_kernel(GemmArgs a)
         __syncthreads();
         first = false;
     }
-    if (first && *sflag == 0 && arow) {   // empty k range: the slot still holds a sum (zero)
+    if (first && *sflag == 0 && arow && q == 0) {   // empty k range: the slot holds a zero sum
         for (int c = 0; c < kTN; ++c) {
-            const int col = blockIdx.y * kTN + c;
+            const int col = j0 + c;
             if (col < a.n) D[long(i) * a.ds_i + long(col) * a.ds_j] = 0.0;
         }
     }
@@ -278,10 +322,10 @@ int tc_gemm(Plan &P, int m, int n, long K, const double *A, long as_i, long as_k
         a.ds_j = ds_j;
         a.dz = 0;
     }
-    const size_t smem = 4 * size_t(kT + kTN) * kSub * 2 + kTN * sizeof(int) + 64;
+    const size_t smem = 4 * size_t(kT + kTN) * kSub * 2 + (kT + kTN) * sizeof(int) + 64;
     EXX_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     int tb = timing_begin(P, EXX_TIMING_GEMM, s);
-    tc_gemm_kernel<<<dim3(unsigned(mt), unsigned(nt), unsigned(Z)), kT, smem, s>>>(a);
+    tc_gemm_kernel<<<dim3(unsigned(mt), unsigned(nt), unsigned(Z)), kThreads, smem, s>>>(a);
     timing_end(P, tb, s);
     EXX_LAUNCH("tc_gemm_kernel");
     P.launches++;
