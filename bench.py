@@ -725,9 +725,24 @@ def cpu_sample(s, budget_s=15.0):
 
 def cpu_baseline(s):
     v, cols, solves, dt, cores = cpu_sample(s)
-    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{cols} output column(s) of the workload = {solves} pair Poisson solves "
-                      f"(plain C FP64 oracle, {dt:.1f} s)"}
+    rec = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{cols} output column(s) of the workload = {solves} pair Poisson solves "
+                     f"(plain C FP64 oracle, {dt:.1f} s)"}
+    # one core on the 24^3 Dirichlet workload (16 orbitals, f = 2): the whole apply
+    import oracle
+    import synth
+    c1 = synth.config1()
+    orc = oracle.Plan(c1.n, c1.h, c1.bc, c1.fd_order, c1.kernel, c1.omega)
+    oracle.set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        orc.exx_apply(c1.psi, c1.f, c1.psi)
+        dt1 = time.perf_counter() - t0
+    finally:
+        oracle.set_num_threads(cores)
+    rec["single_core_24cube_16orb"] = {"value": c1.n_orb * c1.n_occ / dt1, "unit": UNIT, "cores": 1,
+                                       "seconds": dt1, "pair_solves": c1.n_orb * c1.n_occ}
+    return rec
 
 
 def run_reference(args):

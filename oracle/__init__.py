@@ -64,6 +64,7 @@ def lib():
         L.exo_ace_apply.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _D, _D, ctypes.c_int, _D]
         L.exo_set_mutation.argtypes = [ctypes.c_int]
         L.exo_num_threads.restype = ctypes.c_int
+        L.exo_set_num_threads.argtypes = [ctypes.c_int]
         _lib = L
     return _lib
 
@@ -78,6 +79,11 @@ def _c64(a):
 
 def num_threads() -> int:
     return int(lib().exo_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Thread count of the oracle's OpenMP loops (for timing on n cores)."""
+    lib().exo_set_num_threads(int(n))
 
 
 def set_mutation(m: int) -> None:

@@ -61,6 +61,16 @@
 static int g_mutation = 0;
 void exo_set_mutation(int m) { g_mutation = m; }
 
+/* Thread count of the OpenMP loops (timing of the oracle on a given number of cores). */
+void exo_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 int exo_num_threads(void)
 {
 #ifdef _OPENMP
