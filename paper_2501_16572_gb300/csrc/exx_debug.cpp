@@ -69,4 +69,10 @@ int exx_debug_fastdiv(unsigned d, int count, const unsigned *n, unsigned *q)
     return EXX_OK;
 }
 
+int exx_debug_wait_timeout(int *status_h)
+{
+    if (!status_h) return EXX_ERR_INVALID_ARG;
+    return exx::tc_wait_timeout_probe(status_h);
+}
+
 }  // extern "C"

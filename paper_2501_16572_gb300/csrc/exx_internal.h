@@ -194,6 +194,7 @@ int tc_finalize(Plan &P, int n_in, double *out, long ld_out, cudaStream_t s);
 int tc_check_error(Plan &P, cudaStream_t s);
 bool tc_is_hilo(int prec);
 int tc_unit_gemm(int tf32, int n, int k, const float *A, const float *B, float *D, int *err);
+int tc_wait_timeout_probe(int *status_h);
 
 // reductions, GEMM, Cholesky (exx_linalg.cu)
 int energy_fp64(Plan &P, const double *psi, int n, long ld, const double *f, const double *v,

@@ -1461,6 +1461,36 @@ int tc_check_error(Plan &P, cudaStream_t s)
     return EXX_OK;
 }
 
+namespace {
+// The bounded wait of the pass kernels on a barrier that nothing completes: the poll limit
+// runs out, the kernel records the timeout in the error word and returns normally.
+__global__ void tc_wait_timeout_kernel(uint32_t limit, int *err)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) tc::mbar_init(&bar, 1);
+    __syncthreads();
+    if (!tc::mbar_wait_bounded(&bar, 0, limit) && threadIdx.x == 0) atomicExch(err, 1);
+}
+}  // namespace
+
+int tc_wait_timeout_probe(int *status_h)
+{
+    int *err = nullptr;
+    EXX_CUDA(cudaMalloc(&err, sizeof(int)));
+    cudaError_t e = cudaMemset(err, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        tc_wait_timeout_kernel<<<1, 32>>>(1u << 12, err);
+        e = cudaGetLastError();
+    }
+    int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(err);
+    if (e != cudaSuccess) return cuda_fail(e, "tc_wait_timeout_probe");
+    *status_h = h ? EXX_ERR_TIMEOUT : EXX_OK;
+    if (h) set_error("a bounded mbarrier wait ran out (wait-timeout probe)");
+    return EXX_OK;
+}
+
 int tc_unit_gemm(int tf32, int n, int k, const float *A, const float *B, float *D, int *err)
 {
     const int es = tf32 ? 4 : 2;

@@ -228,3 +228,18 @@ def test_split_ace_on_tensor_cores_matches_oracle(exx, case):
     X = xi.cpu().numpy()
     want = -s.dV * (X.T @ (X @ phi.T)).T
     assert pm.rel(got, want) < 1e-8
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(exx):
+    """A wait that runs out (a barrier nothing completes) comes back as EXX_ERR_TIMEOUT
+    from the device error word, and the GPU keeps working afterwards."""
+    L = exx.load()
+    L.exx_debug_wait_timeout.argtypes = [ctypes.POINTER(ctypes.c_int)]
+    st = ctypes.c_int(-1)
+    assert L.exx_debug_wait_timeout(ctypes.byref(st)) == 0
+    assert st.value == exx.EXX_ERR_TIMEOUT
+    # the context is intact: a small apply still matches the oracle
+    s = synth.small_system(n=(10, 9, 8), h=0.4, bc=(0, 0, 0), n_orb=4, kernel=0, seed=2)
+    plan, psi, f, vx, e = _apply(exx, s, SPLIT["bf16x10"][0])
+    orc = oracle.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    assert pm.rel(vx.cpu().numpy(), orc.exx_apply(s.psi[:s.n_occ], s.f, s.psi)) < 1e-6
