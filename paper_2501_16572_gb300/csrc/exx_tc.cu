@@ -25,11 +25,13 @@
 #include "exx_internal.h"
 #include "tc_ptx.cuh"
 
+#include <cuda.h>   // CUtensorMap and its enums (the encoder is fetched at run time)
 #include <cuda_bf16.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 namespace exx {
 
@@ -70,7 +72,7 @@ inline size_t image_bytes(int prec, int Np)
     const PrecInfo pi = prec_info(prec);
     size_t b = size_t(pi.SB) * Np * Np * pi.es;
     if (pi.mode == MODE_FIXED_BF16) b += size_t(Np) * 4;
-    return (b + 15) & ~size_t(15);
+    return (b + 127) & ~size_t(127);   // keeps the staging buffers behind the images 128-byte aligned
 }
 
 // canonical K-major no-swizzle image: byte offset of (row, 16-byte chunk c)
@@ -310,6 +312,11 @@ __device__ __forceinline__ void read4(uint32_t d, int Np, int c0, float rs, cons
 // Warps w, w+4, ... see TMEM lane quarter w%4.  CTAs loop over tiles; the next tile's rows
 // arrive by cp.async while the current tile's MMAs and epilogue run.
 struct TcPassArgs {
+    // [k][row] tiles by TMA (use_tma): tm[0] hi plane, tm[1] lo plane of the input (pair
+    // pass: of the orbitals), each a 3D tensor (R rows, n_d lines, fields or orbitals)
+    // with a 128 x K x 1 box; koff = first line of this K-block
+    CUtensorMap tm[2];
+    int use_tma, koff;
     int nfields, R, K, Np;          // K = contracted length of this block, Np = padded block size
     int Kout;                       // outputs of this block (K = Kout = n_d when not blocked)
     int in_pitch, out_pitch;        // KFAST / NFAST row pitch (= n_d)
@@ -334,7 +341,7 @@ struct TcPassArgs {
 };
 
 template <int MODE, int S, int SB, bool HL, int LOAD, int STORE, bool DOUBLE, int TPR, int NBUF, int NSETS>
-__global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(TcPassArgs a)
+__global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __grid_constant__ TcPassArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     constexpr int ES = MODE == MODE_FLOAT_TF32 ? 4 : 2;
@@ -387,7 +394,8 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(TcPassArgs
     tc::fence_proxy_async_smem();
     if (tid == 0) {
         for (int i = 0; i < 4; ++i) tc::mbar_init(bar1 + i, 1);
-        for (int i = 0; i < 2; ++i) tc::mbar_init(full + i, 32);   // the producer's 32 lanes
+        // the producer's 32 cp.async arrivals, or its one expect_tx arrival (TMA)
+        for (int i = 0; i < 2; ++i) tc::mbar_init(full + i, a.use_tma ? 1 : 32);
         *sflag = 0;
     }
     if (warp == 0) tc::tmem_alloc(tslot, ncols);
@@ -435,8 +443,28 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(TcPassArgs
     // threads when a tile is in; KFAST and pair tiles (measured faster that way: pass 3
     // and the pair pass have one buffer, and the next tile must be requested at once
     // by many threads) are copied by the compute threads, with a barrier after the wait.
-    const bool use_prod = LOAD == LOAD_KSLOW && rvec;
+    const bool use_tma = a.use_tma != 0;   // [k][row] tiles of fields of R = multiple of 128 rows
+    const bool use_prod = use_tma || (LOAD == LOAD_KSLOW && rvec);
     const bool coal = !use_prod && (kcont || (LOAD == LOAD_PAIR && rvec));
+    // Producer, TMA: one box per plane (128 rows x K lines), the tile being one field's
+    // rows; expect_tx announces the bytes, the boxes complete them.
+    auto fill_tma = [&](long t, float *stg, uint64_t *fb) {
+        const uint32_t g0 = uint32_t(t * kRows);
+        const uint32_t f = fast_div(g0, a.divR);
+        const int rr = int(g0 - f * uint32_t(a.R));
+        constexpr int NPL = LOAD == LOAD_PAIR ? 4 : (HL ? 2 : 1);
+        tc::mbar_arrive_expect_tx(fb, uint32_t(NPL) * uint32_t(kRows) * uint32_t(a.K) * 4u);
+        if (LOAD == LOAD_PAIR) {
+            const int2 mn = a.pairs[f];
+            tc::tma_load_3d(stg, &a.tm[0], rr, a.koff, a.occ_off + mn.x, fb);
+            tc::tma_load_3d(stg + stg_len, &a.tm[1], rr, a.koff, a.occ_off + mn.x, fb);
+            tc::tma_load_3d(stg + 2 * stg_len, &a.tm[0], rr, a.koff, mn.y, fb);
+            tc::tma_load_3d(stg + 3 * stg_len, &a.tm[1], rr, a.koff, mn.y, fb);
+        } else {
+            tc::tma_load_3d(stg, &a.tm[0], rr, a.koff, int(f), fb);
+            if (HL) tc::tma_load_3d(stg + stg_len, &a.tm[1], rr, a.koff, int(f), fb);
+        }
+    };
     // Copies of tile t into `stg` by issuer x of nx (nx a multiple of 32).
     auto copy_coalesced = [&](long t, float *stg, int x, int nx) {
         int pp, rr;
@@ -614,13 +642,21 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(TcPassArgs
         //      is done with its buffer (after the last hand-off of tile t, and after the
         //      epilogue of tile t - 1 when that stages its output there) ----
         const int lane = tid - NT - 32;
+        int fills0 = 0, fills1 = 0;   // fills issued per staging buffer
+        auto fill = [&](long tt, int b) {
+            if (use_tma) {
+                if (lane == 0) fill_tma(tt, stg0 + b * buf_len, full + b);
+            } else {
+                copy_coalesced(tt, stg0 + b * buf_len, lane, 32);
+                tc::cp_async_mbar_arrive_noinc(full + b);
+            }
+            if (b == 0) ++fills0;
+            else ++fills1;
+        };
         if (use_prod)
             for (int jb = 0; jb < NBUF; ++jb) {
                 const long t0 = blockIdx.x + long(jb) * gridDim.x;
-                if (t0 < ntiles) {
-                    copy_coalesced(t0, stg0 + jb * buf_len, lane, 32);
-                    tc::cp_async_mbar_arrive_noinc(full + jb);
-                }
+                if (t0 < ntiles) fill(t0, jb);
             }
         long it = 0;
         for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
@@ -628,12 +664,13 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(TcPassArgs
             if (DOUBLE && tc::bar_red_or(kBarHandoff, NT + 64, false)) break;
             if (use_prod && ostage && !DOUBLE && it > 0) tc::bar_sync(kBarEpi, NT + 32);
             const long tn = tile + long(NBUF) * gridDim.x;
-            if (use_prod && tn < ntiles) {
-                copy_coalesced(tn, stg0 + (it % NBUF) * buf_len, lane, 32);
-                tc::cp_async_mbar_arrive_noinc(full + it % NBUF);
-            }
+            if (use_prod && tn < ntiles) fill(tn, int(it % NBUF));
         }
         tc::cp_async_wait_all();   // no copy may still target shared memory at exit
+        if (use_tma) {   // nor a box: only the last fill of a buffer can be unconsumed (after a stop)
+            if (fills0 > 0) tc::mbar_wait_bounded(full, uint32_t((fills0 - 1) & 1), kWaitLimit);
+            if (fills1 > 0) tc::mbar_wait_bounded(full + 1, uint32_t((fills1 - 1) & 1), kWaitLimit);
+        }
     } else if (tid >= NT) {
         // ---- MMA warp: one hand-off per GEMM, in the compute threads' order ----
         long it = 0;
@@ -707,8 +744,12 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(TcPassArgs
                     *reinterpret_cast<float4 *>(dst + a.lo_off + 4 * c) =
                         *reinterpret_cast<const float4 *>(ol + rw * opitch + k);
             }
-            if (to_producer) tc::bar_sync(kBarEpi, NT + 32);   // obuf is free again (the producer refills it)
-            else tc::bar_sync(kBarCompute, NT);
+            if (to_producer) {   // obuf is free again (the producer refills it, maybe by TMA)
+                tc::fence_proxy_async_smem();
+                tc::bar_sync(kBarEpi, NT + 32);
+            } else {
+                tc::bar_sync(kBarCompute, NT);
+            }
             return;
         }
         int pp = 0, rr = 0;
@@ -1183,6 +1224,41 @@ int launch_tc_pass(Plan &P, int kind, int prec, const TcPassArgs &a, cudaStream_
     return launch_tc_pass_nb<MODE, S, SB, HL, LOAD, STORE, DOUBLE, 1, 1>(P, kind, prec, a, s);
 }
 
+// cuTensorMapEncodeTiled, fetched from the driver through the runtime once (no link
+// dependency on the driver library; without a driver the TMA path is simply not taken).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled()
+{
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// 3D FP32 tensor (R rows fastest, L lines, F fields) at `base`, lines R apart, fields N
+// apart, read in 128 x K x 1 boxes.  Requires 16-byte aligned base and R, N multiples of 4.
+bool make_tile_map(CUtensorMap *m, const float *base, long R, long L, long F, long N, int K)
+{
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn || (reinterpret_cast<uintptr_t>(base) & 15) || (R & 3) || (N & 3) || K < 1 || K > 256) return false;
+    const cuuint64_t dims[3] = {cuuint64_t(R), cuuint64_t(L), cuuint64_t(F)};
+    const cuuint64_t strides[2] = {cuuint64_t(R) * 4, cuuint64_t(N) * 4};
+    const cuuint32_t box[3] = {cuuint32_t(kRows), cuuint32_t(K), 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // One launch of pass kernel `kind` (0..4 = P1..P5; 5 = P3's forward half alone, 6 = its
 // inverse half alone, used when the y axis is cut into blocks).
 template <int MODE, int S, int SB, bool HL>
@@ -1254,6 +1330,21 @@ int solve_batch_t(Plan &P, int prec, const int2 *pairs_d, int nfields, float *bu
                 a.acc = c > 0;
                 a.B1 = img1 + size_t(c * nb + h) * a.img_bytes;
                 a.B2 = kind == 2 ? static_cast<const uint8_t *>(P.Btc[prec][3].p) : nullptr;
+                // [k][row] inputs of fields of R = 128 m rows: one TMA box per plane per tile
+                a.use_tma = 0;
+                a.koff = c * bs;
+                if ((g.load == LOAD_PAIR || g.load == LOAD_KSLOW) && g.R % kRows == 0 && (a.lo_off & 3) == 0) {
+                    bool ok;
+                    if (g.load == LOAD_PAIR) {
+                        const long ncols = long(P.psi32.bytes / (8 * size_t(P.N)));
+                        ok = make_tile_map(&a.tm[0], a.psi_hi, g.R, nd, ncols, P.N, a.K) &&
+                             make_tile_map(&a.tm[1], a.psi_lo, g.R, nd, ncols, P.N, a.K);
+                    } else {
+                        ok = make_tile_map(&a.tm[0], a.in, g.R, nd, nfields, P.N, a.K) &&
+                             (!HL || make_tile_map(&a.tm[1], a.in + a.lo_off, g.R, nd, nfields, P.N, a.K));
+                    }
+                    a.use_tma = ok ? 1 : 0;
+                }
                 const bool scale = kind == 5 && c == nb - 1;   // the sums of this block are complete
                 a.Fs = scale ? a.F : nullptr;
                 a.Fs_lo = scale ? a.Flo : nullptr;

@@ -185,6 +185,24 @@ __device__ __forceinline__ void cp_async16(void *dst_smem, const void *src)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst_smem)), "l"(src) : "memory");
 }
+// mbarrier arrival that also announces `bytes` of asynchronous copies to be completed.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+// One 3D box of a tiled tensor map (the map lives in kernel parameter space) -> this
+// CTA's shared memory, completing as transaction bytes on `bar`.  c0 is the innermost
+// coordinate; c0 x element size must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_3d(void *dst_smem, const void *tmap, int c0, int c1, int c2, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+            "r"(smem_addr(dst_smem)),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
+        : "memory");
+}
+
 // The mbarrier receives one arrival once every cp.async this thread issued so far has
 // landed (the arrival counts against the count the barrier was initialised with).
 __device__ __forceinline__ void cp_async_mbar_arrive_noinc(uint64_t *bar)
