@@ -312,9 +312,10 @@ __device__ __forceinline__ void read4(uint32_t d, int Np, int c0, float rs, cons
 // Warps w, w+4, ... see TMEM lane quarter w%4.  CTAs loop over tiles; the next tile's rows
 // arrive by cp.async while the current tile's MMAs and epilogue run.
 struct TcPassArgs {
-    // [k][row] tiles by TMA (use_tma): tm[0] hi plane, tm[1] lo plane of the input (pair
-    // pass: of the orbitals), each a 3D tensor (R rows, n_d lines, fields or orbitals)
-    // with a 128 x K x 1 box; koff = first line of this K-block
+    // Tiles by TMA (use_tma): tm[0] hi plane, tm[1] lo plane of the input (pair pass: of the
+    // orbitals).  [k][row] loads: 3D tensors (R rows, n_d lines, fields or orbitals), a
+    // 128 x K x 1 box; koff = first line of this K-block.  K-fast loads: 2D tensors (K, rows
+    // of the batch) read in 16 x 128 boxes with the 64-byte swizzle, one per 16 columns.
     CUtensorMap tm[2];
     int use_tma, koff;
     int nfields, R, K, Np;          // K = contracted length of this block, Np = padded block size
@@ -373,7 +374,10 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
     // contiguous runs (see the epilogue)
     const int buf_len = max(max(NSTG * stg_len, DOUBLE ? 2 * Np * kRows : 0),
                             STORE == STORE_NFAST ? (HL ? 2 : 1) * kRows * (Kp + 4) : 0);
-    float *stg0 = reinterpret_cast<float *>(sA0 + NSETS * a_piece * S);
+    // K-fast staging starts 1024-byte aligned (the 64-byte TMA swizzle repeats every 512)
+    uint8_t *stg_b = sA0 + NSETS * a_piece * S;
+    if (LOAD == LOAD_KFAST) stg_b += (1024u - (tc::smem_addr(stg_b) & 1023u)) & 1023u;
+    float *stg0 = reinterpret_cast<float *>(stg_b);
     float *maxbuf = stg0 + NBUF * buf_len;
     uint64_t *bar1 = reinterpret_cast<uint64_t *>(maxbuf + NT);   // [2]: first GEMM of each set
     uint64_t *bar2 = bar1 + 2;                                      // [2]: second GEMM (pass 3)
@@ -443,7 +447,7 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
     // threads when a tile is in; KFAST and pair tiles (measured faster that way: pass 3
     // and the pair pass have one buffer, and the next tile must be requested at once
     // by many threads) are copied by the compute threads, with a barrier after the wait.
-    const bool use_tma = a.use_tma != 0;   // [k][row] tiles of fields of R = multiple of 128 rows
+    const bool use_tma = a.use_tma != 0;   // set by the host where the layout allows it
     const bool use_prod = use_tma || (LOAD == LOAD_KSLOW && rvec);
     const bool coal = !use_prod && (kcont || (LOAD == LOAD_PAIR && rvec));
     // Producer, TMA: one box per plane (128 rows x K lines), the tile being one field's
@@ -453,6 +457,15 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
         const uint32_t f = fast_div(g0, a.divR);
         const int rr = int(g0 - f * uint32_t(a.R));
         constexpr int NPL = LOAD == LOAD_PAIR ? 4 : (HL ? 2 : 1);
+        if (LOAD == LOAD_KFAST) {   // ceil(K / 16) swizzled 16 x 128 boxes per plane, rows g0..g0+127
+            const int nsl = (a.K + 15) >> 4;
+            tc::mbar_arrive_expect_tx(fb, uint32_t(NPL) * uint32_t(nsl) * uint32_t(kRows) * 64u);
+            for (int sl = 0; sl < nsl; ++sl) {
+                tc::tma_load_2d(stg + sl * (kRows * 16), &a.tm[0], 16 * sl, int(g0), fb);
+                if (HL) tc::tma_load_2d(stg + stg_len + sl * (kRows * 16), &a.tm[1], 16 * sl, int(g0), fb);
+            }
+            return;
+        }
         tc::mbar_arrive_expect_tx(fb, uint32_t(NPL) * uint32_t(kRows) * uint32_t(a.K) * 4u);
         if (LOAD == LOAD_PAIR) {
             const int2 mn = a.pairs[f];
@@ -550,14 +563,22 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
         }
         tc::cp_async_commit();
     };
+    // Offset (floats) of unit u (elements 4u..4u+3) of this thread's row in a K-fast staging
+    // plane: padded rows [row][Kp + 4] for cp.async copies; for TMA, 16-column slabs of 128
+    // rows x 64 bytes whose 16-byte chunk c sits at c ^ ((row >> 1) & 3) (the 64-byte swizzle)
+    auto kfast_off = [&](int u) {
+        if (use_tma) return (u >> 2) * (kRows * 16) + row * 16 + 4 * ((u & 3) ^ ((row >> 1) & 3));
+        return row * (Kp + 4) + 4 * u;
+    };
     // Staged values (hi, lo) of unit u (elements 4u..4u+3) of this thread's row.
     auto staged_unit = [&](const float *stg, int u, float (&hi)[4], float (&lo)[4]) {
         const int k0 = 4 * u;
         if constexpr (LOAD == LOAD_KFAST) {
-            const float4 h = *reinterpret_cast<const float4 *>(stg + row * (Kp + 4) + k0);
+            const int so = kfast_off(u);
+            const float4 h = *reinterpret_cast<const float4 *>(stg + so);
             hi[0] = h.x; hi[1] = h.y; hi[2] = h.z; hi[3] = h.w;
             if (HL) {
-                const float4 l = *reinterpret_cast<const float4 *>(stg + stg_len + row * (Kp + 4) + k0);
+                const float4 l = *reinterpret_cast<const float4 *>(stg + stg_len + so);
                 lo[0] = l.x; lo[1] = l.y; lo[2] = l.z; lo[3] = l.w;
             } else {
                 lo[0] = lo[1] = lo[2] = lo[3] = 0.f;
@@ -591,7 +612,7 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
         for (int u = q; u < nunit; u += TPR) {
             const int k0 = 4 * u;
             if constexpr (LOAD == LOAD_KFAST) {
-                const float4 h = *reinterpret_cast<const float4 *>(stg + row * (Kp + 4) + k0);
+                const float4 h = *reinterpret_cast<const float4 *>(stg + kfast_off(u));
                 const float v[4] = {h.x, h.y, h.z, h.w};
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
@@ -1172,7 +1193,8 @@ size_t pass_smem(int prec, int Np, bool dbl, int load, int nbuf = 1, int nsets =
     if (store == STORE_NFAST) staging = std::max(staging, size_t(pi.hl ? 2 : 1) * kRows * (Np + 4) * sizeof(float));
     staging *= size_t(nbuf);                                   // staging buffers in flight
     const size_t maxbuf = size_t(kRows) * 4 * sizeof(float);   // up to 4 threads per row
-    return (dbl ? 2 : 1) * image_bytes(prec, Np) + a + staging + maxbuf + 64;
+    const size_t align = load == LOAD_KFAST ? 1024 : 0;          // K-fast staging alignment slack
+    return (dbl ? 2 : 1) * image_bytes(prec, Np) + a + staging + maxbuf + 64 + align;
 }
 
 int tmem_cols(int prec, int Np, int nsets = 1) { return pow2_cols(nsets * prec_info(prec).nacc * Np); }
@@ -1259,6 +1281,21 @@ bool make_tile_map(CUtensorMap *m, const float *base, long R, long L, long F, lo
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 2D FP32 tensor (K columns fastest, `rows` rows, rows K apart) read in 16 x 128 boxes with
+// the 64-byte swizzle; columns >= K of the last box come back as zeros.
+bool make_kfast_map(CUtensorMap *m, const float *base, int K, long rows)
+{
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn || (reinterpret_cast<uintptr_t>(base) & 15) || (K & 3) || K < 16 || rows < kRows) return false;
+    const cuuint64_t dims[2] = {cuuint64_t(K), cuuint64_t(rows)};
+    const cuuint64_t strides[1] = {cuuint64_t(K) * 4};
+    const cuuint32_t box[2] = {16, cuuint32_t(kRows)};
+    const cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // One launch of pass kernel `kind` (0..4 = P1..P5; 5 = P3's forward half alone, 6 = its
 // inverse half alone, used when the y axis is cut into blocks).
 template <int MODE, int S, int SB, bool HL>
@@ -1333,7 +1370,12 @@ int solve_batch_t(Plan &P, int prec, const int2 *pairs_d, int nfields, float *bu
                 // [k][row] inputs of fields of R = 128 m rows: one TMA box per plane per tile
                 a.use_tma = 0;
                 a.koff = c * bs;
-                if ((g.load == LOAD_PAIR || g.load == LOAD_KSLOW) && g.R % kRows == 0 && (a.lo_off & 3) == 0) {
+                if (g.load == LOAD_KFAST && nb == 1 && (a.K & 3) == 0 && (a.lo_off & 3) == 0 && (P.N & 3) == 0) {
+                    // rows of the batch are back to back: a 2D tensor (K, nfields R)
+                    const long nrows = long(nfields) * g.R;
+                    a.use_tma = make_kfast_map(&a.tm[0], a.in, a.K, nrows) &&
+                                (!HL || make_kfast_map(&a.tm[1], a.in + a.lo_off, a.K, nrows));
+                } else if ((g.load == LOAD_PAIR || g.load == LOAD_KSLOW) && g.R % kRows == 0 && (a.lo_off & 3) == 0) {
                     bool ok;
                     if (g.load == LOAD_PAIR) {
                         const long ncols = long(P.psi32.bytes / (8 * size_t(P.N)));

@@ -203,6 +203,16 @@ __device__ __forceinline__ void tma_load_3d(void *dst_smem, const void *tmap, in
         : "memory");
 }
 
+// One 2D box of a tiled tensor map -> shared memory (same rules as tma_load_3d).
+__device__ __forceinline__ void tma_load_2d(void *dst_smem, const void *tmap, int c0, int c1, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_addr(dst_smem)),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(smem_addr(bar))
+        : "memory");
+}
+
 // The mbarrier receives one arrival once every cp.async this thread issued so far has
 // landed (the arrival counts against the count the barrier was initialised with).
 __device__ __forceinline__ void cp_async_mbar_arrive_noinc(uint64_t *bar)
