@@ -95,7 +95,11 @@ enum { EXX_PREC_FP64 = 0, EXX_PREC_BF16X3 = 1, EXX_PREC_TF32X3 = 2, EXX_PREC_BF1
 int exx_plan_create(exx_plan *out, int Nx, int Ny, int Nz, double h, const int bc[3],
                     int fd_order, int kernel, double omega);
 
-/* Select the mode-product arithmetic (EXX_PREC_*); default EXX_PREC_FP64. */
+/* Select the mode-product arithmetic (EXX_PREC_*); default EXX_PREC_FP64.  The split
+ * modes upload fixed-point images of the 1D eigenvector matrices; an axis whose images
+ * do not fit in one CTA's shared memory is cut into blocks of ceil(n/nb) points (nb <= 16)
+ * and each mode product becomes nb x nb block products summed in hi/lo FP32
+ * (EXX_ERR_UNSUPPORTED if 16 blocks do not fit). */
 int exx_plan_set_precision(exx_plan plan, int prec);
 
 /* Tuning: pairs per batch (the paper's n_c, Sec. II.B) and orbitals per pair block.

@@ -210,55 +210,11 @@ __device__ __forceinline__ void issue_gemm(uint32_t d, int Np, uint32_t a_base, 
     }
 }
 
-// Read 8 result columns [c0, c0+8) of this thread's row: combine the NACC levels (level l
+// Read 4 result columns [c0, c0+4) of this thread's row: combine the NACC levels (level l
 // carries weight 2^(-8 l)) and apply the row and column scales.  All level loads are
 // issued before one tcgen05.wait::ld.  With HL the value is returned as an unevaluated
 // sum vh + vl: level 0 is an exact integer, the lower levels are folded into t, and
 // TwoSum keeps the rounding error of l0 + t (the scales are powers of two, exact).
-template <int MODE, int NACC, bool HL>
-__device__ __forceinline__ void read8(uint32_t d, int Np, int c0, float rs, const float *cs, float (&vh)[8],
-                                      float (&vl)[8])
-{
-    uint32_t r[NACC][8];
-#pragma unroll
-    for (int l = 0; l < NACC; ++l) tc::tmem_ld8_issue(d + uint32_t(l * Np + c0), r[l]);
-    tc::tmem_wait_ld();
-#pragma unroll
-    for (int l = 0; l < NACC; ++l)
-#pragma unroll
-        for (int e = 0; e < 8; ++e) tc::order_after_wait(r[l][e]);
-    if constexpr (MODE == MODE_FLOAT_TF32) {
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            vh[e] = __uint_as_float(r[0][e]);
-            vl[e] = 0.f;
-        }
-    } else {
-        float t[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) t[e] = 0.f;
-#pragma unroll
-        for (int l = NACC - 1; l >= 1; --l)
-#pragma unroll
-            for (int e = 0; e < 8; ++e) t[e] = (__uint_as_float(r[l][e]) + t[e]) * (1.f / 256.f);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const float l0 = __uint_as_float(r[0][e]);
-            const float sc = rs * cs[c0 + e];
-            if (HL) {
-                const float h = l0 + t[e];
-                const float bp = h - l0;
-                vl[e] = ((l0 - (h - bp)) + (t[e] - bp)) * sc;
-                vh[e] = h * sc;
-            } else {
-                vh[e] = (l0 + t[e]) * sc;
-                vl[e] = 0.f;
-            }
-        }
-    }
-}
-
-// As read8 for 4 columns [c0, c0+4).
 template <int MODE, int NACC, bool HL>
 __device__ __forceinline__ void read4(uint32_t d, int Np, int c0, float rs, const float *cs, float (&vh)[4],
                                       float (&vl)[4])
@@ -310,7 +266,7 @@ __device__ __forceinline__ void read4(uint32_t d, int Np, int c0, float rs, cons
 // u = q, q+TPR, ... of the row (slicing) and the 4-column units of the result (TMEM read,
 // stores); Np is a multiple of 16, so every thread of a row gets the same number of units.
 // Warps w, w+4, ... see TMEM lane quarter w%4.  CTAs loop over tiles; the next tile's rows
-// arrive by cp.async while the current tile's MMAs and epilogue run.
+// arrive (TMA boxes or cp.async copies) while the current tile's MMAs and epilogue run.
 struct TcPassArgs {
     // Tiles by TMA (use_tma): tm[0] hi plane, tm[1] lo plane of the input (pair pass: of the
     // orbitals).  [k][row] loads: 3D tensors (R rows, n_d lines, fields or orbitals), a
