@@ -680,9 +680,15 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
     // stored partial sums for K-blocks after the first; scaled by f(Lambda) when Fs is set).
     // With obuf (a free staging buffer) and ostage, through shared memory: every compute
     // thread must call it then, as it contains two compute-thread barriers.
-    auto epilogue = [&](long t, int st, float rs_out, const float *cs_out, float *obuf, bool to_producer) {
+    // obuf: [row][Kp + 4] rows (a staging buffer), or with swz a [row][Kp] layout whose 16-byte
+    // chunk u of row r sits at u ^ sw(r) (fits an A-image buffer; conflict-free).
+    auto epilogue = [&](long t, int st, float rs_out, const float *cs_out, float *obuf, bool to_producer,
+                        bool swz) {
         if (ostage && obuf != nullptr) {
-            const int opitch = Kp + 4;
+            const int opitch = swz ? Kp : Kp + 4;
+            // rows Kp floats apart meet the banks at 16 r mod 32 (Kp = 16 mod 32) or at 0:
+            // XOR the chunk with 2 or 3 row bits so that 8 rows cover all 32 banks
+            auto chunk = [&](int r, int u) { return !swz ? u : ((Kp & 16) ? u ^ ((r >> 1) & 3) : u ^ (r & 7)); };
             float *oh = obuf, *ol = obuf + kRows * opitch;
             int fp = 0, fr = 0;
             const bool fact = a.Fs != nullptr && locate(t, row, fp, fr);
@@ -704,8 +710,9 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
                         }
                     }
                 }
-                *reinterpret_cast<float4 *>(oh + row * opitch + 4 * u) = make_float4(v[0], v[1], v[2], v[3]);
-                if (HL) *reinterpret_cast<float4 *>(ol + row * opitch + 4 * u) = make_float4(vlo[0], vlo[1], vlo[2], vlo[3]);
+                const int cu = row * opitch + 4 * chunk(row, u);
+                *reinterpret_cast<float4 *>(oh + cu) = make_float4(v[0], v[1], v[2], v[3]);
+                if (HL) *reinterpret_cast<float4 *>(ol + cu) = make_float4(vlo[0], vlo[1], vlo[2], vlo[3]);
             }
             tc::tc_fence_before();
             tc::bar_sync(kBarCompute, NT);
@@ -715,11 +722,9 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
             float *dst = a.out + size_t(g0) * a.Kout;
             for (int c = tid; c < nrow * kq; c += NT) {
                 const int rw = int(fast_div(uint32_t(c), a.divKo4));
-                const int k = 4 * (c - rw * kq);
-                *reinterpret_cast<float4 *>(dst + 4 * c) = *reinterpret_cast<const float4 *>(oh + rw * opitch + k);
-                if (HL)
-                    *reinterpret_cast<float4 *>(dst + a.lo_off + 4 * c) =
-                        *reinterpret_cast<const float4 *>(ol + rw * opitch + k);
+                const int k = rw * opitch + 4 * chunk(rw, c - rw * kq);
+                *reinterpret_cast<float4 *>(dst + 4 * c) = *reinterpret_cast<const float4 *>(oh + k);
+                if (HL) *reinterpret_cast<float4 *>(dst + a.lo_off + 4 * c) = *reinterpret_cast<const float4 *>(ol + k);
             }
             if (to_producer) {   // obuf is free again (the producer refills it, maybe by TMA)
                 tc::fence_proxy_async_smem();
@@ -823,7 +828,7 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
         if (NSETS == 1 && prev_tile >= 0) {   // one A buffer / TMEM set: finish t-1 first
             if (DOUBLE) wait_bar(bar2 + prev_set, ph2, prev_set);
             else wait_bar(bar1 + prev_set, ph1, prev_set);
-            epilogue(prev_tile, prev_set, prev_rs, prev_cs, nullptr, false);
+            epilogue(prev_tile, prev_set, prev_rs, prev_cs, nullptr, false, false);
             prev_tile = -1;
         }
         int p = 0, r = 0;
@@ -861,11 +866,11 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
         // every thread has consumed this staging buffer: fetch the tile NBUF steps ahead
         // (after the epilogue when that stages its output here)
         if (!DOUBLE && !ostage) prefetch(tile + long(NBUF) * gridDim.x, stg);
-        // ---- epilogue of the previous tile, overlapping this tile's GEMM ----
-        if (prev_tile >= 0) {
-            if (DOUBLE) wait_bar(bar2 + prev_set, ph2, prev_set);
-            else wait_bar(bar1 + prev_set, ph1, prev_set);
-            epilogue(prev_tile, prev_set, prev_rs, prev_cs, stg, use_prod && !DOUBLE);
+        // ---- epilogue of the previous tile, overlapping this tile's GEMM (pass 3: after
+        //      its second GEMM is issued, overlapping the next tile's load instead) ----
+        if (!DOUBLE && prev_tile >= 0) {
+            wait_bar(bar1 + prev_set, ph1, prev_set);
+            epilogue(prev_tile, prev_set, prev_rs, prev_cs, stg, use_prod, false);
         }
         if (!DOUBLE && ostage) prefetch(tile + long(NBUF) * gridDim.x, stg);
         float rs_out = rs1;
@@ -937,6 +942,12 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
             if (stop) break;
             rs_out = rs2;
             cs_out = cs2;
+            // the previous tile's GEMMs are long complete: its A image holds the staged output
+            if (prev_tile >= 0) {
+                wait_bar(bar2 + prev_set, ph2, prev_set);
+                epilogue(prev_tile, prev_set, prev_rs, prev_cs, reinterpret_cast<float *>(set_A(prev_set)), false,
+                         true);
+            }
         }
         prev_tile = tile;
         prev_set = st;
@@ -948,7 +959,7 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
     if (prev_tile >= 0 && !tc::bar_red_or(kBarCompute, NT, *sflag != 0)) {
         if (DOUBLE) wait_bar(bar2 + prev_set, ph2, prev_set);
         else wait_bar(bar1 + prev_set, ph1, prev_set);
-        epilogue(prev_tile, prev_set, prev_rs, prev_cs, stg0, false);
+        epilogue(prev_tile, prev_set, prev_rs, prev_cs, stg0, false, false);
     }
     tc::cp_async_wait_all();   // no copy may still target shared memory at exit
     }   // compute threads
