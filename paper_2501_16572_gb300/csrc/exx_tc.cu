@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
     // compute threads, then one warp that issues the MMAs and one that issues the input
     // copies of the coalesced layouts (the producer)
     constexpr int NT = kRows * TPR;
-    constexpr int kBarHandoff = 1, kBarCompute = 2, kBarEpi = 3;
+    constexpr int kBarHandoff = 1, kBarCompute = 2;
     const int Np = a.Np, Kp = a.Np;
     const int nunit = Np / 4;                // 4-element units per row
     const uint32_t sbo = uint32_t(Kp) * ES * 8;          // bytes per 8-row group
@@ -639,7 +639,6 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
         for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
             if (tc::bar_red_or(kBarHandoff, NT + 64, false)) break;
             if (DOUBLE && tc::bar_red_or(kBarHandoff, NT + 64, false)) break;
-            if (use_prod && ostage && !DOUBLE && it > 0) tc::bar_sync(kBarEpi, NT + 32);
             const long tn = tile + long(NBUF) * gridDim.x;
             if (use_prod && tn < ntiles) fill(tn, int(it % NBUF));
         }
@@ -678,12 +677,11 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
     };
     // Epilogue of tile t from TMEM set st: own 4-column units -> global (added to the
     // stored partial sums for K-blocks after the first; scaled by f(Lambda) when Fs is set).
-    // With obuf (a free staging buffer) and ostage, through shared memory: every compute
-    // thread must call it then, as it contains two compute-thread barriers.
-    // obuf: [row][Kp + 4] rows (a staging buffer), or with swz a [row][Kp] layout whose 16-byte
-    // chunk u of row r sits at u ^ sw(r) (fits an A-image buffer; conflict-free).
-    auto epilogue = [&](long t, int st, float rs_out, const float *cs_out, float *obuf, bool to_producer,
-                        bool swz) {
+    // With obuf (free shared memory) and ostage, through shared memory: every compute thread
+    // must call it then, as it contains two compute-thread barriers.  obuf: [row][Kp + 4]
+    // rows (an idle staging buffer), or with swz a [row][Kp] layout whose 16-byte chunk u of
+    // row r sits at u ^ sw(r) (the previous tile's A image, whose GEMMs have completed).
+    auto epilogue = [&](long t, int st, float rs_out, const float *cs_out, float *obuf, bool swz) {
         if (ostage && obuf != nullptr) {
             const int opitch = swz ? Kp : Kp + 4;
             // rows Kp floats apart meet the banks at 16 r mod 32 (Kp = 16 mod 32) or at 0:
@@ -726,12 +724,7 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
                 *reinterpret_cast<float4 *>(dst + 4 * c) = *reinterpret_cast<const float4 *>(oh + k);
                 if (HL) *reinterpret_cast<float4 *>(dst + a.lo_off + 4 * c) = *reinterpret_cast<const float4 *>(ol + k);
             }
-            if (to_producer) {   // obuf is free again (the producer refills it, maybe by TMA)
-                tc::fence_proxy_async_smem();
-                tc::bar_sync(kBarEpi, NT + 32);
-            } else {
-                tc::bar_sync(kBarCompute, NT);
-            }
+            tc::bar_sync(kBarCompute, NT);   // obuf is free again
             return;
         }
         int pp = 0, rr = 0;
@@ -828,7 +821,7 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
         if (NSETS == 1 && prev_tile >= 0) {   // one A buffer / TMEM set: finish t-1 first
             if (DOUBLE) wait_bar(bar2 + prev_set, ph2, prev_set);
             else wait_bar(bar1 + prev_set, ph1, prev_set);
-            epilogue(prev_tile, prev_set, prev_rs, prev_cs, nullptr, false, false);
+            epilogue(prev_tile, prev_set, prev_rs, prev_cs, nullptr, false);
             prev_tile = -1;
         }
         int p = 0, r = 0;
@@ -864,15 +857,13 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
         //      tile it-2, which every thread finished before this hand-off ----
         if (handoff()) break;
         // every thread has consumed this staging buffer: fetch the tile NBUF steps ahead
-        // (after the epilogue when that stages its output here)
-        if (!DOUBLE && !ostage) prefetch(tile + long(NBUF) * gridDim.x, stg);
+        if (!DOUBLE) prefetch(tile + long(NBUF) * gridDim.x, stg);
         // ---- epilogue of the previous tile, overlapping this tile's GEMM (pass 3: after
         //      its second GEMM is issued, overlapping the next tile's load instead) ----
-        if (!DOUBLE && prev_tile >= 0) {
+        if (!DOUBLE && prev_tile >= 0) {   // staged output (N-fast) in the previous tile's A image
             wait_bar(bar1 + prev_set, ph1, prev_set);
-            epilogue(prev_tile, prev_set, prev_rs, prev_cs, stg, use_prod, false);
+            epilogue(prev_tile, prev_set, prev_rs, prev_cs, reinterpret_cast<float *>(set_A(prev_set)), true);
         }
-        if (!DOUBLE && ostage) prefetch(tile + long(NBUF) * gridDim.x, stg);
         float rs_out = rs1;
         const float *cs_out = cs1;
         if (DOUBLE) {
@@ -945,8 +936,7 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
             // the previous tile's GEMMs are long complete: its A image holds the staged output
             if (prev_tile >= 0) {
                 wait_bar(bar2 + prev_set, ph2, prev_set);
-                epilogue(prev_tile, prev_set, prev_rs, prev_cs, reinterpret_cast<float *>(set_A(prev_set)), false,
-                         true);
+                epilogue(prev_tile, prev_set, prev_rs, prev_cs, reinterpret_cast<float *>(set_A(prev_set)), true);
             }
         }
         prev_tile = tile;
@@ -959,7 +949,7 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
     if (prev_tile >= 0 && !tc::bar_red_or(kBarCompute, NT, *sflag != 0)) {
         if (DOUBLE) wait_bar(bar2 + prev_set, ph2, prev_set);
         else wait_bar(bar1 + prev_set, ph1, prev_set);
-        epilogue(prev_tile, prev_set, prev_rs, prev_cs, stg0, false, false);
+        epilogue(prev_tile, prev_set, prev_rs, prev_cs, stg0, false);
     }
     tc::cp_async_wait_all();   // no copy may still target shared memory at exit
     }   // compute threads
