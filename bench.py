@@ -56,7 +56,7 @@ FP64_PEAK_NOTE = "FP64 CUDA-core peak: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="auto")
@@ -97,6 +97,19 @@ class Clocks:
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # wait (at most 5 s) until the sampler writes, so the timed region starts with it live;
+        # the samples already written were taken before the region and are skipped
+        self.skip = 0
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and self.proc.poll() is None:
+            self.fh.flush()
+            with open(self.path) as fh:
+                n = sum(1 for _ in fh)
+            if n:
+                self.skip = n
+                break
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:
@@ -107,25 +120,31 @@ class Clocks:
         except Exception:
             self.proc.kill()
         self.fh.close()
-        sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
+                sm_mhz, max_mhz = float(parts[1]), float(parts[2])
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
+            rows.append((sm_mhz, max_mhz, {nm for nm, v in zip(names, parts[5:9]) if v.lower().startswith("active")}))
         os.unlink(self.path)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
-                "reasons": sorted(reasons)}
+        skip = getattr(self, "skip", 0)
+        inside = rows[skip:]
+        note = None
+        if not inside:
+            if not rows:
+                return None
+            # the region was shorter than the sampling interval: the last sample before it
+            inside, note = rows[-1:], "timed region shorter than the 200 ms sampling interval; last sample before it"
+        rec = {"sm_mhz": statistics.median(r[0] for r in inside), "sm_max_mhz": max(r[1] for r in inside),
+               "samples": len(rows[skip:]), "reasons": sorted(set().union(*(r[2] for r in inside)))}
+        if note:
+            rec["note"] = note
+        return rec
 
 
 def measured_peaks():

@@ -1083,9 +1083,10 @@ __device__ __forceinline__ int diag_idx(int i, int j, int nI) { return i * nI - 
 // One launch per batch: CUDA block (x, y) = 256 grid points of the outputs of Block y.
 // Blocks of one batch have disjoint outputs, so no atomics are needed.
 template <bool HL>
-__global__ void __launch_bounds__(256) tc_accum_kernel(long N, const Block *blocks, const float *V, long lo_off,
-                                                       const float *g, const float *g_lo, float *acc_hi,
-                                                       float *acc_lo)
+__global__ void __launch_bounds__(256) tc_accum_kernel(long N, const Block *blocks, const float *__restrict__ V,
+                                                       long lo_off, const float *__restrict__ g,
+                                                       const float *__restrict__ g_lo, float *__restrict__ acc_hi,
+                                                       float *__restrict__ acc_lo)
 {
     const Block b = blocks[blockIdx.y];
     const long r = long(blockIdx.x) * blockDim.x + threadIdx.x;
