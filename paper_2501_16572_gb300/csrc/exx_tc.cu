@@ -1080,10 +1080,12 @@ __device__ __forceinline__ void sub_product(float &s, float &c, float gh, float 
 
 __device__ __forceinline__ int diag_idx(int i, int j, int nI) { return i * nI - (i * (i - 1)) / 2 + (j - i); }
 
+constexpr int kAccBlock = 8;   // widest block edge of the one-sweep form (the default edge)
+
 // One launch per batch: CUDA block (x, y) = 256 grid points of the outputs of Block y.
 // Blocks of one batch have disjoint outputs, so no atomics are needed.
 template <bool HL>
-__global__ void __launch_bounds__(256) tc_accum_kernel(long N, const Block *blocks, const float *__restrict__ V,
+__global__ void __launch_bounds__(256, 6) tc_accum_kernel(long N, const Block *blocks, const float *__restrict__ V,
                                                        long lo_off, const float *__restrict__ g,
                                                        const float *__restrict__ g_lo, float *__restrict__ acc_hi,
                                                        float *__restrict__ acc_lo)
@@ -1102,6 +1104,38 @@ __global__ void __launch_bounds__(256) tc_accum_kernel(long N, const Block *bloc
         acc_lo[size_t(t) * N + r] = c - (hs - s);
         acc_hi[size_t(t) * N + r] = hs;
     };
+    if (b.kind == BLK_SYM_OFF && b.nJ <= kAccBlock) {
+        // Both sides in one sweep over the block's fields: field (i, j) adds to output J0+j
+        // (source I0+i) and to output I0+i (source J0+j), so each field is read from memory
+        // once. Per output the terms still come in the order of the other index, as below.
+        float sj[kAccBlock], cj[kAccBlock];
+#pragma unroll
+        for (int j = 0; j < kAccBlock; ++j)
+            if (j < b.nJ) {
+                sj[j] = acc_hi[size_t(b.J0 + j) * N + r];
+                cj[j] = acc_lo[size_t(b.J0 + j) * N + r];
+            }
+#pragma unroll 1
+        for (int i = 0; i < b.nI; ++i) {
+            const int oi = b.I0 + i;
+            const float gih = g[size_t(oi) * N + r], gil = g_lo[size_t(oi) * N + r];
+            float si = acc_hi[size_t(oi) * N + r], ci = acc_lo[size_t(oi) * N + r];
+#pragma unroll
+            for (int j = 0; j < kAccBlock; ++j)
+                if (j < b.nJ) {
+                    const size_t fo = size_t(i * b.nJ + j) * N;
+                    const float vh = vh_at(fo), vl = vl_at(fo);
+                    sub_product(sj[j], cj[j], gih, gil, vh, vl);
+                    const size_t src = size_t(b.J0 + j) * N + r;
+                    sub_product(si, ci, g[src], g_lo[src], vh, vl);
+                }
+            finish(oi, si, ci);
+        }
+#pragma unroll
+        for (int j = 0; j < kAccBlock; ++j)
+            if (j < b.nJ) finish(b.J0 + j, sj[j], cj[j]);
+        return;
+    }
     if (b.kind == BLK_SYM_DIAG) {
         for (int t = 0; t < b.nI; ++t) {
             const int o = b.I0 + t;
