@@ -234,13 +234,17 @@ __device__ __forceinline__ void read4(uint32_t d, int Np, int c0, float rs, cons
             vl[e] = 0.f;
         }
     } else {
+        // t = sum_{l>=1} r_l 2^(-8 l) by Horner's rule: each FMA rounds exactly where the sum
+        // of r_l and the (exactly scaled) lower levels would, so this equals adding the
+        // levels from the lowest up with one rounding per level
         float t[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) t[e] = 0.f;
+        for (int e = 0; e < 4; ++e) {
+            float acc = NACC >= 2 ? __uint_as_float(r[NACC - 1][e]) : 0.f;
 #pragma unroll
-        for (int l = NACC - 1; l >= 1; --l)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) t[e] = (__uint_as_float(r[l][e]) + t[e]) * (1.f / 256.f);
+            for (int l = NACC - 2; l >= 1; --l) acc = fmaf(acc, 1.f / 256.f, __uint_as_float(r[l][e]));
+            t[e] = acc * (1.f / 256.f);
+        }
         const float4 c4 = *reinterpret_cast<const float4 *>(cs + c0);   // 16-byte aligned
         const float csv[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
@@ -264,7 +268,8 @@ __device__ __forceinline__ void read4(uint32_t d, int Np, int c0, float rs, cons
 // Pass kernel.  Rows of the batch are cut into tiles of 128 (= TMEM lanes); TPR threads
 // share a row, thread (q, row) = threadIdx.x = q*128 + row owning the 4-element units
 // u = q, q+TPR, ... of the row (slicing) and the 4-column units of the result (TMEM read,
-// stores); Np is a multiple of 16, so every thread of a row gets the same number of units.
+// stores).  The 32 threads of a warp share q, so they run the same number of units and the
+// warp-collective TMEM loads stay uniform (threads with different q may differ by one unit).
 // Warps w, w+4, ... see TMEM lane quarter w%4.  CTAs loop over tiles; the next tile's rows
 // arrive (TMA boxes or cp.async copies) while the current tile's MMAs and epilogue run.
 struct TcPassArgs {
@@ -322,14 +327,12 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
     // k >= K are zero from the start and never written); KFAST: [row][Kp + 4] (16-byte
     // copies, read back conflict-free because (Kp + 4)/4 is odd; columns k >= K are
     // masked when read).  PAIR stages psi_m hi, psi_m lo, psi_n hi, psi_n lo; the others
-    // hi (and lo).  Pass 3 stages f(Lambda) D1 ([col][row], hi and lo) in the same space
-    // after the first GEMM.  NBUF staging buffers = tiles whose copies are in flight.
+    // hi (and lo).  NBUF staging buffers = tiles whose copies are in flight.
     constexpr int NSTG = LOAD == LOAD_PAIR ? 4 : (HL ? 2 : 1);
     const int stg_len = kRows * (LOAD == LOAD_KFAST ? Kp + 4 : Kp);
     // NFAST outputs are also staged here ([row][Kp + 4], hi then lo) to leave as
     // contiguous runs (see the epilogue)
-    const int buf_len = max(max(NSTG * stg_len, DOUBLE ? 2 * Np * kRows : 0),
-                            STORE == STORE_NFAST ? (HL ? 2 : 1) * kRows * (Kp + 4) : 0);
+    const int buf_len = max(NSTG * stg_len, STORE == STORE_NFAST ? (HL ? 2 : 1) * kRows * (Kp + 4) : 0);
     // K-fast staging starts 1024-byte aligned (the 64-byte TMA swizzle repeats every 512)
     uint8_t *stg_b = sA0 + NSETS * a_piece * S;
     if (LOAD == LOAD_KFAST) stg_b += (1024u - (tc::smem_addr(stg_b) & 1023u)) & 1023u;
@@ -539,8 +542,7 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
             } else {
                 lo[0] = lo[1] = lo[2] = lo[3] = 0.f;
             }
-            // columns k >= K of a KFAST row are not copied, and in pass 3 they still hold
-            // the previous tile's middle values (staged over the same space): zero them
+            // columns k >= K of a KFAST row are not copied (and may hold stale values): zero them
             if (k0 + 4 > a.K) {
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
@@ -616,8 +618,9 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
 
     if (tid >= NT + 32) {
         // ---- producer warp: the copies of tile t + NBUF go out once every compute thread
-        //      is done with its buffer (after the last hand-off of tile t, and after the
-        //      epilogue of tile t - 1 when that stages its output there) ----
+        //      is done with its buffer, i.e. after the first hand-off of tile t (the slices
+        //      of tile t are its last use: epilogues stage their output in A images, and
+        //      pass 3 keeps its middle values in the A image) ----
         const int lane = tid - NT - 32;
         int fills0 = 0, fills1 = 0;   // fills issued per staging buffer
         auto fill = [&](long tt, int b) {
@@ -638,9 +641,9 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
         long it = 0;
         for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
             if (tc::bar_red_or(kBarHandoff, NT + 64, false)) break;
-            if (DOUBLE && tc::bar_red_or(kBarHandoff, NT + 64, false)) break;
             const long tn = tile + long(NBUF) * gridDim.x;
             if (use_prod && tn < ntiles) fill(tn, int(it % NBUF));
+            if (DOUBLE && tc::bar_red_or(kBarHandoff, NT + 64, false)) break;
         }
         tc::cp_async_wait_all();   // no copy may still target shared memory at exit
         if (use_tma) {   // nor a box: only the last fill of a buffer can be unconsumed (after a stop)
@@ -857,37 +860,45 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
         //      tile it-2, which every thread finished before this hand-off ----
         if (handoff()) break;
         // every thread has consumed this staging buffer: fetch the tile NBUF steps ahead
-        if (!DOUBLE) prefetch(tile + long(NBUF) * gridDim.x, stg);
-        // ---- epilogue of the previous tile, overlapping this tile's GEMM (pass 3: after
-        //      its second GEMM is issued, overlapping the next tile's load instead) ----
-        if (!DOUBLE && prev_tile >= 0) {   // staged output (N-fast) in the previous tile's A image
-            wait_bar(bar1 + prev_set, ph1, prev_set);
+        prefetch(tile + long(NBUF) * gridDim.x, stg);
+        // pass 3: f(Lambda) of the next unit of the middle step is loaded while the current
+        // one is processed, the first one while the previous tile's epilogue runs
+        float fh_n[4], fl_n[4];
+        auto load_f = [&](int u) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int col = 4 * u + e;
+                const bool ok = active && u < nunit && col < a.Kout;
+                const size_t fi = size_t(col) * a.R + r;
+                fh_n[e] = ok ? a.F[fi] : 0.f;
+                fl_n[e] = ok ? a.Flo[fi] : 0.f;
+            }
+        };
+        if (DOUBLE) load_f(q);
+        // ---- epilogue of the previous tile, overlapping this tile's (first) GEMM; the
+        //      output (N-fast) is staged in the previous tile's A image, whose GEMMs are
+        //      complete ----
+        if (prev_tile >= 0) {
+            if (DOUBLE) wait_bar(bar2 + prev_set, ph2, prev_set);
+            else wait_bar(bar1 + prev_set, ph1, prev_set);
             epilogue(prev_tile, prev_set, prev_rs, prev_cs, reinterpret_cast<float *>(set_A(prev_set)), true);
         }
         float rs_out = rs1;
         const float *cs_out = cs1;
         if (DOUBLE) {
-            // D1 * f(Lambda) -> staging ([col][row], own units) -> A[st] (its first GEMM
-            // is complete) -> second GEMM into the same TMEM set
-            // f(Lambda) of the next unit is loaded while the current one is processed (the
-            // first one while the GEMM finishes)
-            float fh_n[4], fl_n[4];
-            auto load_f = [&](int u) {
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int col = 4 * u + e;
-                    const bool ok = active && u < nunit && col < a.Kout;
-                    const size_t fi = size_t(col) * a.R + r;
-                    fh_n[e] = ok ? a.F[fi] : 0.f;
-                    fl_n[e] = ok ? a.Flo[fi] : 0.f;
-                }
+            // D1 * f(Lambda) -> A[st] (its first GEMM is complete), each thread's values of
+            // unit u in the very bytes its slices of unit u take (two 8-byte slots for the
+            // hi parts, two for the lo parts; one 16-byte slot for tf32), so no other
+            // thread writes there before it has read them back -> row maximum -> slices in
+            // place -> second GEMM into the same TMEM set.
+            static_assert(!HL || S >= 4, "hi + lo middle values need four slots per unit");
+            auto mid_slot = [&](int u) {
+                return ES == 4 ? sA + img_off(row, u, sbo) : sA + img_off(row, u >> 1, sbo) + (u & 1) * 8;
             };
-            load_f(q);
             wait_bar(bar1 + st, ph1, st);
-            float *mid_hi = stg, *mid_lo = stg + Np * kRows;
             float mx2 = 0.f;
             for (int u = q; u < nunit; u += TPR) {
-                float v[4], vlo[4], fh[4], fl[4];
+                float v[4], vlo[4], fh[4], fl[4], x[4], xl[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     fh[e] = fh_n[e];
@@ -897,16 +908,25 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
                 read4<MODE, NACC, HL>(set_tmem(st) + lane_q, Np, 4 * u, rs1, cs1, v, vlo);
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    float x, xl = 0.f;
                     if (HL) {   // (v + vlo)(fh + fl) as x + xl
-                        x = v[e] * fh[e];
-                        xl = fmaf(v[e], fh[e], -x) + fmaf(v[e], fl[e], vlo[e] * fh[e]);
+                        x[e] = v[e] * fh[e];
+                        xl[e] = fmaf(v[e], fh[e], -x[e]) + fmaf(v[e], fl[e], vlo[e] * fh[e]);
                     } else {
-                        x = fmaf(v[e], fh[e], v[e] * fl[e]);
+                        x[e] = fmaf(v[e], fh[e], v[e] * fl[e]);
+                        xl[e] = 0.f;
                     }
-                    mx2 = fmaxf(mx2, fabsf(x));
-                    mid_hi[(4 * u + e) * kRows + row] = x;
-                    mid_lo[(4 * u + e) * kRows + row] = xl;
+                    mx2 = fmaxf(mx2, fabsf(x[e]));
+                }
+                uint8_t *p = mid_slot(u);
+                if (ES == 4) {
+                    *reinterpret_cast<float4 *>(p) = make_float4(x[0], x[1], x[2], x[3]);
+                } else {
+                    *reinterpret_cast<float2 *>(p) = make_float2(x[0], x[1]);
+                    *reinterpret_cast<float2 *>(p + a_piece) = make_float2(x[2], x[3]);
+                    if (HL) {
+                        *reinterpret_cast<float2 *>(p + 2 * a_piece) = make_float2(xl[0], xl[1]);
+                        *reinterpret_cast<float2 *>(p + 3 * a_piece) = make_float2(xl[2], xl[3]);
+                    }
                 }
             }
             tc::tc_fence_before();
@@ -914,30 +934,34 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
             float s2, rs2;
             scales(mx2, s2, rs2);
             for (int u = q; u < nunit; u += TPR) {   // the same units: own values only
-                float vals[4][4];
+                float hi[4], lo[4] = {0.f, 0.f, 0.f, 0.f}, vals[4][4];
+                const uint8_t *p = mid_slot(u);
+                if (ES == 4) {
+                    const float4 h = *reinterpret_cast<const float4 *>(p);
+                    hi[0] = h.x; hi[1] = h.y; hi[2] = h.z; hi[3] = h.w;
+                } else {
+                    const float2 h0 = *reinterpret_cast<const float2 *>(p);
+                    const float2 h1 = *reinterpret_cast<const float2 *>(p + a_piece);
+                    hi[0] = h0.x; hi[1] = h0.y; hi[2] = h1.x; hi[3] = h1.y;
+                    if (HL) {
+                        const float2 l0 = *reinterpret_cast<const float2 *>(p + 2 * a_piece);
+                        const float2 l1 = *reinterpret_cast<const float2 *>(p + 3 * a_piece);
+                        lo[0] = l0.x; lo[1] = l0.y; lo[2] = l1.x; lo[3] = l1.y;
+                    }
+                }
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const int k = 4 * u + e;
                     float qv[4];
-                    if (MODE == MODE_FLOAT_TF32) split_tf32(mid_hi[k * kRows + row], 0.f, qv);
-                    else slice_fixed<S>(mid_hi[k * kRows + row], mid_lo[k * kRows + row], s2, qv);
+                    if (MODE == MODE_FLOAT_TF32) split_tf32(hi[e], 0.f, qv);
+                    else slice_fixed<S>(hi[e], lo[e], s2, qv);
 #pragma unroll
                     for (int t2 = 0; t2 < 4; ++t2) vals[t2][e] = qv[t2];
                 }
                 store_unit<ES, S>(sA, a_piece, row, u, sbo, vals);
             }
-            const bool stop = handoff();
-            // every thread is past the middle step, whose staging ([col][row]) overlaps
-            // other threads' input rows: only now refill this buffer
-            if (!stop) prefetch(tile + long(NBUF) * gridDim.x, stg);
-            if (stop) break;
+            if (handoff()) break;
             rs_out = rs2;
             cs_out = cs2;
-            // the previous tile's GEMMs are long complete: its A image holds the staged output
-            if (prev_tile >= 0) {
-                wait_bar(bar2 + prev_set, ph2, prev_set);
-                epilogue(prev_tile, prev_set, prev_rs, prev_cs, reinterpret_cast<float *>(set_A(prev_set)), true);
-            }
         }
         prev_tile = tile;
         prev_set = st;
@@ -1175,23 +1199,23 @@ __global__ void tc_finalize_kernel(long N, int n_in, const float *acc_hi, const 
 }
 
 // ---- launch helpers -------------------------------------------------------------------
+// Threads per tile row.  The pass kernels are bound by instruction issue: 6 or 7 threads
+// per row (more warps, less work each) measured slower than 4.
+constexpr int kTPR = 4;
 size_t pass_smem(int prec, int Np, bool dbl, int load, int nbuf = 1, int nsets = 1, int store = STORE_NSLOW)
 {
     const PrecInfo pi = prec_info(prec);
     size_t a = size_t(nsets) * pi.S * kRows * Np * pi.es;   // A buffers
     const int pitch = load == LOAD_KFAST ? Np + 4 : Np;   // KFAST rows are padded, [k][row] layouts not
     size_t staging = size_t(load == LOAD_PAIR ? 4 : (pi.hl ? 2 : 1)) * kRows * pitch * sizeof(float);
-    if (dbl) staging = std::max(staging, size_t(2) * kRows * Np * sizeof(float));
     if (store == STORE_NFAST) staging = std::max(staging, size_t(pi.hl ? 2 : 1) * kRows * (Np + 4) * sizeof(float));
     staging *= size_t(nbuf);                                   // staging buffers in flight
-    const size_t maxbuf = size_t(kRows) * 4 * sizeof(float);   // up to 4 threads per row
+    const size_t maxbuf = size_t(kRows) * kTPR * sizeof(float);   // one partial maximum per thread
     const size_t align = load == LOAD_KFAST ? 1024 : 0;          // K-fast staging alignment slack
     return (dbl ? 2 : 1) * image_bytes(prec, Np) + a + staging + maxbuf + 64 + align;
 }
 
 int tmem_cols(int prec, int Np, int nsets = 1) { return pow2_cols(nsets * prec_info(prec).nacc * Np); }
-
-constexpr int kTPR = 4;   // threads per tile row
 
 template <int MODE, int S, int SB, bool HL, int LOAD, int STORE, bool DOUBLE, int NBUF, int NSETS>
 int launch_tc_pass_nb(Plan &P, int kind, int prec, const TcPassArgs &a, cudaStream_t s)
