@@ -7,11 +7,11 @@
 //
 //  * Fixed-point bf16 slices (BF16X3: 2 slices, BF16X6: 3 slices).  Every row of A and
 //    every row of B gets a power-of-two scale from its largest entry, and the scaled
-//    row is cut into integer slices of at most 8 bits, x = 2^(e-7) (q0 + q1/2^8 + q2/2^16),
-//    stored exactly as bf16.  Slice products of one "level" (i + j = l) share one unit,
-//    so each level is summed in its own TMEM accumulator as an integer below 2^24: the
-//    tensor core never rounds.  The levels are combined and rescaled in FP32 in the
-//    epilogue.  The result is the fixed-point product to about 2^-8S of the row maxima,
+//    row is cut into slices x = 2^(e-7) (q0 + q1/2^8 + q2/2^16) with integers q_i of at
+//    most 8 bits; slice i is stored as q_i 2^(-8i), exact in bf16.  Slice products of one
+//    "level" (i + j = l) share the weight 2^(-8l), so each level is summed in its own TMEM
+//    accumulator as 2^(-8l) times an integer below 2^24: the tensor core never rounds.
+//    The levels are added and rescaled in FP32 in the epilogue.  The result is the fixed-point product to about 2^-8S of the row maxima,
 //    with round-to-nearest slicing and no directed rounding anywhere.
 //  * Floating tf32 split (TF32X3): x = x0 + x1 with x0 = tf32(x), x1 = tf32(x - x0), the
 //    three leading cross products accumulated in one FP32 accumulator.  The tensor core
@@ -103,25 +103,29 @@ __device__ __forceinline__ void split_tf32(float hi, float lo, float (&p)[4])
     p[3] = 0.f;
 }
 
-// Round to the nearest integer (ties to even) for |x| < 2^22: adding 1.5 * 2^23 leaves no
-// fraction bits, so the FP32 addition itself rounds; both additions stay on the FMA pipe.
-__device__ __forceinline__ float round_int(float x)
+// Round x to the nearest multiple of 2^-G (ties to even) for |x| < 2^(22-G): adding
+// 1.5 * 2^(23-G) leaves no bits below 2^-G, so the FP32 addition itself rounds; both
+// additions stay on the FMA pipe.
+template <int G>
+__device__ __forceinline__ float round_grid(float x)
 {
-    return __fadd_rn(__fadd_rn(x, 12582912.f), -12582912.f);
+    constexpr float kMagic = 12582912.f / float(1u << G);
+    return __fadd_rn(__fadd_rn(x, kMagic), -kMagic);
 }
 
-// Fixed-point slices of (hi + lo) * s, s = 2^(7 - e): integers of at most 8 bits.
-// Each residual (t_i - q_i) is exact; only the first one absorbs lo.
+// Fixed-point slices of (hi + lo) * s, s = 2^(7 - e): q[i] = q_i 2^(-8i) with q_i an integer
+// of at most 8 bits (balanced digits, each rounded to nearest).  Each residual r_i - q[i]
+// is exact; only the first one absorbs lo.
 template <int S>
 __device__ __forceinline__ void slice_fixed(float hi, float lo, float s, float (&q)[4])
 {
     const float t = hi * s;
-    q[0] = round_int(t);
-    const float t1 = ((t - q[0]) + lo * s) * 256.f;
-    q[1] = (S >= 2) ? round_int(t1) : 0.f;
-    const float t2 = (t1 - q[1]) * 256.f;
-    q[2] = (S >= 3) ? round_int(t2) : 0.f;
-    q[3] = (S >= 4) ? round_int((t2 - q[2]) * 256.f) : 0.f;
+    q[0] = round_grid<0>(t);
+    const float r1 = fmaf(lo, s, t - q[0]);
+    q[1] = (S >= 2) ? round_grid<8>(r1) : 0.f;
+    const float r2 = r1 - q[1];
+    q[2] = (S >= 3) ? round_grid<16>(r2) : 0.f;
+    q[3] = (S >= 4) ? round_grid<24>(r2 - q[2]) : 0.f;
 }
 
 // Store one 16-byte chunk per piece: vals[q][e] for e < 16/ES elements of row `row`.
@@ -163,7 +167,7 @@ __device__ __forceinline__ void store_unit(uint8_t *img, uint32_t piece_bytes, i
                 make_uint4(__float_as_uint(vals[q][0]), __float_as_uint(vals[q][1]), __float_as_uint(vals[q][2]),
                            __float_as_uint(vals[q][3]));
         } else {
-            // the values are integers of at most 8 significant bits, so their bf16 form is
+            // the values have at most 8 significant bits (q_i 2^(-8i)), so their bf16 form is
             // the upper half of their FP32 bits: pack two with one byte permute
             const uint32_t w0 = __byte_perm(__float_as_uint(vals[q][0]), __float_as_uint(vals[q][1]), 0x7632);
             const uint32_t w1 = __byte_perm(__float_as_uint(vals[q][2]), __float_as_uint(vals[q][3]), 0x7632);
@@ -210,8 +214,8 @@ __device__ __forceinline__ void issue_gemm(uint32_t d, int Np, uint32_t a_base, 
     }
 }
 
-// Read 4 result columns [c0, c0+4) of this thread's row: combine the NACC levels (level l
-// carries weight 2^(-8 l)) and apply the row and column scales.  All level loads are
+// Read 4 result columns [c0, c0+4) of this thread's row: add the NACC levels (level l holds
+// its weight 2^(-8 l) already) and apply the row and column scales.  All level loads are
 // issued before one tcgen05.wait::ld.  With HL the value is returned as an unevaluated
 // sum vh + vl: level 0 is an exact integer, the lower levels are folded into t, and
 // TwoSum keeps the rounding error of l0 + t (the scales are powers of two, exact).
@@ -234,16 +238,14 @@ __device__ __forceinline__ void read4(uint32_t d, int Np, int c0, float rs, cons
             vl[e] = 0.f;
         }
     } else {
-        // t = sum_{l>=1} r_l 2^(-8 l) by Horner's rule: each FMA rounds exactly where the sum
-        // of r_l and the (exactly scaled) lower levels would, so this equals adding the
-        // levels from the lowest up with one rounding per level
+        // t = sum_{l>=1} level l, added from the lowest level up, one rounding per level
         float t[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             float acc = NACC >= 2 ? __uint_as_float(r[NACC - 1][e]) : 0.f;
 #pragma unroll
-            for (int l = NACC - 2; l >= 1; --l) acc = fmaf(acc, 1.f / 256.f, __uint_as_float(r[l][e]));
-            t[e] = acc * (1.f / 256.f);
+            for (int l = NACC - 2; l >= 1; --l) acc = __uint_as_float(r[l][e]) + acc;
+            t[e] = acc;
         }
         const float4 c4 = *reinterpret_cast<const float4 *>(cs + c0);   // 16-byte aligned
         const float csv[4] = {c4.x, c4.y, c4.z, c4.w};
@@ -1478,7 +1480,7 @@ int tc_upload(Plan &P, int prec)
                     } else {
                         uint32_t u;
                         std::memcpy(&u, &v, 4);
-                        uint16_t hb = uint16_t(u >> 16);   // v is bf16-exact (a small integer)
+                        uint16_t hb = uint16_t(u >> 16);   // v is bf16-exact (at most 8 significant bits)
                         std::memcpy(&img[off], &hb, 2);
                     }
                 };
@@ -1495,7 +1497,7 @@ int tc_upload(Plan &P, int prec)
                             double t = coef(n, k) * sc;
                             for (int q = 0; q < pi.SB; ++q) {   // t = q0 + q1/2^8 + q2/2^16 + ...
                                 const double qq = std::nearbyint(t);
-                                put(q, n, k, float(qq));
+                                put(q, n, k, float(std::ldexp(qq, -8 * q)));   // slice q carries 2^(-8q)
                                 t = (t - qq) * 256.0;
                             }
                         }
