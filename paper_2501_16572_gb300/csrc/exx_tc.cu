@@ -683,7 +683,7 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
     // Epilogue of tile t from TMEM set st: own 4-column units -> global (added to the
     // stored partial sums for K-blocks after the first; scaled by f(Lambda) when Fs is set).
     // With obuf (free shared memory) and ostage, through shared memory: every compute thread
-    // must call it then, as it contains two compute-thread barriers.  obuf: [row][Kp + 4]
+    // must call it then, as it contains compute-thread barriers.  obuf: [row][Kp + 4]
     // rows (an idle staging buffer), or with swz a [row][Kp] layout whose 16-byte chunk u of
     // row r sits at u ^ sw(r) (the previous tile's A image, whose GEMMs have completed).
     auto epilogue = [&](long t, int st, float rs_out, const float *cs_out, float *obuf, bool swz) {
@@ -729,7 +729,10 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
                 *reinterpret_cast<float4 *>(dst + 4 * c) = *reinterpret_cast<const float4 *>(oh + k);
                 if (HL) *reinterpret_cast<float4 *>(dst + a.lo_off + 4 * c) = *reinterpret_cast<const float4 *>(ol + k);
             }
-            tc::bar_sync(kBarCompute, NT);   // obuf is free again
+            // obuf is free again once every thread is past here.  An A image (swz) needs no
+            // barrier for that: its next writer is the slicing of the next tile, which every
+            // thread reaches only through that tile's row-maximum barrier.
+            if (!swz) tc::bar_sync(kBarCompute, NT);
             return;
         }
         int pp = 0, rr = 0;
@@ -844,13 +847,16 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
         const float mx = row_max(active ? staged_max(stg) : 0.f);
         float s_in, rs1;
         scales(mx, s_in, rs1);
+        // rows past the end slice to zeros: fixed mode through a zero scale (the staging
+        // buffers hold only finite values: zeros, loaded inputs or earlier tiles' inputs)
+        if (!active) s_in = 0.f;
         for (int u = q; u < nunit; u += TPR) {
             float vals[4][4], hi[4], lo[4];
             staged_unit(stg, u, hi, lo);
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 float qv[4];
-                if (!active) hi[e] = lo[e] = 0.f;
+                if (MODE == MODE_FLOAT_TF32 && !active) hi[e] = lo[e] = 0.f;
                 if (MODE == MODE_FLOAT_TF32) split_tf32(hi[e], lo[e], qv);
                 else slice_fixed<S>(hi[e], lo[e], s_in, qv);
 #pragma unroll
