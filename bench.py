@@ -154,10 +154,21 @@ def measured_peaks():
         return {}
 
 
+def code_text(src):
+    """Source text without // comments and blank lines: edits to comments alone leave the
+    compiled kernel, and so its recorded counters, valid."""
+    lines = []
+    for line in src.splitlines():
+        code = line.split("//", 1)[0].rstrip()
+        if code:
+            lines.append(code)
+    return "\n".join(lines)
+
+
 def src_hash(paths):
     h = hashlib.sha256()
     for p in paths:
-        h.update(open(os.path.join(ROOT, p), "rb").read())
+        h.update(code_text(open(os.path.join(ROOT, p), encoding="utf-8").read()).encode())
     return h.hexdigest()[:16]
 
 

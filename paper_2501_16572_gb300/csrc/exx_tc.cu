@@ -332,8 +332,9 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
     // hi (and lo).  NBUF staging buffers = tiles whose copies are in flight.
     constexpr int NSTG = LOAD == LOAD_PAIR ? 4 : (HL ? 2 : 1);
     const int stg_len = kRows * (LOAD == LOAD_KFAST ? Kp + 4 : Kp);
-    // NFAST outputs are also staged here ([row][Kp + 4], hi then lo) to leave as
-    // contiguous runs (see the epilogue)
+    // The last tile's NFAST output is also staged here ([row][Kp + 4], hi then lo) to leave
+    // as contiguous runs; earlier tiles' outputs go through the previous A image (see the
+    // epilogue)
     const int buf_len = max(NSTG * stg_len, STORE == STORE_NFAST ? (HL ? 2 : 1) * kRows * (Kp + 4) : 0);
     // K-fast staging starts 1024-byte aligned (the 64-byte TMA swizzle repeats every 512)
     uint8_t *stg_b = sA0 + NSETS * a_piece * S;
