@@ -27,6 +27,29 @@ def test_fd_weights_order12_rational():
     assert pm.fd_weights_taylor(6) == P6_EXACT
 
 
+def _published_fd_table():
+    """tests/golden/fd_second_derivative_central.txt: {p: [w_0, ..., w_p]} as Fractions."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "fd_second_derivative_central.txt")
+    table = {}
+    for line in open(path):
+        line = line.split("#", 1)[0].split()
+        if line:
+            table[int(line[0])] = [Fraction(v) for v in line[1:]]
+    return table
+
+
+def test_fd_weights_match_published_table():
+    # Fornberg (1988), Table 1: the oracle's closed form and the exact Taylor solve of the
+    # pins both reproduce the published centred second-derivative weights, orders 2..12
+    table = _published_fd_table()
+    assert sorted(table) == [1, 2, 3, 4, 5, 6]
+    for p, w_pub in table.items():
+        assert len(w_pub) == p + 1
+        assert pm.fd_weights_taylor(p) == w_pub
+        np.testing.assert_allclose(oracle.fd_weights(p), [float(x) for x in w_pub], rtol=2e-16, atol=0)
+
+
 @pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6, 7, 8])
 def test_fd_weights_match_taylor_conditions(p):
     w = oracle.fd_weights(p)
