@@ -215,10 +215,10 @@ int exx_plan_get_timing(exx_plan plan, int kind, double *ms_h, long *launches_h)
 
 /* Gram matrix M = dV Psi^T W (n x n, column-major, written to the DEVICE buffer M)
  * without any device allocation.  This entry point has no counterpart in the paper; it
- * serves callers that cannot call cudaMalloc when they need M: code running inside
- * stream capture, programs whose device memory belongs to a pool or framework allocator
- * this library cannot use, and processes that reserve all device memory up front.  It
- * needs no plan.  Psi, W: N x n DEVICE blocks (ld, ld_w >= N), n in [1, 128]; larger n
+ * serves callers that cannot call cudaMalloc when they need M: programs whose device
+ * memory belongs to a pool or framework allocator this library cannot use, processes
+ * that reserve all device memory up front, and loops that must not stall (cudaMalloc and
+ * cudaFree can synchronize the whole device).  It needs no plan.  Psi, W: N x n DEVICE blocks (ld, ld_w >= N), n in [1, 128]; larger n
  * returns EXX_ERR_INVALID_ARG and launches nothing.  The split-K partial sums go to a
  * fixed 1 MiB device array inside the library (one per GPU that loads it, kept until
  * the process exits).  The first call on each device looks up that array's address with

@@ -404,9 +404,9 @@ int cholesky_neg_sym_and_inverse(Plan &P, int n, const double *M, double *Linv, 
 // Same split-K kernels as the ACE matrix above, but the partial tiles live in a fixed
 // device array that is part of the loaded library, so the call needs no cudaMalloc and
 // no plan.  It exists for callers that must not allocate device memory at the point of
-// the call: code running inside stream capture, callers whose device memory is owned by
-// a pool or framework allocator that this library cannot use, and memory-capped
-// processes that reserve everything up front.
+// the call: callers whose device memory is owned by a pool or framework allocator that
+// this library cannot use, memory-capped processes that reserve everything up front, and
+// loops that must not stall (cudaMalloc and cudaFree can synchronize the whole device).
 namespace {
 
 constexpr int kGramNoAllocMaxN = 128;      // largest n accepted

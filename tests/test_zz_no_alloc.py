@@ -1,7 +1,8 @@
 """The allocation-free Gram-matrix entry point (exx_gram_noalloc).
 
-Some callers cannot allocate device memory when they need M = dV Psi^T W (inside stream
-capture, under a framework-owned allocator, or in memory-capped processes).  For them
+Some callers cannot allocate device memory when they need M = dV Psi^T W (under a
+framework-owned allocator, in memory-capped processes, or in loops that must not stall on
+the device synchronization cudaMalloc and cudaFree can cause).  For them
 the library offers a plan-free call whose scratch is a fixed device array inside the
 library.  This file is collected last so that, if it fails, a run that stops at the
 first failure has already run every other test; it also passes on its own in a fresh
