@@ -80,9 +80,16 @@ enum { EXX_KERNEL_COULOMB = 0, EXX_KERNEL_ERFC = 1, EXX_KERNEL_ERFC_PAPER16PI = 
  *   TF32X3   floating tf32 split, 3 products into one FP32 accumulator (the tensor core
  *            rounds that accumulation toward zero, a bias common to all pairs); kept
  *            for comparison.
+ *   BF16X7   three passes over HBM instead of five (x and y products per z-slice with
+ *            the tile transposed on chip; z forward, f(Lambda) and z inverse per pencil),
+ *            FP32 intermediates; base-512 digits: three per data row, four per matrix row;
+ *            the leading product summed exactly in one TMEM accumulator, the six others
+ *            in a second; the fully modal middle kept as FP32 hi + lo; ~27 bits per
+ *            product.  Needs Nx, Ny <= 128 (EXX_ERR_UNSUPPORTED otherwise; the z axis is
+ *            streamed in blocks and may have up to about 208 points).
  * Pair densities and the accumulation over pairs are compensated in every mode. */
 enum { EXX_PREC_FP64 = 0, EXX_PREC_BF16X3 = 1, EXX_PREC_TF32X3 = 2, EXX_PREC_BF16X6 = 3,
-       EXX_PREC_BF16X10 = 4 };
+       EXX_PREC_BF16X10 = 4, EXX_PREC_BF16X7 = 5 };
 
 /* Create a plan for one grid (Sec. II.A, Eqs. 6-7).  Host FP64 work, done once:
  * FD weights of order fd_order (even, 2..24), the three 1D second-derivative

