@@ -193,8 +193,10 @@ int exx_ace_step_host(exx_plan plan, const double *Psi_h, int n, long ld, int n_
  *      A replay reads whatever the pointed-to buffers hold at that time, so callers
  *      refill the same buffers in place between calls.
  *   3. With stream NULL, or timing on, the launches are issued one by one.
- * Every plan must use the same precision; a plan must not be used by another call on
- * another stream while its work is in flight.  exx_plan_destroy drops the cached
+ * Every plan must use the same precision and appear at most once in plans[] (a plan owns
+ * one pair schedule and one workspace; a repeated plan returns EXX_ERR_INVALID_ARG before
+ * anything runs); a plan must not be used by another call on another stream while its
+ * work is in flight.  exx_plan_destroy drops the cached
  * graphs that use the plan.  Errors: EXX_ERR_INVALID_ARG (NULL or inconsistent
  * arguments, with the index-free message of exx_apply), EXX_ERR_OOM, EXX_ERR_CUDA
  * (capture, instantiation or launch failed). */

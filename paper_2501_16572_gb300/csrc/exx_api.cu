@@ -584,6 +584,11 @@ int exx_apply_batched(const exx_plan *plans, int nsys, const exx_apply_args *arg
     std::vector<ApplyCall> calls(nsys);
     std::vector<uintptr_t> key;
     int prec0 = -1;
+    // a plan holds one pair schedule and one workspace: the same plan twice in one call
+    // would run the earlier system with the later system's schedule
+    for (int i = 0; i < nsys; ++i)
+        for (int j = 0; j < i; ++j)
+            if (plans[i] == plans[j]) return invalid("exx_apply_batched: a plan appears more than once in plans[]");
     for (int i = 0; i < nsys; ++i) {
         Plan *P = as_plan(plans[i]);
         if (!P) return invalid("exx_apply_batched: NULL plan");

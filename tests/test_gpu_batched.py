@@ -132,3 +132,20 @@ def test_long_axes_bf16x10_match_oracle(exx, n, bc):
     e = p.energy(psi[:s.n_occ], f, out)
     e_ref = orc.energy(s.psi[:s.n_occ], s.f, ref)
     assert abs(e - e_ref) <= 1e-8 * abs(e_ref)
+
+
+def test_repeated_plan_is_rejected(exx):
+    """A plan holds one schedule: the same plan twice in one call is refused before any
+    launch, and the outputs are left untouched."""
+    systems, plans, bufs = _setup(exx, exx.EXX_PREC_FP64, 70)
+    psi, f, out = bufs[0]
+    s = systems[0]
+    other = torch.full_like(psi, float("nan"))
+    args = [(psi[:s.n_occ], f, psi, out), (psi[:2], f, psi, other)]
+    with pytest.raises(exx.ExxError) as ei:
+        exx.exx_apply_batched([plans[0], plans[0]], args, stream=torch.cuda.Stream())
+    assert ei.value.status == exx.EXX_ERR_INVALID_ARG
+    torch.cuda.synchronize()
+    assert bool(torch.isnan(out).all()) and bool(torch.isnan(other).all())
+    for p in plans:
+        p.close()

@@ -1,8 +1,8 @@
 """Parity at the full workload sizes, in the launch configuration bench.py times, on
 sampled outputs that the CPU oracle recomputes one by one (Sec. II.B solves + Eq. 1):
 
-* 48^3 periodic, 256 orbitals (the precision study): FP64 path <= 1e-10, BF16X10 <= 1e-6
-  on sampled output orbitals, E_x of the split path against the FP64 path <= 1e-8;
+* 48^3 periodic, 256 orbitals (the precision study): BF16X10 <= 1e-6 on sampled output
+  orbitals (FP64 and BF16X7 are compared on every column in test_gpu_oracle_full.py);
 * the 48-system batch, through one exx_apply_batched call: sampled outputs of systems with
   every boundary mix against the oracle;
 * the 72x72x144 slab with 1024 orbitals (800 occupied): BF16X10 on sampled outputs, one of
@@ -37,16 +37,11 @@ def test_periodic48_256_orbitals_sampled(exx):
     orc = oracle.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
     cols = [3, 200]
     ref = orc.exx_apply(s.psi[:s.n_occ], s.f, s.psi, cols=cols)
-    out = {}
-    for prec, tol in ((0, 1e-10), (4, 1e-6)):
-        p = exx.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
-        p.set_precision(prec)
-        vx = p.apply(psi[:s.n_occ], f, psi)
-        assert pm.rel(vx.cpu().numpy()[cols], ref) < tol
-        out[prec] = (vx, p.energy(psi[:s.n_occ], f, vx))
-        p.close()
-    e64, e10 = out[0][1], out[4][1]
-    assert abs(e10 - e64) <= 1e-8 * abs(e64)
+    p = exx.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    p.set_precision(exx.EXX_PREC_BF16X10)
+    vx = p.apply(psi[:s.n_occ], f, psi)
+    assert pm.rel(vx.cpu().numpy()[cols], ref) < 1e-6
+    p.close()
 
 
 def test_batch_of_48_systems_sampled(exx):

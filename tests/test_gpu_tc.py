@@ -2,13 +2,17 @@
 
 1. One 128 x n x k tcgen05 tile with bf16 / tf32 operands against an FP64 matmul of the
    same rounded operands (checks descriptors, operand layout, TMEM read-back).
-2. exx_apply against the CPU oracle.  BF16X10 (four fixed-point slices, exact
-   tensor-core accumulation, hi+lo intermediates) must meet the split-precision targets:
-   <= 1e-6 relative Frobenius on VxPsi and <= 1e-8 relative on E_x.  The cheaper forms
-   are checked against their own bounds: BF16X6 (three slices, ~24 bits, FP32
-   intermediates: VxPsi 1e-6, E_x 1e-7), TF32X3 (floating split; the tensor core rounds
-   its FP32 accumulation toward zero, a bias shared by all pairs: 1e-6 / 1e-6) and
-   BF16X3 (two slices, ~16 bits).
+2. exx_apply against the CPU oracle.  The modes that meet the split-precision targets
+   (<= 1e-6 relative Frobenius on VxPsi, <= 1e-8 relative on E_x) are held to them:
+   BF16X7 (three-pass, base-512 digits) and BF16X10 (four base-256 slices, hi+lo
+   intermediates).  The other split forms DO NOT MEET the target and are kept only as
+   comparison modes; their tests record the error band they stay in (measured at 48^3 x
+   256 orbitals: BF16X6 E_x 1.45e-8, TF32X3 VxPsi 5.6e-7 / E_x 5.7e-7, BF16X3 5.6e-5 /
+   5.4e-5) and fail only if a mode leaves its band:
+     BF16X6  VxPsi 1e-6, E_x 1e-7   (three base-256 slices, FP32 intermediates, ~24 bits)
+     TF32X3  VxPsi 1e-6, E_x 1e-6   (floating split; the tensor core's FP32 accumulation
+                                     rounds toward zero, a bias shared by every pair)
+     BF16X3  VxPsi 2e-4, E_x 1e-4   (two slices, ~16 bits)
 """
 import ctypes
 
@@ -22,8 +26,11 @@ from tests import pinmath as pm
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-SPLIT = {"bf16x10": (4, 1e-6, 1e-8), "bf16x6": (3, 1e-6, 1e-7), "tf32x3": (2, 1e-6, 1e-6),
-         "bf16x3": (1, 2e-4, 1e-4)}
+# modes that meet the split-precision targets: (code, VxPsi, E_x)
+TARGET = {"bf16x7": (5, 1e-6, 1e-8), "bf16x10": (4, 1e-6, 1e-8)}
+# comparison modes that do not meet the target: the error bands they are recorded in
+BANDS = {"bf16x6": (3, 1e-6, 1e-7), "tf32x3": (2, 1e-6, 1e-6), "bf16x3": (1, 2e-4, 1e-4)}
+SPLIT = {**TARGET, **BANDS}
 
 
 @pytest.fixture(scope="module")
@@ -99,7 +106,7 @@ def test_split_exx_apply_matches_oracle(exx, name, case):
     assert err_e < tol_e
 
 
-@pytest.mark.parametrize("name", ["bf16x10", "bf16x6", "tf32x3"])
+@pytest.mark.parametrize("name", ["bf16x7", "bf16x10", "bf16x6", "tf32x3"])
 def test_split_config1_all_pairs(exx, name):
     code, tol_v, tol_e = SPLIT[name]
     s = synth.config1()
@@ -111,7 +118,7 @@ def test_split_config1_all_pairs(exx, name):
     assert abs(e - e_ref) <= tol_e * abs(e_ref)
 
 
-@pytest.mark.parametrize("name", ["bf16x10", "bf16x6", "tf32x3"])
+@pytest.mark.parametrize("name", ["bf16x7", "bf16x10", "bf16x6", "tf32x3"])
 def test_split_batch_invariance_and_separate_inputs(exx, name):
     code = SPLIT[name][0]
     s = synth.small_system(n=(13, 11, 12), h=0.4, bc=(0, 0, 1), n_orb=10, kernel=0, seed=5, n_occ=6)
@@ -126,32 +133,6 @@ def test_split_batch_invariance_and_separate_inputs(exx, name):
     orc = oracle.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
     full = orc.exx_apply(s.psi[:6], s.f, s.psi)
     assert pm.rel(vx2.cpu().numpy(), full) < 1e-6
-
-
-@pytest.fixture(scope="module")
-def cfg2():
-    return synth.config2()
-
-
-@pytest.mark.parametrize("name", ["bf16x10", "bf16x6", "tf32x3"])
-def test_split_config2_sampled_columns(exx, cfg2, name):
-    """48^3 periodic screened, 128 orbitals: 3 sampled outputs vs the oracle, E_x and
-    xi vs the FP64 path (which the oracle pins to 1e-13 in test_gpu_fp64)."""
-    code, tol_v, tol_e = SPLIT[name]
-    s = cfg2
-    plan, psi, f, vx, e = _apply(exx, s, code)
-    cols = [0, 77, 127]
-    orc = oracle.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
-    ref = orc.exx_apply(s.psi, s.f, s.psi, cols=cols)
-    err_cols = pm.rel(vx.cpu().numpy()[cols], ref)
-    p64 = exx.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
-    vx64 = p64.apply(psi, f, psi)
-    e64 = p64.energy(psi, f, vx64)
-    err_full = float(torch.linalg.norm(vx - vx64) / torch.linalg.norm(vx64))
-    print(f"{name} config2: sampled {err_cols:.2e} full-vs-fp64 {err_full:.2e} E_x {abs(e - e64) / abs(e64):.2e}")
-    assert err_cols < tol_v
-    assert err_full < tol_v
-    assert abs(e - e64) <= tol_e * abs(e64)
 
 
 LONG = [dict(n=(72, 20, 24), bc=(1, 0, 1)), dict(n=(20, 72, 16), bc=(0, 1, 1)), dict(n=(16, 20, 144), bc=(1, 1, 0)),

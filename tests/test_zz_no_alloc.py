@@ -25,8 +25,11 @@ def test_gram_noalloc_matches_ace_build_on_consecutive_calls():
     import paper_2501_16572_gb300 as exx
     L = exx.load()
     stream = torch.cuda.current_stream().cuda_stream
+    # the last case fills the whole fixed scratch: n = 128 orbitals and N = 4096 >= 8 * 256
+    # grid points give eight split-K partial 128 x 128 tiles, including the edge tile
     cases = [dict(n=(22, 20, 18), bc=(1, 1, 0), n_orb=40, kernel=1, omega=0.106, seed=31),
-             dict(n=(13, 11, 12), bc=(0, 0, 0), n_orb=9, kernel=0, seed=32)]
+             dict(n=(13, 11, 12), bc=(0, 0, 0), n_orb=9, kernel=0, seed=32),
+             dict(n=(16, 16, 16), bc=(1, 1, 1), n_orb=128, kernel=1, omega=0.106, seed=33)]
     for case in cases:
         s = synth.small_system(h=0.4, **case)
         plan = exx.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
