@@ -1,0 +1,102 @@
+"""Write the oracle's exchange energy of the 72 x 72 x 144 slab workload (1024 orbitals, 800
+occupied) to tests/golden/slab72x72x144_energy.json.
+
+E_x = -1/4 sum_{m,n < 800} f_m f_n dV <rho_mn, V_mn> needs 320,400 unique pair solves
+(about 2.8e14 flop; hours on a CPU), so it is computed once and stored.  Only the CPU oracle
+(oracle/) does arithmetic here; this script splits the occupied orbitals into blocks and
+adds the block results:
+  * a diagonal block I: oracle energy_pairs over the pairs m <= n of I;
+  * an off-diagonal block pair I < J: oracle exx_apply with the occupied set I applied to the
+    orbitals of J gives out_n = -sum_{m in I} f_m psi_m V_mn, and twice the oracle energy of
+    (J, out) is the contribution of the pairs (m, n) and (n, m), m in I, n in J.
+The partial sums are checkpointed (one line per block or block pair), so an interrupted run
+resumes.  The record is keyed by the input recipe (workload name, seed, sizes and a hash of
+the synthetic-input module's source) and carries a fingerprint of Psi (sums over every
+orbital of psi^2 and of psi times a fixed weight): inputs regenerated on another machine
+may differ in the last bits (the exponentials and the QR factorisation are library code),
+so a reader compares the fingerprint within 1e-12 before using the stored energy; a
+relative input change of 1e-15 moves E_x by about 1e-15.
+
+Usage: python tests/golden/make_slab_energy.py [--block 40] [--threads N]
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import oracle  # noqa: E402
+import synth  # noqa: E402
+
+OUT = os.path.join(HERE, "slab72x72x144_energy.json")
+CKPT = os.path.join(HERE, "slab72x72x144_energy.partial.jsonl")
+
+
+def recipe_key(s):
+    src = open(os.path.join(ROOT, "synth", "__init__.py"), "rb").read()
+    rec = f"{s.name}|{s.n}|{s.h}|{s.bc}|{s.fd_order}|{s.kernel}|{s.omega}|{s.n_orb}|{s.n_occ}|" \
+          f"seed={synth.SEED_BASE + 5}|synth={hashlib.sha256(src).hexdigest()[:16]}"
+    return hashlib.sha256(rec.encode()).hexdigest()[:24], rec
+
+
+def fingerprint(psi):
+    """Per-orbital sums of psi^2 and of psi * w, w(r) = 1 + (r mod 7) / 7 (fixed weight)."""
+    w = 1.0 + (np.arange(psi.shape[1]) % 7) / 7.0
+    return {"sum_sq": [float(v) for v in np.einsum("ij,ij->i", psi, psi)],
+            "sum_w": [float(v) for v in psi @ w]}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--block", type=int, default=40)
+    ap.add_argument("--threads", type=int, default=0)
+    a = ap.parse_args()
+    if a.threads:
+        oracle.set_num_threads(a.threads)
+    s = synth.config5()
+    key, rec = recipe_key(s)
+    no = s.n_occ
+    psi = s.psi
+    f = s.f
+    orc = oracle.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    blocks = [(b, min(no, b + a.block)) for b in range(0, no, a.block)]
+    done = {}
+    if os.path.exists(CKPT):
+        for line in open(CKPT):
+            r = json.loads(line)
+            if r["key"] == key and r["block"] == a.block:
+                done[(r["I"], r["J"])] = r["E"]
+    t0 = time.time()
+    todo = [(i, j) for i in range(len(blocks)) for j in range(i, len(blocks)) if (i, j) not in done]
+    for k, (i, j) in enumerate(todo):
+        (i0, i1), (j0, j1) = blocks[i], blocks[j]
+        if i == j:
+            e = orc.energy_pairs(psi[i0:i1], f[i0:i1])
+        else:
+            out = orc.exx_apply(psi[i0:i1], f[i0:i1], psi[j0:j1])
+            e = 2.0 * orc.energy(psi[j0:j1], f[j0:j1], out)
+        done[(i, j)] = e
+        with open(CKPT, "a") as fh:
+            fh.write(json.dumps({"key": key, "block": a.block, "I": i, "J": j, "E": e}) + "\n")
+        el = time.time() - t0
+        print(f"[{k + 1}/{len(todo)}] blocks ({i},{j}) E={e:.15e}  {el:.0f} s", flush=True)
+    E = math.fsum(done.values())
+    json.dump({"workload": s.name, "key": key, "recipe": rec, "E_x": E, "n_occ": no,
+               "unique_pair_solves": no * (no + 1) // 2, "block": a.block,
+               "oracle_threads": oracle.num_threads(), "fingerprint": fingerprint(psi),
+               "how": "oracle energy_pairs per diagonal block + 2 x oracle energy of oracle exx_apply per "
+                      "off-diagonal block pair, summed with math.fsum (tests/golden/make_slab_energy.py)"},
+              open(OUT, "w"), indent=1)
+    print("E_x", E, "->", OUT)
+
+
+if __name__ == "__main__":
+    main()

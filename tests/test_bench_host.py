@@ -32,3 +32,28 @@ def test_traffic_record_is_well_formed():
         assert r["bytes_per_field"] > 0, name
         assert len(r["src_hash"]) == 16 and r["sources"], name
         b.src_hash(r["sources"])   # every listed source exists and hashes
+
+
+def test_roofline_bytes_follow_the_staged_fp32_rule():
+    """Algorithmic bytes of a pass: 4 B in + 4 B out per grid element and pair field, plus
+    f(Lambda) (8 B per point) once per launch for the pass that scales; the apply roofline
+    counts 16 N B per unique pair plus the compulsory FP64 input and output."""
+    b = _bench()
+
+    class S:
+        n = (48, 48, 48)
+        N = 48 ** 3
+        n_orb = 128
+        n_occ = 128
+
+        def unique_pairs(self):
+            return 8256
+
+    s = S()
+    r = b.roofline(s, "bf16x7", "pass3", 10.0, 10, 1, {"hbm_gbs": 6000.0})
+    fields = 8256 / 10
+    assert r["algorithmic_bytes_per_launch"] == 8 * s.N * fields + 8 * s.N
+    assert abs(r["achieved"] - r["algorithmic_bytes_per_launch"] / 1e-3 / 1e9) < 1e-6
+    assert r["kernel"].startswith("zpass_kernel")
+    ra = b.roofline_apply(s, "bf16x7", 10.0, {"hbm_gbs": 6000.0})
+    assert ra["bytes_per_apply"] == 16 * s.N * 8256 + 8 * s.N * 256
