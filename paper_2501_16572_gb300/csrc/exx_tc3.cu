@@ -29,7 +29,6 @@
 #include "exx_internal.h"
 #include "tc_ptx.cuh"
 
-#include <cuda.h>   // CUtensorMap (the encoder is fetched from the driver at run time)
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -489,9 +488,6 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 2) slice_pass_kernel(const _
 // The matrix images stream through nbuf shared-memory buffers (bulk copies by the producer
 // warp) unless all 2 NB blocks are resident.
 struct ZArgs {
-    CUtensorMap tmap;            // staged input: (R rows, n3 lines, fields), box 128 x n3 x 1
-    int stage;
-    uint32_t offS;
     long ntiles;
     int tpfz, R, n3, Kp;
     long N;
@@ -507,8 +503,26 @@ struct ZArgs {
     int *err;
 };
 
-template <int TPR>
-__global__ void __launch_bounds__(kRows * TPR + 96) zpass_kernel(const __grid_constant__ ZArgs a)
+// Input of tile t for this thread's units u = dq + g TPR of row `row` (zeros past n3 and for
+// rows past the field or tiles past the end).
+template <int TPR, int UPT>
+__device__ __forceinline__ void z_load_tile(const ZArgs &a, long t, int row, int dq, float (&x)[UPT][4])
+{
+    const long pp = t / a.tpfz;
+    const long rr = (t - pp * a.tpfz) * kRows + row;
+    const bool ok_row = t < a.ntiles && rr < a.R;
+    const float *src = a.in + size_t(ok_row ? pp : 0) * a.N + (ok_row ? rr : 0);
+#pragma unroll
+    for (int g = 0; g < UPT; ++g)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int z = 4 * (dq + g * TPR) + e;
+            x[g][e] = (ok_row && z < a.n3) ? src[size_t(z) * a.R] : 0.f;
+        }
+}
+
+template <int TPR, int UPT>
+__global__ void __launch_bounds__(kRows * TPR + 64, (UPT <= 4 ? 2 : 1)) zpass_kernel(const __grid_constant__ ZArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     constexpr int NT = kRows * TPR;
@@ -522,10 +536,8 @@ __global__ void __launch_bounds__(kRows * TPR + 96) zpass_kernel(const __grid_co
     uint64_t *bar_d = bar_a + 1;
     uint64_t *bfull = bar_a + 2;
     uint64_t *bempty = bfull + a.nbuf;
-    uint64_t *stg_full = bempty + a.nbuf, *stg_empty = stg_full + 1;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(stg_empty + 1);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bempty + a.nbuf);
     int *sflag = reinterpret_cast<int *>(tslot + 1);
-    const float *stg = reinterpret_cast<const float *>(smem + a.offS);   // [z][128 rows]
     const int Kp = a.Kp, WN = a.WN, NB = a.NB;
     const uint32_t sbo = uint32_t(Kp) * 16u;
     const uint32_t a_piece = uint32_t(kRows) * Kp * 2u;
@@ -546,8 +558,6 @@ __global__ void __launch_bounds__(kRows * TPR + 96) zpass_kernel(const __grid_co
             tc::mbar_init(bfull + b, 1);
             tc::mbar_init(bempty + b, 1);
         }
-        tc::mbar_init(stg_full, 1);
-        tc::mbar_init(stg_empty, 1);
         *sflag = 0;
     }
     if (warp == 0) tc::tmem_alloc(tslot, uint32_t(a.tmem_cols));
@@ -561,24 +571,7 @@ __global__ void __launch_bounds__(kRows * TPR + 96) zpass_kernel(const __grid_co
         return (j < NB ? a.imgF : a.imgI) + size_t(j < NB ? j : j - NB) * a.blk_bytes;
     };
 
-    if (warp == NT / 32 + 2) {
-        // ---- staging warp: the next tile's input rows (one TMA box), once the compute
-        //      threads have cut the current tile's forward operand ----
-        if (a.stage && lane == 0) {
-            long it = 0;
-            for (long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
-                if (it > 0 && !tc::mbar_wait_bounded(stg_empty, uint32_t((it - 1) & 1), kWaitLimit)) {
-                    atomicExch(sflag, 1);
-                    break;
-                }
-                const long p = tile / a.tpfz;
-                const int r0 = int(tile - p * a.tpfz) * kRows;
-                tc::mbar_arrive_expect_tx(stg_full, uint32_t(kRows) * uint32_t(a.n3) * 4u);
-                tc::tma_load_3d(smem + a.offS, &a.tmap, r0, 0, int(p), stg_full);
-            }
-            if (it > 0 && !tc::mbar_wait_bounded(stg_full, uint32_t((it - 1) & 1), kWaitLimit)) atomicExch(sflag, 1);
-        }
-    } else if (warp == NT / 32 + 1) {
+    if (warp == NT / 32 + 1) {
         // ---- producer warp: matrix blocks into the shared-memory buffers ----
         if (lane == 0) {
             if (a.resident) {
@@ -661,7 +654,10 @@ __global__ void __launch_bounds__(kRows * TPR + 96) zpass_kernel(const __grid_co
             first = false;
         }
     } else {
-        // ---- compute threads: row drow of this warp's TMEM quarter, part dq ----
+        // ---- compute threads: row `row` of this warp's TMEM quarter, part dq.  Each thread
+        //      keeps its units u = dq + g TPR (g < UPT) of the row in registers: the tile's
+        //      input, then f(Lambda) (loaded while the forward GEMM runs), and the next tile's
+        //      input is loaded while the inverse GEMM runs ----
         const int quarter = warp & 3, dq = warp >> 2;
         const int row = quarter * 32 + lane;
         const uint32_t lane_q = uint32_t(quarter * 32) << 16;
@@ -676,13 +672,10 @@ __global__ void __launch_bounds__(kRows * TPR + 96) zpass_kernel(const __grid_co
             for (int q = 0; q < TPR; ++q) m = fmaxf(m, maxb[q * kRows + row]);
             return m;
         };
-        auto handoff = [&](bool release) {
+        auto handoff = [&]() {
             tc::fence_proxy_async_smem();
             const bool stop = tc::bar_red_or(1, NT, *sflag != 0);
-            if (tid == 0 && !stop) {
-                mbar_arrive(bar_a);
-                if (release && a.stage) mbar_arrive(stg_empty);
-            }
+            if (tid == 0 && !stop) mbar_arrive(bar_a);
             return stop;
         };
         auto wait_d = [&]() {
@@ -690,106 +683,87 @@ __global__ void __launch_bounds__(kRows * TPR + 96) zpass_kernel(const __grid_co
             ph ^= 1u;
             tc::tc_fence_after();
         };
-        long it = 0;
-        for (long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
+        float x[UPT][4];
+        z_load_tile<TPR, UPT>(a, blockIdx.x, row, dq, x);
+        for (long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
             const long p = tile / a.tpfz;
             const long r0 = (tile - p * a.tpfz) * kRows;
             const bool act = r0 + row < R;
             const long r = act ? r0 + row : 0;
-            const float *src = a.in + size_t(p) * a.N + r;
-            // ---- forward operand: row max, then digits.  Staged: from the tile in shared
-            //      memory; else straight from global memory, three units of loads in flight ----
-            if (a.stage && !tc::mbar_wait_bounded(stg_full, uint32_t(it & 1), kWaitLimit)) atomicExch(sflag, 1);
-            auto load3 = [&](int base, float (&h)[3][4]) {
-#pragma unroll
-                for (int g = 0; g < 3; ++g)
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int z = 4 * (base + g * TPR) + e;
-                        h[g][e] = 0.f;
-                        if (act && z < n3) h[g][e] = a.stage ? stg[size_t(z) * kRows + row] : src[size_t(z) * R];
-                    }
-            };
+            // ---- forward operand from the registers: row max, digits ----
             float mx = 0.f;
-            for (int base = dq; 4 * base < n3; base += 3 * TPR) {
-                float h[3][4];
-                load3(base, h);
 #pragma unroll
-                for (int g = 0; g < 3; ++g)
+            for (int g = 0; g < UPT; ++g)
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) mx = fmaxf(mx, fabsf(h[g][e]));
-            }
+                for (int e = 0; e < 4; ++e) mx = fmaxf(mx, fabsf(x[g][e]));
             float sc, inv;
             row_scales(rowmax(mx), sc, inv);
             const float rs_f = inv;
-            for (int base = dq; 4 * base < n3; base += 3 * TPR) {
-                float h[3][4];
-                load3(base, h);
-                if (!act) continue;
+            if (act) {
 #pragma unroll
-                for (int g = 0; g < 3; ++g) {
-                    const int z0 = 4 * (base + g * TPR);
-                    if (z0 >= n3) continue;
-                    const float l[4] = {0.f, 0.f, 0.f, 0.f};
-                    store_digits4(sA, a_piece, img_at(row, z0 >> 3, sbo) + uint32_t(z0 & 7) * 2u, h[g], l, sc);
+                for (int g = 0; g < UPT; ++g) {
+                    const int z0 = 4 * (dq + g * TPR);
+                    if (z0 < n3) {
+                        const float l[4] = {0.f, 0.f, 0.f, 0.f};
+                        store_digits4(sA, a_piece, img_at(row, z0 >> 3, sbo) + uint32_t(z0 & 7) * 2u, x[g], l, sc);
+                    }
                 }
             }
-            if (handoff(true)) break;
+            if (handoff()) break;
+            // f(Lambda) of this thread's columns, loaded while the forward GEMM runs
+            float fh[UPT][4], fl[UPT][4];
+#pragma unroll
+            for (int g = 0; g < UPT; ++g)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int c = 4 * (dq + g * TPR) + e;
+                    const bool ok = act && c < n3;
+                    fh[g][e] = ok ? a.Fh[size_t(c) * R + r] : 0.f;
+                    fl[g][e] = ok ? a.Fl[size_t(c) * R + r] : 0.f;
+                }
             wait_d();
             // ---- middle: (D f) as hi (plane 0: low halves, plane 1: high halves) + lo
-            //      (plane 2, bf16) in the bytes its own digits take, then re-slice; the
-            //      f(Lambda) values of three units are loaded before their TMEM reads ----
+            //      (plane 2, bf16) in the bytes its own digits take, then re-slice ----
             float mx2 = 0.f;
-            for (int base = dq; base < a.NC / 4; base += 3 * TPR) {
-                float fh[3][4], fl[3][4];
 #pragma unroll
-                for (int g = 0; g < 3; ++g)
+            for (int g = 0; g < UPT; ++g) {
+                const int u4 = dq + g * TPR;
+                if (u4 >= a.NC / 4) break;   // uniform across the warp
+                float v0[4], v1[4];
+                tmem_pair4(tmem + lane_q + uint32_t(4 * u4), tmem + lane_q + uint32_t(a.NC + 4 * u4), v0, v1);
+                const int c0 = 4 * u4;
+                if (!act || c0 >= n3) continue;
+                uint32_t lo16[4], hi16[4], lb[4];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int c = 4 * (base + g * TPR) + e;
-                        const bool ok = act && c < n3;
-                        fh[g][e] = ok ? a.Fh[size_t(c) * R + r] : 0.f;
-                        fl[g][e] = ok ? a.Fl[size_t(c) * R + r] : 0.f;
-                    }
-#pragma unroll
-                for (int g = 0; g < 3; ++g) {
-                    const int u4 = base + g * TPR;
-                    if (u4 >= a.NC / 4) break;   // uniform across the warp
-                    float v0[4], v1[4];
-                    tmem_pair4(tmem + lane_q + uint32_t(4 * u4), tmem + lane_q + uint32_t(a.NC + 4 * u4), v0, v1);
-                    const int c0 = 4 * u4;
-                    if (!act || c0 >= n3) continue;
-                    uint32_t lo16[4], hi16[4], lb[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const float scl = rs_f * csF[c0 + e];
-                        const float h0 = v0[e] + v1[e];
-                        const float bp = h0 - v0[e];
-                        const float l0 = ((v0[e] - (h0 - bp)) + (v1[e] - bp)) * scl;
-                        const float h = h0 * scl;
-                        const float prh = h * fh[g][e];   // zero past n3 (f = 0 there)
-                        const float prl = fmaf(h, fh[g][e], -prh) + fmaf(h, fl[g][e], l0 * fh[g][e]);
-                        mx2 = fmaxf(mx2, fabsf(prh));
-                        const uint32_t hb = __float_as_uint(prh);
-                        lo16[e] = hb & 0xffffu;
-                        hi16[e] = hb >> 16;
-                        lb[e] = uint32_t(__bfloat16_as_ushort(__float2bfloat16_rn(prl)));
-                    }
-                    const uint32_t o = img_at(row, c0 >> 3, sbo) + uint32_t(c0 & 7) * 2u;
-                    *reinterpret_cast<uint2 *>(sA + o) =
-                        make_uint2(lo16[0] | (lo16[1] << 16), lo16[2] | (lo16[3] << 16));
-                    *reinterpret_cast<uint2 *>(sA + a_piece + o) =
-                        make_uint2(hi16[0] | (hi16[1] << 16), hi16[2] | (hi16[3] << 16));
-                    *reinterpret_cast<uint2 *>(sA + 2 * a_piece + o) =
-                        make_uint2(lb[0] | (lb[1] << 16), lb[2] | (lb[3] << 16));
+                for (int e = 0; e < 4; ++e) {
+                    const float scl = rs_f * csF[c0 + e];
+                    const float h0 = v0[e] + v1[e];
+                    const float bp = h0 - v0[e];
+                    const float l0 = ((v0[e] - (h0 - bp)) + (v1[e] - bp)) * scl;
+                    const float h = h0 * scl;
+                    const float prh = h * fh[g][e];   // zero past n3 (f = 0 there)
+                    const float prl = fmaf(h, fh[g][e], -prh) + fmaf(h, fl[g][e], l0 * fh[g][e]);
+                    mx2 = fmaxf(mx2, fabsf(prh));
+                    const uint32_t hb = __float_as_uint(prh);
+                    lo16[e] = hb & 0xffffu;
+                    hi16[e] = hb >> 16;
+                    lb[e] = uint32_t(__bfloat16_as_ushort(__float2bfloat16_rn(prl)));
                 }
+                const uint32_t o = img_at(row, c0 >> 3, sbo) + uint32_t(c0 & 7) * 2u;
+                *reinterpret_cast<uint2 *>(sA + o) = make_uint2(lo16[0] | (lo16[1] << 16), lo16[2] | (lo16[3] << 16));
+                *reinterpret_cast<uint2 *>(sA + a_piece + o) =
+                    make_uint2(hi16[0] | (hi16[1] << 16), hi16[2] | (hi16[3] << 16));
+                *reinterpret_cast<uint2 *>(sA + 2 * a_piece + o) =
+                    make_uint2(lb[0] | (lb[1] << 16), lb[2] | (lb[3] << 16));
             }
             tc::tc_fence_before();
             row_scales(rowmax(mx2), sc, inv);
             const float rs_i = inv;
-            if (act)
-                for (int u4 = dq; 4 * u4 < n3; u4 += TPR) {
-                    const int c0 = 4 * u4;
+            if (act) {
+#pragma unroll
+                for (int g = 0; g < UPT; ++g) {
+                    const int c0 = 4 * (dq + g * TPR);
+                    if (c0 >= n3) continue;
                     const uint32_t o = img_at(row, c0 >> 3, sbo) + uint32_t(c0 & 7) * 2u;
                     const uint2 wl = *reinterpret_cast<const uint2 *>(sA + o);
                     const uint2 wh = *reinterpret_cast<const uint2 *>(sA + a_piece + o);
@@ -805,11 +779,16 @@ __global__ void __launch_bounds__(kRows * TPR + 96) zpass_kernel(const __grid_co
                     }
                     store_digits4(sA, a_piece, o, h, l, sc);
                 }
-            if (handoff(false)) break;
+            }
+            if (handoff()) break;
+            z_load_tile<TPR, UPT>(a, tile + gridDim.x, row, dq, x);   // the next tile, while the inverse GEMM runs
             wait_d();
             // ---- inverse result -> (r, z) of the output field ----
             float *dst = a.out + size_t(p) * a.N + r;
-            for (int u4 = dq; u4 < a.NC / 4; u4 += TPR) {
+#pragma unroll
+            for (int g = 0; g < UPT; ++g) {
+                const int u4 = dq + g * TPR;
+                if (u4 >= a.NC / 4) break;
                 float v0[4], v1[4];
                 tmem_pair4(tmem + lane_q + uint32_t(4 * u4), tmem + lane_q + uint32_t(a.NC + 4 * u4), v0, v1);
                 if (!act) continue;
@@ -923,24 +902,27 @@ SliceLayout slice_layout(const Plan &P, bool pair = true)
 
 struct ZLayout {
     size_t smem;
-    uint32_t offB, offCs, offMax, offBar, blk_bytes, offS;
-    int NB, WN, NC, nbuf, resident, tmem_cols, stage;
+    uint32_t offB, offCs, offMax, offBar, blk_bytes;
+    int NB, WN, NC, nbuf, resident, tmem_cols;
 };
 
 constexpr int kTPRz = 4;
 constexpr int kTPRs = 4;
 
-// R = rows of a field (n1 n2): the input tile is staged by TMA when R % 4 == 0 and it fits
-bool z_layout(int n3, long R, ZLayout &L)
+// Matrix blocks: all 2 NB resident when they fit; else streamed through 2 (or 3) buffers,
+// the fewest blocks (widest N) that fit first (measured: wider blocks with two buffers beat
+// narrower ones with three).
+bool z_layout(int n3, ZLayout &L)
 {
     const int Kp = pad16i(n3);
     const size_t abytes = 3 * size_t(kRows) * Kp * 2;
-    for (int pass = 0; pass < 2; ++pass) {   // first: every block resident; then: streamed
+    for (int pass = 0; pass < 3; ++pass) {   // resident; streamed, 2 buffers; streamed, 3 buffers
         for (int NB = 1; NB <= 16; ++NB) {
             const int WN = pad16i((n3 + NB - 1) / NB);
             if (WN * (NB - 1) >= n3) continue;   // no empty block
             const size_t blk = mat_image_bytes(WN, Kp);
-            const int nbuf = pass == 0 ? 2 * NB : 2;
+            const int nbuf = pass == 0 ? 2 * NB : (pass == 1 ? 2 : 3);
+            if (pass > 0 && nbuf >= 2 * NB) continue;
             size_t off = align_up(abytes, 1024);
             const uint32_t offB = uint32_t(off);
             off += size_t(nbuf) * blk;
@@ -949,14 +931,11 @@ bool z_layout(int n3, long R, ZLayout &L)
             const uint32_t offMax = uint32_t(align_up(off, 16));
             off = offMax + size_t(kTPRz) * kRows * 4;
             const uint32_t offBar = uint32_t(align_up(off, 16));
-            off = offBar + 16 + 16 * size_t(nbuf) + 16 + 16;
+            off = offBar + 16 + 16 * size_t(nbuf) + 16;
             const int NC = NB * WN;
             if (off <= kSmemLimit && 2 * NC <= 512) {
-                const uint32_t offS = uint32_t(align_up(off, 1024));
-                const size_t staged = offS + size_t(kRows) * n3 * 4;
-                const int stage = (R % 4 == 0 && staged <= kSmemLimit) ? 1 : 0;
-                L = {stage ? staged : off, offB, offCs, offMax, offBar, uint32_t(blk), offS, NB, WN, NC, nbuf,
-                     pass == 0 ? 1 : 0, tmem_pow2(2 * NC), stage};
+                L = {off, offB, offCs, offMax, offBar, uint32_t(blk), NB, WN, NC, nbuf, pass == 0 ? 1 : 0,
+                     tmem_pow2(2 * NC)};
                 return true;
             }
         }
@@ -964,37 +943,13 @@ bool z_layout(int n3, long R, ZLayout &L)
     return false;
 }
 
-// cuTensorMapEncodeTiled, fetched from the driver through the runtime once.
-typedef CUresult (*EncodeTiled3)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-EncodeTiled3 encoder()
+// Units of 4 grid points per thread and row in pass B, from a few compiled widths.
+int z_upt(int n3)
 {
-    static EncodeTiled3 fn = [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            return reinterpret_cast<EncodeTiled3>(p);
-        return EncodeTiled3(nullptr);
-    }();
-    return fn;
-}
-
-// FP32 fields (R rows fastest, n3 lines R apart, fields N apart) read in 128 x n3 x 1 boxes;
-// rows past R come back as zeros.  Needs a 16-byte aligned base and R, N multiples of 4.
-bool make_rows_map(CUtensorMap *m, const float *base, long R, int n3, long nfields, long N)
-{
-    EncodeTiled3 fn = encoder();
-    if (!fn || (reinterpret_cast<uintptr_t>(base) & 15) || (R & 3) || (N & 3) || n3 < 1 || n3 > 256) return false;
-    const cuuint64_t dims[3] = {cuuint64_t(R), cuuint64_t(n3), cuuint64_t(nfields)};
-    const cuuint64_t strides[2] = {cuuint64_t(R) * 4, cuuint64_t(N) * 4};
-    const cuuint32_t box[3] = {cuuint32_t(kRows), cuuint32_t(n3), 1};
-    const cuuint32_t es[3] = {1, 1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, es,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    const int need = ((n3 + 3) / 4 + kTPRz - 1) / kTPRz;
+    for (int u : {2, 3, 4, 6, 9, 13})
+        if (need <= u) return u;
+    return 0;
 }
 
 // CTAs per SM from the SM's limits (registers in 256-register warp units, shared memory with
@@ -1035,7 +990,7 @@ bool tc3_supported(const Plan &P, std::string *why)
         return false;
     }
     ZLayout Z;
-    if (!z_layout(P.n[2], long(P.n[0]) * P.n[1], Z)) {
+    if (!z_layout(P.n[2], Z) || z_upt(P.n[2]) == 0) {
         if (why) *why = "BF16X7: the z axis is too long for the on-chip operand images";
         return false;
     }
@@ -1066,7 +1021,7 @@ int tc3_upload(Plan &P)
     }
     // z: NB blocks of WN outputs each
     ZLayout Z;
-    z_layout(P.n[2], long(P.n[0]) * P.n[1], Z);
+    z_layout(P.n[2], Z);
     {
         const int nd = P.n[2], Kp = pad16i(nd);
         const std::vector<double> &V = P.V[2];
@@ -1138,9 +1093,9 @@ int tc3_solve_batch(Plan &P, const int2 *pairs_d, int nfields, float *bufA, floa
         a.offS = L.offS;
         a.stg_plane = L.stg_plane;
         a.err = static_cast<int *>(P.err_d.p);
+        size_t smem = L.smem;
         auto kern = pair ? slice_pass_kernel<true, kTPRs> : slice_pass_kernel<false, kTPRs>;
         const int threads = kRows * kTPRs + 64;
-        size_t smem = L.smem;
         int per_sm = 1;
         if (int rc = launch_setup(kern, threads, smem, L.tmem_cols, per_sm)) return rc;
         const int grid = int(std::min<long>(a.ntiles, long(P.num_sms) * per_sm));
@@ -1155,12 +1110,9 @@ int tc3_solve_batch(Plan &P, const int2 *pairs_d, int nfields, float *bufA, floa
     // pass B
     {
         ZLayout Z;
-        z_layout(n3, long(n1) * n2, Z);
+        z_layout(n3, Z);
         ZArgs a{};
         a.R = n1 * n2;
-        a.stage = Z.stage;
-        a.offS = Z.offS;
-        if (a.stage && !make_rows_map(&a.tmap, bufA, a.R, n3, nfields, P.N)) a.stage = 0;
         a.tpfz = (a.R + kRows - 1) / kRows;
         a.ntiles = long(nfields) * a.tpfz;
         a.n3 = n3;
@@ -1184,9 +1136,17 @@ int tc3_solve_batch(Plan &P, const int2 *pairs_d, int nfields, float *bufA, floa
         a.offBar = Z.offBar;
         a.tmem_cols = Z.tmem_cols;
         a.err = static_cast<int *>(P.err_d.p);
-        auto kern = zpass_kernel<kTPRz>;
-        const int threads = kRows * kTPRz + 96;
-        size_t smem = a.stage ? Z.smem : std::min<size_t>(Z.smem, Z.offS);
+        void (*kern)(const ZArgs) = nullptr;
+        switch (z_upt(n3)) {
+        case 2: kern = zpass_kernel<kTPRz, 2>; break;
+        case 3: kern = zpass_kernel<kTPRz, 3>; break;
+        case 4: kern = zpass_kernel<kTPRz, 4>; break;
+        case 6: kern = zpass_kernel<kTPRz, 6>; break;
+        case 9: kern = zpass_kernel<kTPRz, 9>; break;
+        default: kern = zpass_kernel<kTPRz, 13>; break;
+        }
+        const int threads = kRows * kTPRz + 64;
+        size_t smem = Z.smem;
         int per_sm = 1;
         if (int rc = launch_setup(kern, threads, smem, Z.tmem_cols, per_sm)) return rc;
         const int grid = int(std::min<long>(a.ntiles, long(P.num_sms) * per_sm));
