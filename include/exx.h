@@ -122,6 +122,27 @@ int exx_plan_set_batch(exx_plan plan, int pairs_per_batch, int block_orbitals);
  * runs everything.  0 <= rank < world. */
 int exx_plan_set_shard(exx_plan plan, int rank, int world);
 
+/* Autotuner of the tile and schedule settings (Sec. II.B's batch size n_c and the kernel
+ * shapes), measured on this grid with the caller's own data: exx_apply's arguments and
+ * rules (out is used as scratch and left holding partial results).  Coordinate descent over
+ *   pairs per batch {default, 256, 512, 1024} x orbitals per pair block {8, 16}, then, in
+ *   the BF16X7 mode, the pass-B matrix block width and shared-memory buffer count (every
+ *   choice that fits) and the slice-pass input staging (on, off);
+ * each candidate runs up to three batches of the pair schedule twice (warm-up, then timed
+ * with CUDA events on `stream`); the fastest per pair solve is kept in the plan (as by
+ * exx_plan_set_batch) and in a process-wide cache keyed by grid, boundary conditions,
+ * precision, n_occ, n_in and aliasing, so that a later plan with the same key takes it
+ * without measuring.  flags bit 0 = measure again even if cached.  Synchronizes `stream`.
+ * Results of exx_apply do not depend on the choice (up to the order of compensated sums). */
+int exx_plan_autotune(exx_plan plan, const double *Psi_occ, int n_occ, long ld_occ, const double *f,
+                      const double *Psi_in, int n_in, long ld_in, double *out, long ld_out, int flags,
+                      exx_stream_t stream);
+
+/* The plan's settings (HOST int[5]: pairs per batch, orbitals per block, pass-B block width,
+ * pass-B buffers, slice staging; 0 / -1 = automatic), the autotuner's trial time per pair
+ * solve in ms (0 if never tuned) and *tuned_h = 0 (not tuned), 1 (measured), 2 (cache). */
+int exx_plan_get_tuning(exx_plan plan, int *settings_h, double *ms_per_pair_h, int *tuned_h);
+
 /* Free the plan and its device workspace (synchronizes the device first). */
 int exx_plan_destroy(exx_plan plan);
 
@@ -141,6 +162,17 @@ int exx_plan_get(exx_plan plan, int which, double *dst_h, long count);
 int exx_apply(exx_plan plan, const double *Psi_occ, int n_occ, long ld_occ, const double *f,
               const double *Psi_in, int n_in, long ld_in, double *out, long ld_out,
               exx_stream_t stream);
+
+/* The original (non-batched) Kronecker product formalism of Sec. II.A, Eq. 8: the same
+ * result as exx_apply (same arguments, layout, aliasing rule and errors), computed in FP64
+ * whatever the plan's precision, one orbital pair at a time, each pair's linear system with
+ * its 4 n_z + 2 dense matrix products issued as separate small GEMM launches (per frontal
+ * slice Vx^T B_k Vy, then the z axis, the f(Lambda) product, and the inverse).  It is there
+ * to measure what batching the right-hand sides buys (Sec. II.B, Figs. 1-2); it is launch
+ * bound by design and far slower than exx_apply.  Needs 3 N doubles of plan workspace. */
+int exx_apply_original(exx_plan plan, const double *Psi_occ, int n_occ, long ld_occ, const double *f,
+                       const double *Psi_in, int n_in, long ld_in, double *out, long ld_out,
+                       exx_stream_t stream);
 
 /* Exchange energy E_x = 1/4 sum_{n < n_occ} f_n dV <psi_n, VxPsi_n>, FP64 with
  * compensated (Neumaier) sums in a fixed order (the paper prints no formula; this

@@ -44,7 +44,8 @@ PREC_NAMES = {EXX_PREC_FP64: "fp64", EXX_PREC_BF16X3: "bf16x3", EXX_PREC_TF32X3:
 EXPORTED = ["exx_plan_create", "exx_plan_set_precision", "exx_plan_set_batch", "exx_plan_destroy",
             "exx_plan_get", "exx_apply", "exx_energy", "ace_build", "ace_apply", "exx_ace_step_host",
             "exx_apply_batched", "exx_plan_launch_count", "exx_status_string", "exx_last_error",
-            "exx_plan_set_timing", "exx_plan_get_timing", "exx_gram_noalloc", "exx_plan_set_shard"]
+            "exx_plan_set_timing", "exx_plan_get_timing", "exx_gram_noalloc", "exx_plan_set_shard",
+            "exx_apply_original", "exx_plan_autotune", "exx_plan_get_tuning"]
 TIMING_KINDS = ["pass1", "pass2", "pass3", "pass4", "pass5", "accum", "prep", "gemm", "chol", "energy"]
 
 _lib = None
@@ -87,6 +88,9 @@ def load():
     L.exx_ace_step_host.argtypes = [_vp, _vp, _i, _l, _i, _vp, _vp, _l, ctypes.POINTER(_d),
                                     ctypes.POINTER(_i), _vp]
     L.exx_apply_batched.argtypes = [ctypes.POINTER(_vp), _i, ctypes.POINTER(ExxApplyArgs), _vp]
+    L.exx_apply_original.argtypes = [_vp, _vp, _i, _l, _vp, _vp, _i, _l, _vp, _l, _vp]
+    L.exx_plan_autotune.argtypes = [_vp, _vp, _i, _l, _vp, _vp, _i, _l, _vp, _l, _i, _vp]
+    L.exx_plan_get_tuning.argtypes = [_vp, ctypes.POINTER(_i), ctypes.POINTER(_d), ctypes.POINTER(_i)]
     L.exx_plan_launch_count.argtypes = [_vp]
     L.exx_plan_launch_count.restype = _l
     L.exx_plan_set_timing.argtypes = [_vp, _i]
@@ -217,6 +221,42 @@ class Plan:
             raise ValueError("out must have n_in rows")
         _check(load().exx_apply(self._h, _ptr(psi_occ), n_occ, ld_occ, _ptr(f), _ptr(psi_in), n_in, ld_in,
                                 _ptr(out), ld_out, _stream(stream)), "exx_apply")
+        return out
+
+    def autotune(self, psi_occ, f, psi_in, out=None, remeasure=False, stream=None):
+        """exx_plan_autotune on these buffers; returns tuning() afterwards."""
+        import torch
+        n_occ, ld_occ = _orb(psi_occ, self.N, "psi_occ")
+        n_in, ld_in = _orb(psi_in, self.N, "psi_in")
+        if out is None:
+            out = torch.empty((n_in, self.N), dtype=torch.float64, device=psi_in.device)
+        _, ld_out = _orb(out, self.N, "out")
+        _check(load().exx_plan_autotune(self._h, _ptr(psi_occ), n_occ, ld_occ, _ptr(f), _ptr(psi_in), n_in, ld_in,
+                                        _ptr(out), ld_out, 1 if remeasure else 0, _stream(stream)), "exx_plan_autotune")
+        return self.tuning()
+
+    def tuning(self):
+        """{'pairs_per_batch', 'block_orbitals', 'z_block', 'z_buffers', 'staging', 'ms_per_pair', 'tuned'}"""
+        v = (_i * 5)()
+        ms, tuned = _d(0.0), _i(0)
+        _check(load().exx_plan_get_tuning(self._h, v, ctypes.byref(ms), ctypes.byref(tuned)), "exx_plan_get_tuning")
+        return {"pairs_per_batch": v[0], "block_orbitals": v[1], "z_block": v[2], "z_buffers": v[3],
+                "staging": v[4], "ms_per_pair": ms.value, "tuned": tuned.value}
+
+    def apply_original(self, psi_occ, f, psi_in, out=None, stream=None):
+        """exx_apply_original: the same result, one pair at a time with Eq. 8's 4 n_z + 2 GEMMs."""
+        import torch
+        n_occ, ld_occ = _orb(psi_occ, self.N, "psi_occ")
+        n_in, ld_in = _orb(psi_in, self.N, "psi_in")
+        if f.dtype != torch.float64 or not f.is_cuda or f.numel() < n_occ or not f.is_contiguous():
+            raise ValueError("f must be a contiguous float64 CUDA tensor with n_occ entries")
+        if out is None:
+            out = torch.empty((n_in, self.N), dtype=torch.float64, device=psi_in.device)
+        n_o, ld_out = _orb(out, self.N, "out")
+        if n_o != n_in:
+            raise ValueError("out must have n_in rows")
+        _check(load().exx_apply_original(self._h, _ptr(psi_occ), n_occ, ld_occ, _ptr(f), _ptr(psi_in), n_in,
+                                         ld_in, _ptr(out), ld_out, _stream(stream)), "exx_apply_original")
         return out
 
     def energy(self, psi_occ, f, vx, stream=None):

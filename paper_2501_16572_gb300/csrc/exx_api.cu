@@ -67,6 +67,9 @@ static void free_plan_buffers(Plan &P)
     for (auto &row : P.t3img)
         for (auto &b : row) dev_free(b);
     dev_free(P.F32n);
+    dev_free(P.orig_V);
+    dev_free(P.F64n);
+    dev_free(P.orig_ws);
     for (auto *b : {&P.F64, &P.F32, &P.work[0], &P.work[1], &P.work[2], &P.pairs_d, &P.blocks_d,
                     &P.acc_hi, &P.acc_lo, &P.g32, &P.psi32, &P.gemm_ws, &P.small_ws, &P.info_d,
                     &P.red_ws, &P.host_stage_psi, &P.host_stage_f, &P.host_stage_xi, &P.host_stage_w,
@@ -376,17 +379,21 @@ static int apply_prepare(Plan *P, ApplyCall &c, cudaStream_t s)
     return dev_reserve(P->work[1], fb);
 }
 
-// The launches of one exx_apply (stream work only: capturable into a CUDA graph).
-static int apply_launch(Plan *P, const ApplyCall &c, cudaStream_t s)
+// The launches of one exx_apply (stream work only: capturable into a CUDA graph).  With
+// b_count >= 0 only batches [b_first, b_first + b_count) run (autotuner trials).
+static int apply_launch(Plan *P, const ApplyCall &c, cudaStream_t s, int b_first = 0, int b_count = -1)
 {
     const Schedule &S = P->sched;
+    auto skip = [&](size_t b) {
+        return b_count >= 0 && (int(b) < b_first || int(b) >= b_first + b_count);
+    };
     const int2 *pairs_d = static_cast<const int2 *>(P->pairs_d.p);
     const Block *blocks_d = static_cast<const Block *>(P->blocks_d.p);
     if (P->prec == EXX_PREC_FP64) {
         EXX_CUDA(cudaMemset2DAsync(c.out, size_t(c.ld_out) * sizeof(double), 0, size_t(P->N) * sizeof(double),
                                    c.n_in, s));
         for (size_t b = 0; b < S.batches.size(); ++b) {
-            if (int(b % P->shard_world) != P->shard_rank) continue;
+            if (int(b % P->shard_world) != P->shard_rank || skip(b)) continue;
             const Batch &bt = S.batches[b];
             double *V = nullptr;
             if (int rc = fp64_solve_batch(*P, c.Psi_occ, c.ld_occ, c.Psi_in, c.ld_in, pairs_d + S.pair0[b], bt.nfields,
@@ -402,7 +409,7 @@ static int apply_launch(Plan *P, const ApplyCall &c, cudaStream_t s)
     if (int rc = tc_prepare_orbitals(*P, c.Psi_occ, c.n_occ, c.ld_occ, c.f, c.Psi_in, c.n_in, c.ld_in, c.aliased, s))
         return rc;
     for (size_t b = 0; b < S.batches.size(); ++b) {
-        if (int(b % P->shard_world) != P->shard_rank) continue;
+        if (int(b % P->shard_world) != P->shard_rank || skip(b)) continue;
         const Batch &bt = S.batches[b];
         if (int rc = tc_solve_batch(*P, prec, pairs_d + S.pair0[b], bt.nfields, static_cast<float *>(P->work[0].p),
                                     static_cast<float *>(P->work[1].p), s))
@@ -462,6 +469,171 @@ int exx_apply(exx_plan plan, const double *Psi_occ, int n_occ, long ld_occ, cons
     if (int rc = apply_prepare(P, c, s)) return rc;
     P->launches = 0;
     return apply_launch(P, c, s);
+}
+
+int exx_apply_original(exx_plan plan, const double *Psi_occ, int n_occ, long ld_occ, const double *f,
+                       const double *Psi_in, int n_in, long ld_in, double *out, long ld_out, exx_stream_t stream)
+{
+    Plan *P = as_plan(plan);
+    if (!P) return invalid("exx_apply_original: plan is NULL");
+    if (!Psi_occ || !f || !Psi_in || !out) return invalid("exx_apply_original: NULL array");
+    if (n_occ < 1 || n_in < 1 || n_occ > 65536 || n_in > 65536)
+        return invalid("exx_apply_original: orbital counts must be in [1, 65536]");
+    if (ld_occ < P->N || ld_in < P->N || ld_out < P->N) return invalid("exx_apply_original: leading dimensions must be >= N");
+    const char *o0 = reinterpret_cast<const char *>(out);
+    const char *o1 = o0 + (size_t(n_in - 1) * ld_out + P->N) * sizeof(double);
+    auto overlaps = [&](const double *a, int n, long ld) {
+        const char *a0 = reinterpret_cast<const char *>(a);
+        const char *a1 = a0 + (size_t(n - 1) * ld + P->N) * sizeof(double);
+        return a0 < o1 && o0 < a1;
+    };
+    if (overlaps(Psi_occ, n_occ, ld_occ) || overlaps(Psi_in, n_in, ld_in)) return invalid("exx_apply_original: out overlaps an input");
+    const bool aliased = (Psi_in == Psi_occ) && (ld_in == ld_occ) && (n_in >= n_occ);
+    P->launches = 0;
+    return original_apply(*P, Psi_occ, n_occ, ld_occ, f, Psi_in, n_in, ld_in, out, ld_out, aliased,
+                          reinterpret_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"
+
+namespace exx {
+
+// ---- autotuner: tile and schedule settings measured on the caller's grid and data ---------
+struct TuneKey {
+    int n[3], bc[3], prec, n_occ, n_in, aliased;
+    bool operator==(const TuneKey &o) const
+    {
+        return std::equal(n, n + 3, o.n) && std::equal(bc, bc + 3, o.bc) && prec == o.prec && n_occ == o.n_occ &&
+               n_in == o.n_in && aliased == o.aliased;
+    }
+};
+struct TuneVal {
+    int pairs, block, zwn, znbuf, stage;
+    double ms;
+};
+static std::mutex g_tune_mutex;
+static std::vector<std::pair<TuneKey, TuneVal>> g_tune_cache;
+
+static void tune_set(Plan &P, const TuneVal &v)
+{
+    P.pairs_per_batch = v.pairs;
+    P.block_orbitals = v.block;
+    P.t3_zwn = v.zwn;
+    P.t3_znbuf = v.znbuf;
+    P.t3_stage = v.stage;
+    std::fill(P.sched_key, P.sched_key + 4, -1);
+    bump_epoch(P);
+}
+
+// Device time per pair solve of batches [b0, b0 + nb) with setting v (one warm-up run, then
+// one timed run, CUDA events on s); +inf when the setting does not apply.
+static double tune_trial(Plan &P, ApplyCall c, const TuneVal &v, cudaStream_t s, int &rc)
+{
+    rc = EXX_OK;
+    tune_set(P, v);
+    if (P.prec == EXX_PREC_BF16X7 && (rc = tc3_upload(P)) != EXX_OK) return 1e300;
+    if ((rc = apply_prepare(&P, c, s)) != EXX_OK) return 1e300;
+    const int nb = int(P.sched.batches.size());
+    const int b0 = nb > 2 ? 1 : 0, cnt = std::min(3, nb - b0);
+    long pairs = 0;
+    for (int b = b0; b < b0 + cnt; ++b) pairs += P.sched.batches[b].nfields;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        rc = EXX_ERR_CUDA;
+        return 1e300;
+    }
+    double ms = 1e300;
+    if ((rc = apply_launch(&P, c, s, b0, cnt)) == EXX_OK) {
+        cudaEventRecord(e0, s);
+        rc = apply_launch(&P, c, s, b0, cnt);
+        cudaEventRecord(e1, s);
+        float t = 0.f;
+        if (rc == EXX_OK && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess)
+            ms = double(t) / double(std::max(1L, pairs));
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms;
+}
+
+}  // namespace exx
+
+extern "C" {
+
+int exx_plan_autotune(exx_plan plan, const double *Psi_occ, int n_occ, long ld_occ, const double *f,
+                      const double *Psi_in, int n_in, long ld_in, double *out, long ld_out, int flags,
+                      exx_stream_t stream)
+{
+    Plan *P = as_plan(plan);
+    ApplyCall c{Psi_occ, n_occ, ld_occ, f, Psi_in, n_in, ld_in, out, ld_out, false};
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (int rc = apply_prepare(P, c, s)) return rc;   // argument checks, aliasing
+    TuneKey key{{P->n[0], P->n[1], P->n[2]}, {P->bc[0], P->bc[1], P->bc[2]}, P->prec, n_occ, n_in, c.aliased ? 1 : 0};
+    if (!(flags & 1)) {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        for (auto &kv : g_tune_cache)
+            if (kv.first == key) {
+                tune_set(*P, kv.second);
+                if (P->prec == EXX_PREC_BF16X7)
+                    if (int rc = tc3_upload(*P)) return rc;
+                P->tuned = 2;
+                P->tune_ms = kv.second.ms;
+                return EXX_OK;
+            }
+    }
+    // coordinate descent: pair batch and orbital block, then (three-pass mode) the pass-B
+    // matrix blocks and buffers, then the slice-pass staging
+    TuneVal best{0, 0, 0, 0, -1, 1e300};
+    auto consider = [&](TuneVal v) -> int {
+        int rc = EXX_OK;
+        v.ms = tune_trial(*P, c, v, s, rc);
+        if (rc != EXX_OK && rc != EXX_ERR_UNSUPPORTED && rc != EXX_ERR_OOM) return rc;
+        if (rc == EXX_OK && v.ms < best.ms) best = v;
+        return EXX_OK;
+    };
+    for (int pairs : {0, 256, 512, 1024})
+        for (int block : {8, 16})
+            if (int rc = consider({pairs, block, 0, 0, -1, 0.0})) return rc;
+    if (P->prec == EXX_PREC_BF16X7) {
+        const TuneVal base = best;
+        for (auto &zc : tc3_z_choices(P->n[2]))
+            if (int rc = consider({base.pairs, base.block, zc.first, zc.second, -1, 0.0})) return rc;
+        const TuneVal base2 = best;
+        for (int st : {0, 1})
+            if (int rc = consider({base2.pairs, base2.block, base2.zwn, base2.znbuf, st, 0.0})) return rc;
+    }
+    if (best.ms >= 1e300) {
+        set_error("exx_plan_autotune: no candidate setting ran");
+        return EXX_ERR_UNSUPPORTED;
+    }
+    tune_set(*P, best);
+    if (P->prec == EXX_PREC_BF16X7)
+        if (int rc = tc3_upload(*P)) return rc;
+    if (int rc = apply_prepare(P, c, s)) return rc;
+    P->tuned = 1;
+    P->tune_ms = best.ms;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    for (auto &kv : g_tune_cache)
+        if (kv.first == key) {
+            kv.second = best;
+            return EXX_OK;
+        }
+    g_tune_cache.push_back({key, best});
+    return EXX_OK;
+}
+
+int exx_plan_get_tuning(exx_plan plan, int *settings_h, double *ms_per_pair_h, int *tuned_h)
+{
+    Plan *P = as_plan(plan);
+    if (!P || !settings_h || !ms_per_pair_h || !tuned_h) return invalid("exx_plan_get_tuning: NULL argument");
+    settings_h[0] = P->pairs_per_batch;
+    settings_h[1] = P->block_orbitals;
+    settings_h[2] = P->t3_zwn;
+    settings_h[3] = P->t3_znbuf;
+    settings_h[4] = P->t3_stage;
+    *ms_per_pair_h = P->tune_ms;
+    *tuned_h = P->tuned;
+    return EXX_OK;
 }
 
 int exx_energy(exx_plan plan, const double *Psi_occ, int n_occ, long ld, const double *f, const double *VxPsi,

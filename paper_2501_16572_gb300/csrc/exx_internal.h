@@ -158,6 +158,12 @@ struct Plan {
     DevBuf t3img[3][2];
     DevBuf F32n;
     int t3_share01 = 0;             // x and y have the same length and bc: one image serves both
+    int t3_zwn = 0, t3_znbuf = 0;   // pass B matrix block width and buffers (0 = automatic)
+    int t3_stage = -1;              // slice-pass input staging (-1 = automatic)
+    int tuned = 0;                  // 1 = measured by exx_plan_autotune, 2 = taken from its cache
+    double tune_ms = 0.0;           // the chosen setting's trial time per pair solve
+    // original (non-batched) formalism: eigenvectors, f(Lambda) in the natural layout, workspace
+    DevBuf orig_V, F64n, orig_ws;
     // workspace
     DevBuf work[3];                 // batch buffers (fields x N)
     DevBuf pairs_d, blocks_d;       // schedule on the device
@@ -198,10 +204,14 @@ int tc_accumulate(Plan &P, const Block *blocks_d, int nblocks, const float *V, c
 int tc_finalize(Plan &P, int n_in, double *out, long ld_out, cudaStream_t s);
 int tc_check_error(Plan &P, cudaStream_t s);
 bool tc_is_hilo(int prec);
+// original Kronecker formalism, one pair at a time (exx_original.cu)
+int original_apply(Plan &P, const double *psi_occ, int n_occ, long ld_occ, const double *f, const double *psi_in,
+                   int n_in, long ld_in, double *out, long ld_out, bool aliased, cudaStream_t s);
 // three-pass split path (exx_tc3.cu)
 bool tc3_supported(const Plan &P, std::string *why);
 int tc3_upload(Plan &P);
 int tc3_solve_batch(Plan &P, const int2 *pairs_d, int nfields, float *bufA, float *bufB, cudaStream_t s);
+std::vector<std::pair<int, int>> tc3_z_choices(int n3);
 int tc_unit_gemm(int tf32, int n, int k, const float *A, const float *B, float *D, int *err);
 int tc_wait_timeout_probe(int *status_h);
 

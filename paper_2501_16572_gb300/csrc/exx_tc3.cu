@@ -895,6 +895,7 @@ SliceLayout slice_layout(const Plan &P, bool pair = true)
     // so the buffer is used only where it does not cost that second CTA
     const size_t two_per_sm = 233472 / 2 - 1024;
     L.stage = (R % 4 == 0 && with_stage <= kSmemLimit && (with_stage <= two_per_sm || off > two_per_sm)) ? 1 : 0;
+    if (P.t3_stage >= 0) L.stage = (P.t3_stage && R % 4 == 0 && with_stage <= kSmemLimit) ? 1 : 0;   // tuned
     L.smem = L.stage ? with_stage : off;
     L.tmem_cols = tmem_pow2(2 * std::max(Kp1, Kp2));
     return L;
@@ -912,7 +913,7 @@ constexpr int kTPRs = 4;
 // Matrix blocks: all 2 NB resident when they fit; else streamed through 2 (or 3) buffers,
 // the fewest blocks (widest N) that fit first (measured: wider blocks with two buffers beat
 // narrower ones with three).
-bool z_layout(int n3, ZLayout &L)
+bool z_layout(int n3, ZLayout &L, int want_wn = 0, int want_nbuf = 0)
 {
     const int Kp = pad16i(n3);
     const size_t abytes = 3 * size_t(kRows) * Kp * 2;
@@ -923,6 +924,7 @@ bool z_layout(int n3, ZLayout &L)
             const size_t blk = mat_image_bytes(WN, Kp);
             const int nbuf = pass == 0 ? 2 * NB : (pass == 1 ? 2 : 3);
             if (pass > 0 && nbuf >= 2 * NB) continue;
+            if (want_wn && (WN != want_wn || nbuf != want_nbuf)) continue;   // a tuned choice
             size_t off = align_up(abytes, 1024);
             const uint32_t offB = uint32_t(off);
             off += size_t(nbuf) * blk;
@@ -942,6 +944,27 @@ bool z_layout(int n3, ZLayout &L)
     }
     return false;
 }
+
+}  // namespace
+
+// The (block width, buffers) choices of pass B that fit for an axis of n3 points.
+std::vector<std::pair<int, int>> tc3_z_choices(int n3)
+{
+    std::vector<std::pair<int, int>> out;
+    for (int NB = 1; NB <= 16; ++NB) {
+        const int WN = pad16i((n3 + NB - 1) / NB);
+        for (int nbuf : {2 * NB, 2, 3}) {
+            ZLayout L;
+            if (z_layout(n3, L, WN, nbuf)) {
+                std::pair<int, int> c{WN, L.nbuf};
+                if (std::find(out.begin(), out.end(), c) == out.end()) out.push_back(c);
+            }
+        }
+    }
+    return out;
+}
+
+namespace {
 
 // Units of 4 grid points per thread and row in pass B, from a few compiled widths.
 int z_upt(int n3)
@@ -1021,7 +1044,7 @@ int tc3_upload(Plan &P)
     }
     // z: NB blocks of WN outputs each
     ZLayout Z;
-    z_layout(P.n[2], Z);
+    if (!z_layout(P.n[2], Z, P.t3_zwn, P.t3_znbuf)) z_layout(P.n[2], Z);
     {
         const int nd = P.n[2], Kp = pad16i(nd);
         const std::vector<double> &V = P.V[2];
@@ -1110,7 +1133,7 @@ int tc3_solve_batch(Plan &P, const int2 *pairs_d, int nfields, float *bufA, floa
     // pass B
     {
         ZLayout Z;
-        z_layout(n3, Z);
+        if (!z_layout(n3, Z, P.t3_zwn, P.t3_znbuf)) z_layout(n3, Z);
         ZArgs a{};
         a.R = n1 * n2;
         a.tpfz = (a.R + kRows - 1) / kRows;
