@@ -176,62 +176,9 @@ gemm_rows_kernel(long M, int Nc, int K, const double *A, long lda, const double 
         }
 }
 
-// One CTA: A = -(M + M^T)/2 (lower part), right-looking Cholesky A = L L^T in place,
-// then Linv = L^{-1} (lower).  info_d[0] = 0 or 1 + failing pivot.
 constexpr int kCholThreads = 1024;
-__global__ void __launch_bounds__(kCholThreads)
-cholesky_inverse_kernel(int n, const double *M, double *L, double *Linv, int *info_d)
-{
-    __shared__ int failed;
-    const int tid = threadIdx.x;
-    for (long e = tid; e < long(n) * n; e += blockDim.x) {
-        int i = int(e % n), j = int(e / n);
-        L[e] = (i >= j) ? -0.5 * (M[i + size_t(n) * j] + M[j + size_t(n) * i]) : 0.0;
-        Linv[e] = 0.0;
-    }
-    if (tid == 0) {
-        failed = 0;
-        info_d[0] = 0;
-    }
-    __syncthreads();
-    for (int j = 0; j < n; ++j) {
-        if (tid == 0) {
-            double d = L[j + size_t(n) * j];
-            if (!(d > 0.0)) {
-                failed = 1;
-                info_d[0] = j + 1;
-            } else {
-                L[j + size_t(n) * j] = sqrt(d);
-            }
-        }
-        __syncthreads();
-        if (failed) return;
-        const double djj = L[j + size_t(n) * j];
-        for (int i = j + 1 + tid; i < n; i += blockDim.x) L[i + size_t(n) * j] /= djj;
-        __syncthreads();
-        // trailing update of the lower triangle, columns k in (j, n), rows i >= k
-        const int m = n - j - 1;
-        for (long e = tid; e < long(m) * m; e += blockDim.x) {
-            int ii = int(e % m), kk = int(e / m);
-            if (ii < kk) continue;
-            int i = j + 1 + ii, k = j + 1 + kk;
-            L[i + size_t(n) * k] -= L[i + size_t(n) * j] * L[k + size_t(n) * j];
-        }
-        __syncthreads();
-    }
-    // Linv: row by row, X(i, c) = (delta_ic - sum_{k=c}^{i-1} L(i,k) X(k,c)) / L(i,i), c <= i
-    for (int i = 0; i < n; ++i) {
-        const double lii = L[i + size_t(n) * i];
-        for (int c = tid; c <= i; c += blockDim.x) {
-            double s = (c == i) ? 1.0 : 0.0;
-            for (int k = c; k < i; ++k) s -= L[i + size_t(n) * k] * Linv[k + size_t(n) * c];
-            Linv[i + size_t(n) * c] = s / lii;
-        }
-        __syncthreads();
-    }
-}
 
-// The same for n <= kCholSmemMax with everything in shared memory (column-major n x n):
+// n <= kCholSmemMax: one CTA with everything in shared memory (column-major n x n):
 // right-looking Cholesky (column j: pivot, scale, rank-1 update of the trailing lower
 // triangle), then the inverse in place, columns from the right (unblocked triangular
 // inverse): X_jj = 1 / L_jj and X(j+1:, j) = -X_jj X(j+1:, j+1:) L(j+1:, j), the
@@ -300,6 +247,249 @@ cholesky_inverse_smem_kernel(int n, const double *M, double *Linv, int *info_d)
     for (int e = tid; e < n * n; e += blockDim.x) {
         const int i = e % n, j = e / n;
         Linv[e] = (i >= j) ? S[e] : 0.0;
+    }
+}
+
+// ---- blocked Cholesky and triangular inverse for n > kCholSmemMax (many CTAs) -----------
+// A = -(M + M^T)/2 is factored in place, right-looking, in column blocks of kCb:
+//   diagonal block: A_kk = L_kk L_kk^T and D_k = L_kk^{-1} (one CTA, shared memory);
+//   panel:          L_ik = A_ik D_k^T for the row blocks i > k (a CTA per row block);
+//   trailing:       A_ij -= L_ik L_jk^T for i >= j > k (a CTA per lower 64 x 64 tile).
+// Then X = L^{-1} block row by block row: X_ii = D_i (written with the factorisation),
+// X_ij = -D_i sum_{k=j}^{i-1} L_ik X_kj (a CTA per block j < i).
+// A failed pivot sets info_d[0] = 1 + its index; every later kernel then returns at once.
+constexpr int kCb = 64;
+
+__global__ void chol_prep_kernel(int n, const double *M, double *A, double *X, int *info_d)
+{
+    for (long e = long(blockIdx.x) * blockDim.x + threadIdx.x; e < long(n) * n; e += long(gridDim.x) * blockDim.x) {
+        const int i = int(e % n), j = int(e / n);
+        A[e] = (i >= j) ? -0.5 * (M[i + size_t(n) * j] + M[j + size_t(n) * i]) : 0.0;
+        X[e] = 0.0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) info_d[0] = 0;
+}
+
+// One CTA: the diagonal block at (k0, k0) of size b <= kCb: factor, write L_kk into A and
+// D = L_kk^{-1} (lower, b x b, leading dimension kCb) into Dk and into X's diagonal block.
+__global__ void __launch_bounds__(kCholThreads) chol_diag_kernel(int n, double *A, int k0, int b, double *Dk,
+                                                                 double *X, int *info_d)
+{
+    __shared__ double S[kCb * kCb];
+    __shared__ double y[kCb];
+    __shared__ int failed;
+    const int tid = threadIdx.x;
+    if (tid == 0) failed = info_d[0] != 0;
+    __syncthreads();
+    if (failed) return;
+    for (int e = tid; e < b * b; e += blockDim.x) {
+        const int i = e % b, j = e / b;
+        S[i + kCb * j] = (i >= j) ? A[(k0 + i) + size_t(n) * (k0 + j)] : 0.0;
+    }
+    __syncthreads();
+    for (int j = 0; j < b; ++j) {
+        if (tid == 0) {
+            const double d = S[j + kCb * j];
+            if (!(d > 0.0)) {
+                failed = 1;
+                info_d[0] = k0 + j + 1;
+            } else {
+                S[j + kCb * j] = sqrt(d);
+            }
+        }
+        __syncthreads();
+        if (failed) return;
+        const double djj = S[j + kCb * j];
+        for (int i = j + 1 + tid; i < b; i += blockDim.x) S[i + kCb * j] /= djj;
+        __syncthreads();
+        for (int k = j + 1 + (tid >> 5); k < b; k += blockDim.x >> 5) {
+            const double lk = S[k + kCb * j];
+            for (int i = k + (tid & 31); i < b; i += 32) S[i + kCb * k] -= S[i + kCb * j] * lk;
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < b * b; e += blockDim.x) {
+        const int i = e % b, j = e / b;
+        if (i >= j) A[(k0 + i) + size_t(n) * (k0 + j)] = S[i + kCb * j];
+    }
+    __syncthreads();
+    // in-place inverse of the b x b lower triangle, columns from the right
+    for (int j = b - 1; j >= 0; --j) {
+        const double xjj = 1.0 / S[j + kCb * j];
+        for (int i = j + 1 + tid; i < b; i += blockDim.x) {
+            double acc = 0.0;
+            for (int k = j + 1; k <= i; ++k) acc = fma(S[i + kCb * k], S[k + kCb * j], acc);
+            y[i] = acc;
+        }
+        __syncthreads();
+        for (int i = j + 1 + tid; i < b; i += blockDim.x) S[i + kCb * j] = -xjj * y[i];
+        if (tid == 0) S[j + kCb * j] = xjj;
+        __syncthreads();
+    }
+    for (int e = tid; e < kCb * kCb; e += blockDim.x) {
+        const int i = e % kCb, j = e / kCb;
+        const double v = (i < b && j < b && i >= j) ? S[i + kCb * j] : 0.0;
+        Dk[e] = v;
+        if (i < b && j < b) X[(k0 + i) + size_t(n) * (k0 + j)] = v;
+    }
+}
+
+// C (rows r0.., columns c0.., 64 x 64 tile, leading dimension n) op= sum_t P(r, t) Q(c, t),
+// P(r, t) = Pm[r + ldp t], Q(c, t) = Qm[c + ldq t], t < K; mode 0: C = alpha acc; 1: C += alpha acc.
+__device__ __forceinline__ void tile_gemm_nt(int rows, int cols, int K, const double *Pm, long ldp, const double *Qm,
+                                             long ldq, double alpha, double *C, long ldc, int mode)
+{
+    __shared__ double Ps[kKt][kTile + 1];
+    __shared__ double Qs[kKt][kTile + 1];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    double acc[4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += kKt) {
+        for (int t = threadIdx.x; t < kKt * kTile; t += kGemmThreads) {
+            const int rr = t % kTile, kk = t / kTile;
+            Ps[kk][rr] = (rr < rows && k0 + kk < K) ? Pm[rr + ldp * (k0 + kk)] : 0.0;
+            Qs[kk][rr] = (rr < cols && k0 + kk < K) ? Qm[rr + ldq * (k0 + kk)] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < kKt; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] = Ps[kk][tx + 16 * u];
+                b[u] = Qs[kk][ty + 16 * u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int w = 0; w < 4; ++w) acc[u][w] = fma(a[u], b[w], acc[u][w]);
+        }
+        __syncthreads();
+    }
+    for (int u = 0; u < 4; ++u)
+        for (int w = 0; w < 4; ++w) {
+            const int r = tx + 16 * u, c = ty + 16 * w;
+            if (r < rows && c < cols) {
+                double *o = C + r + ldc * c;
+                *o = mode ? *o + alpha * acc[u][w] : alpha * acc[u][w];
+            }
+        }
+}
+
+// panel: row block i = k0/kCb + 1 + blockIdx.x, L_ik = A_ik D_k^T (into a scratch copy first:
+// the tile reads A_ik while writing it)
+__global__ void __launch_bounds__(kGemmThreads) chol_panel_kernel(int n, double *A, int k0, int b, const double *Dk,
+                                                                  double *scratch, const int *info_d)
+{
+    if (info_d[0]) return;
+    const int r0 = k0 + b + blockIdx.x * kCb;
+    const int rows = min(kCb, n - r0);
+    double *tmp = scratch + size_t(blockIdx.x) * kCb * kCb;
+    // tmp(r, c) = sum_t A(r0 + r, k0 + t) D(c, t)
+    tile_gemm_nt(rows, b, b, A + r0 + size_t(n) * k0, n, Dk, kCb, 1.0, tmp, kCb, 0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kCb * kCb; e += blockDim.x) {
+        const int r = e % kCb, c = e / kCb;
+        if (r < rows && c < b) A[(r0 + r) + size_t(n) * (k0 + c)] = tmp[r + kCb * c];
+    }
+}
+
+// trailing update of the lower triangle: tile (bi, bj), bi >= bj, of the part past k0 + b
+__global__ void __launch_bounds__(kGemmThreads) chol_update_kernel(int n, double *A, int k0, int b, const int *info_d)
+{
+    if (info_d[0]) return;
+    const int bi = blockIdx.x, bj = blockIdx.y;
+    if (bi < bj) return;
+    const int base = k0 + b;
+    const int r0 = base + bi * kCb, c0 = base + bj * kCb;
+    const int rows = min(kCb, n - r0), cols = min(kCb, n - c0);
+    // A(r, c) -= sum_t L(r, k0 + t) L(c, k0 + t)   (the strict upper part of a diagonal tile
+    // is updated too; it is never read and is cleared at the end)
+    tile_gemm_nt(rows, cols, b, A + r0 + size_t(n) * k0, n, A + c0 + size_t(n) * k0, n, -1.0,
+                 A + r0 + size_t(n) * c0, n, 1);
+}
+
+// block row i of X = L^{-1}: for bj < i (blockIdx.x): T = sum_{k=bj}^{i-1} L_ik X_kj, X_ij = -D_i T
+__global__ void __launch_bounds__(kGemmThreads) chol_inv_row_kernel(int n, const double *A, double *X, int bi,
+                                                                    const double *Dall, double *scratch,
+                                                                    const int *info_d)
+{
+    if (info_d[0]) return;
+    const int bj = blockIdx.x;
+    const int r0 = bi * kCb, c0 = bj * kCb;
+    const int rows = min(kCb, n - r0), cols = min(kCb, n - c0);
+    double *T = scratch + size_t(blockIdx.x) * kCb * kCb;
+    // T(r, c) = sum_{t = c0 .. r0-1} L(r0 + r, t) X(t, c0 + c): P = L rows, Q(c, t) = X(t, c0 + c)
+    // (Q given transposed: Q(c, t) = Xm[c + ldq t] needs X^T; use the rows form instead)
+    const int K = r0 - c0;
+    {
+        __shared__ double Ps[kKt][kTile + 1];
+        __shared__ double Qs[kKt][kTile + 1];
+        const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+        double acc[4][4] = {};
+        for (int k = 0; k < K; k += kKt) {
+            for (int t = threadIdx.x; t < kKt * kTile; t += kGemmThreads) {
+                const int rr = t % kTile, kk = t / kTile;
+                const int tt = c0 + k + kk;
+                Ps[kk][rr] = (rr < rows && k + kk < K) ? A[(r0 + rr) + size_t(n) * tt] : 0.0;
+                Qs[kk][rr] = (rr < cols && k + kk < K) ? X[tt + size_t(n) * (c0 + rr)] : 0.0;
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int kk = 0; kk < kKt; ++kk) {
+                double a[4], b[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    a[u] = Ps[kk][tx + 16 * u];
+                    b[u] = Qs[kk][ty + 16 * u];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) acc[u][w] = fma(a[u], b[w], acc[u][w]);
+            }
+            __syncthreads();
+        }
+        for (int u = 0; u < 4; ++u)
+            for (int w = 0; w < 4; ++w) {
+                const int r = tx + 16 * u, c = ty + 16 * w;
+                T[r + kCb * c] = (r < rows && c < cols) ? acc[u][w] : 0.0;
+            }
+    }
+    __syncthreads();
+    // X_ij(r, c) = -sum_t D_i(r, t) T(t, c): P = D_i (rows r), Q(c, t) = T(t, c) -> T^T
+    const double *Di = Dall + size_t(bi) * kCb * kCb;
+    {
+        __shared__ double Ps[kKt][kTile + 1];
+        __shared__ double Qs[kKt][kTile + 1];
+        const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+        double acc[4][4] = {};
+        for (int k = 0; k < rows; k += kKt) {
+            for (int t = threadIdx.x; t < kKt * kTile; t += kGemmThreads) {
+                const int rr = t % kTile, kk = t / kTile;
+                Ps[kk][rr] = (k + kk < rows) ? Di[rr + kCb * (k + kk)] : 0.0;
+                Qs[kk][rr] = (k + kk < rows) ? T[(k + kk) + kCb * rr] : 0.0;
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int kk = 0; kk < kKt; ++kk) {
+                double a[4], b[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    a[u] = Ps[kk][tx + 16 * u];
+                    b[u] = Qs[kk][ty + 16 * u];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) acc[u][w] = fma(a[u], b[w], acc[u][w]);
+            }
+            __syncthreads();
+        }
+        for (int u = 0; u < 4; ++u)
+            for (int w = 0; w < 4; ++w) {
+                const int r = tx + 16 * u, c = ty + 16 * w;
+                if (r < rows && c < cols) X[(r0 + r) + size_t(n) * (c0 + c)] = -acc[u][w];
+            }
     }
 }
 
@@ -377,9 +567,6 @@ int gemm_fp64_nn(Plan &P, int M, int Nc, int K, const double *A, long lda, const
 int cholesky_neg_sym_and_inverse(Plan &P, int n, const double *M, double *Linv, int *info_d,
                                  cudaStream_t s)
 {
-    if (n > kCholSmemMax) {
-        if (int rc = dev_reserve(P.small_ws, size_t(n) * n * sizeof(double))) return rc;
-    }
     int tb = timing_begin(P, EXX_TIMING_CHOL, s);
     if (n <= kCholSmemMax) {
         const size_t smem = (size_t(n) * n + n) * sizeof(double);
@@ -388,13 +575,39 @@ int cholesky_neg_sym_and_inverse(Plan &P, int n, const double *M, double *Linv, 
         cholesky_inverse_smem_kernel<<<1, kCholThreads, smem, s>>>(n, M, Linv, info_d);
         timing_end(P, tb, s);
         EXX_LAUNCH("cholesky_inverse_smem_kernel");
-    } else {
-        double *L = static_cast<double *>(P.small_ws.p);
-        cholesky_inverse_kernel<<<1, kCholThreads, 0, s>>>(n, M, L, Linv, info_d);
-        timing_end(P, tb, s);
-        EXX_LAUNCH("cholesky_inverse_kernel");
+        P.launches++;
+        return EXX_OK;
     }
+    // workspace: A (n x n), the diagonal-block inverses (nbk blocks of kCb^2), tile scratch
+    const int nbk = (n + kCb - 1) / kCb;
+    const size_t nn = size_t(n) * n, blk = size_t(kCb) * kCb;
+    if (int rc = dev_reserve(P.small_ws, (nn + 2 * size_t(nbk) * blk) * sizeof(double))) return rc;
+    double *A = static_cast<double *>(P.small_ws.p);
+    double *Dall = A + nn;
+    double *scratch = Dall + size_t(nbk) * blk;
+    const int eg = std::min(4 * P.num_sms, int((nn + 255) / 256));
+    chol_prep_kernel<<<eg, 256, 0, s>>>(n, M, A, Linv, info_d);
+    EXX_LAUNCH("chol_prep_kernel");
     P.launches++;
+    for (int kb = 0; kb < nbk; ++kb) {
+        const int k0 = kb * kCb, b = std::min(kCb, n - k0);
+        chol_diag_kernel<<<1, kCholThreads, 0, s>>>(n, A, k0, b, Dall + size_t(kb) * blk, Linv, info_d);
+        EXX_LAUNCH("chol_diag_kernel");
+        P.launches++;
+        const int rest = nbk - kb - 1;
+        if (rest == 0) break;
+        chol_panel_kernel<<<rest, kGemmThreads, 0, s>>>(n, A, k0, b, Dall + size_t(kb) * blk, scratch, info_d);
+        EXX_LAUNCH("chol_panel_kernel");
+        chol_update_kernel<<<dim3(rest, rest), kGemmThreads, 0, s>>>(n, A, k0, b, info_d);
+        EXX_LAUNCH("chol_update_kernel");
+        P.launches += 2;
+    }
+    for (int bi = 1; bi < nbk; ++bi) {
+        chol_inv_row_kernel<<<bi, kGemmThreads, 0, s>>>(n, A, Linv, bi, Dall, scratch, info_d);
+        EXX_LAUNCH("chol_inv_row_kernel");
+        P.launches++;
+    }
+    timing_end(P, tb, s);
     return EXX_OK;
 }
 
