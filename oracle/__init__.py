@@ -58,6 +58,23 @@ def lib():
                                     ctypes.c_int, _D]
         L.exo_energy.argtypes = [ctypes.c_void_p, _D, ctypes.c_int, _D, _D, ctypes.c_long]
         L.exo_energy.restype = ctypes.c_double
+        L.exo_bloch_operator_1d.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_double, _D]
+        L.exo_hermitian_eigh.argtypes = [ctypes.c_int, _D, _D, _D]
+        L.exo_cplan_new.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _I, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_double, _D]
+        L.exo_cplan_new.restype = ctypes.c_void_p
+        L.exo_cplan_free.argtypes = [ctypes.c_void_p]
+        for nm in ("exo_cplan_eigvecs", "exo_cplan_eigvals"):
+            getattr(L, nm).argtypes = [ctypes.c_void_p, ctypes.c_int]
+            getattr(L, nm).restype = _D
+        L.exo_cplan_F.argtypes = [ctypes.c_void_p]
+        L.exo_cplan_F.restype = _D
+        L.exo_csolve.argtypes = [ctypes.c_void_p, _D, _D]
+        L.exo_cexx_apply.argtypes = [ctypes.c_void_p, _D, ctypes.c_int, _D, _D, ctypes.c_int, _I, ctypes.c_int, _D]
+        L.exo_cenergy.argtypes = [ctypes.c_void_p, _D, ctypes.c_int, _D, _D]
+        L.exo_cenergy.restype = ctypes.c_double
+        L.exo_cace.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _D, _D, _D, _D, _D]
         L.exo_energy_pairs.argtypes = [ctypes.c_void_p, _D, ctypes.c_int, _D]
         L.exo_energy_pairs.restype = ctypes.c_double
         L.exo_ace.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _D, _D, _D, _D, _D]
@@ -213,3 +230,101 @@ def ace_apply(xi, phi, dV):
     out = np.zeros_like(phi)
     lib().exo_ace_apply(N, n, float(dV), _p(xi), _p(phi), phi.shape[0], _p(out))
     return out
+
+
+# ---- complex (Bloch) path -----------------------------------------------------------------
+
+def _cz(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def _pz(a):
+    return a.ctypes.data_as(_D)
+
+
+def bloch_operator_1d(n, h, bc, p, theta) -> np.ndarray:
+    D = np.zeros((n, n), dtype=np.complex128, order="F")
+    if lib().exo_bloch_operator_1d(n, float(h), int(bc), int(p), float(theta), _pz(D)):
+        raise ValueError("bad operator arguments")
+    return D
+
+
+def hermitian_eigh(A):
+    A = np.asfortranarray(A, dtype=np.complex128)
+    n = A.shape[0]
+    V = np.zeros((n, n), dtype=np.complex128, order="F")
+    lam = np.zeros(n)
+    if lib().exo_hermitian_eigh(n, _pz(A), _pz(V), _p(lam)):
+        raise MemoryError
+    return lam, V
+
+
+class CPlan:
+    """Oracle plan of the Bloch problem: theta[d] = phase across one period of axis d."""
+
+    def __init__(self, n, h, bc, fd_order=12, kernel=0, omega=0.0, theta=(0.0, 0.0, 0.0)):
+        self.n = tuple(int(v) for v in n)
+        self.N = self.n[0] * self.n[1] * self.n[2]
+        self.h = float(h)
+        self.dV = self.h ** 3
+        bca = (ctypes.c_int * 3)(*[int(b) for b in bc])
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        self._p = lib().exo_cplan_new(self.n[0], self.n[1], self.n[2], self.h, bca, int(fd_order), int(kernel),
+                                      float(omega), _p(th))
+        if not self._p:
+            raise ValueError("oracle Bloch plan creation failed")
+
+    def __del__(self):
+        if getattr(self, "_p", None) and _lib is not None:
+            _lib.exo_cplan_free(self._p)
+            self._p = None
+
+    def eigvals(self, d):
+        return np.ctypeslib.as_array(lib().exo_cplan_eigvals(self._p, d), shape=(self.n[d],)).copy()
+
+    def eigvecs(self, d):
+        nd = self.n[d]
+        raw = np.ctypeslib.as_array(lib().exo_cplan_eigvecs(self._p, d), shape=(2 * nd * nd,)).copy()
+        return raw.view(np.complex128).reshape(nd, nd, order="F")
+
+    def F(self):
+        return np.ctypeslib.as_array(lib().exo_cplan_F(self._p), shape=(self.N,)).copy()
+
+    def solve(self, rho):
+        rho = _cz(rho).reshape(-1)
+        out = np.zeros(self.N, dtype=np.complex128)
+        if lib().exo_csolve(self._p, _pz(rho), _pz(out)):
+            raise MemoryError
+        return out
+
+    def exx_apply(self, psi_occ, f, psi_in, cols=None):
+        psi_occ, psi_in, f = _cz(psi_occ), _cz(psi_in), _c64(f)
+        n_occ, n_in = psi_occ.shape[0], psi_in.shape[0]
+        if cols is None:
+            out = np.zeros((n_in, self.N), dtype=np.complex128)
+            rc = lib().exo_cexx_apply(self._p, _pz(psi_occ), n_occ, _p(f), _pz(psi_in), n_in, None, n_in, _pz(out))
+        else:
+            ci = np.ascontiguousarray(cols, dtype=np.int32)
+            out = np.zeros((ci.size, self.N), dtype=np.complex128)
+            rc = lib().exo_cexx_apply(self._p, _pz(psi_occ), n_occ, _p(f), _pz(psi_in), n_in,
+                                      ci.ctypes.data_as(_I), ci.size, _pz(out))
+        if rc:
+            raise RuntimeError(f"oracle complex exx_apply failed ({rc})")
+        return out
+
+    def energy(self, psi, f, vx):
+        psi, vx, f = _cz(psi), _cz(vx), _c64(f)
+        return float(lib().exo_cenergy(self._p, _pz(psi), psi.shape[0], _p(f), _pz(vx)))
+
+
+def cace(psi, W, dV):
+    """Complex ACE: (M, L, xi) with M = dV Psi^H W, -(M + M^H)/2 = L L^H, xi = W L^{-H}."""
+    psi, W = _cz(psi), _cz(W)
+    n, N = psi.shape
+    M = np.zeros(n * n, dtype=np.complex128)
+    L = np.zeros(n * n, dtype=np.complex128)
+    xi = np.zeros((n, N), dtype=np.complex128)
+    rc = lib().exo_cace(N, n, float(dV), _pz(psi), _pz(W), _pz(M), _pz(L), _pz(xi))
+    if rc:
+        raise ValueError(f"not positive definite at pivot {rc - 1}")
+    return M.reshape(n, n, order="F"), L.reshape(n, n, order="F"), xi

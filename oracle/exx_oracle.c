@@ -505,3 +505,319 @@ int exo_ace_apply(int N, int n, double dV, const double *xi, const double *Phi, 
     free(chi);
     return 0;
 }
+
+/* ===========================================================================
+ * Complex (Bloch) path: Eq. 1 with Brillouin-zone wavevectors.  The pair problem of
+ * Eq. 2 / Eq. 3 for rho = conj(psi_{mq}) phi_{nk} is solved with Bloch boundary
+ * conditions at k - q along the extended axes (Sec. II, below Eq. 3): a grid function
+ * u on an axis of n points with Bloch phase theta (radians across one period) obeys
+ * u(j + n) = exp(i theta) u(j).  Dirichlet axes are unchanged.  Complex arrays are
+ * interleaved (re, im) doubles; orbital blocks are N x n complex, column-major.
+ * Readings (design notes): the library takes theta_d = (k - q)_d L_d per periodic axis;
+ * occupations and Brillouin-zone weights enter only through the weights f given per
+ * occupied orbital; E_x = 1/4 sum_n f_n dV Re <psi_n, Vx psi_n>; ACE: M = dV Psi^H W,
+ * -(M + M^H)/2 = L L^H, xi = W L^{-H}.
+ */
+#include <complex.h>
+
+/* 1D second-derivative operator with Bloch phase theta (n x n complex, column-major,
+ * interleaved): D(i, (i + k) mod n) += w_|k| exp(i theta floor((i + k) / n)) / h^2 for
+ * |k| <= p.  bc = 0 (Dirichlet) gives the real truncated operator, theta ignored. */
+int exo_bloch_operator_1d(int n, double h, int bc, int p, double theta, double *Dout)
+{
+    double w[32];
+    if (n < 1 || exo_fd_weights(p, w)) return -1;
+    double complex *D = (double complex *)Dout;
+    for (size_t e = 0; e < (size_t)n * n; ++e) D[e] = 0.0;
+    const double ih2 = 1.0 / (h * h);
+    for (int i = 0; i < n; ++i)
+        for (int k = -p; k <= p; ++k) {
+            const double wk = w[k < 0 ? -k : k] * ih2;
+            const int j = i + k;
+            if (bc != 1) {
+                if (j >= 0 && j < n) D[i + (size_t)n * j] += wk;
+                continue;
+            }
+            const int wraps = (j >= 0) ? j / n : -((-j + n - 1) / n);   /* floor(j / n) */
+            const int jj = j - wraps * n;
+            D[i + (size_t)n * jj] += wk * cexp(I * theta * wraps);
+        }
+    return 0;
+}
+
+/* Cyclic Jacobi for a Hermitian n x n matrix: A = V diag(lam) V^H, eigenvalues ascending.
+ * Each step first turns A(p, q) real by the phase of column q (A <- D^H A D,
+ * V <- V D, D = diag(1, ..., exp(-i phi), ...)), then applies the real Jacobi rotation
+ * of the (p, q) plane. */
+int exo_hermitian_eigh(int n, const double *Ain, double *Vout, double *lam)
+{
+    double complex *A = (double complex *)malloc(sizeof(double complex) * (size_t)n * n);
+    double complex *V = (double complex *)Vout;
+    if (!A) return -1;
+    memcpy(A, Ain, sizeof(double complex) * (size_t)n * n);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) V[i + (size_t)n * j] = (i == j) ? 1.0 : 0.0;
+    double fro = 0.0;
+    for (size_t e = 0; e < (size_t)n * n; ++e) fro += creal(A[e] * conj(A[e]));
+    fro = sqrt(fro);
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int q = 1; q < n; ++q)
+            for (int pp = 0; pp < q; ++pp) off += creal(A[pp + (size_t)n * q] * conj(A[pp + (size_t)n * q]));
+        if (sqrt(2.0 * off) <= 1e-17 * fro) break;
+        for (int pp = 0; pp < n - 1; ++pp)
+            for (int q = pp + 1; q < n; ++q) {
+                const double complex apq = A[pp + (size_t)n * q];
+                const double mag = cabs(apq);
+                if (mag == 0.0) continue;
+                const double complex ph = conj(apq) / mag;      /* exp(-i phi) */
+                for (int k = 0; k < n; ++k) A[k + (size_t)n * q] *= ph;          /* column q */
+                for (int k = 0; k < n; ++k) A[q + (size_t)n * k] *= conj(ph);    /* row q */
+                for (int k = 0; k < n; ++k) V[k + (size_t)n * q] *= ph;
+                A[pp + (size_t)n * q] = mag;
+                A[q + (size_t)n * pp] = mag;
+                const double app = creal(A[pp + (size_t)n * pp]), aqq = creal(A[q + (size_t)n * q]);
+                const double th = (aqq - app) / (2.0 * mag);
+                const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; ++k) {
+                    const double complex akp = A[k + (size_t)n * pp], akq = A[k + (size_t)n * q];
+                    A[k + (size_t)n * pp] = c * akp - s * akq;
+                    A[k + (size_t)n * q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double complex apk = A[pp + (size_t)n * k], aqk = A[q + (size_t)n * k];
+                    A[pp + (size_t)n * k] = c * apk - s * aqk;
+                    A[q + (size_t)n * k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double complex vkp = V[k + (size_t)n * pp], vkq = V[k + (size_t)n * q];
+                    V[k + (size_t)n * pp] = c * vkp - s * vkq;
+                    V[k + (size_t)n * q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    for (int i = 0; i < n; ++i) lam[i] = creal(A[i + (size_t)n * i]);
+    for (int i = 0; i < n; ++i) {
+        int best = i;
+        for (int j = i + 1; j < n; ++j) if (lam[j] < lam[best]) best = j;
+        if (best != i) {
+            const double tl = lam[i]; lam[i] = lam[best]; lam[best] = tl;
+            for (int k = 0; k < n; ++k) {
+                const double complex v = V[k + (size_t)n * i];
+                V[k + (size_t)n * i] = V[k + (size_t)n * best];
+                V[k + (size_t)n * best] = v;
+            }
+        }
+    }
+    free(A);
+    return 0;
+}
+
+typedef struct {
+    int n[3];
+    double h, dV;
+    double complex *V[3];
+    double *lam[3];
+    double *F;
+} exo_cplan;
+
+void exo_cplan_free(exo_cplan *P)
+{
+    if (!P) return;
+    for (int d = 0; d < 3; ++d) { free(P->V[d]); free(P->lam[d]); }
+    free(P->F);
+    free(P);
+}
+
+/* Plan of the Bloch problem: theta[d] is the phase across one period of axis d (used on
+ * periodic axes only).  Returns NULL on failure. */
+exo_cplan *exo_cplan_new(int n1, int n2, int n3, double h, const int *bc, int fd_order, int kernel,
+                         double omega, const double *theta)
+{
+    exo_cplan *P = (exo_cplan *)calloc(1, sizeof(exo_cplan));
+    if (!P) return NULL;
+    const int n[3] = {n1, n2, n3};
+    P->h = h;
+    P->dV = h * h * h;
+    for (int d = 0; d < 3; ++d) {
+        P->n[d] = n[d];
+        double *D = (double *)malloc(sizeof(double complex) * (size_t)n[d] * n[d]);
+        P->V[d] = (double complex *)malloc(sizeof(double complex) * (size_t)n[d] * n[d]);
+        P->lam[d] = (double *)malloc(sizeof(double) * n[d]);
+        if (!D || !P->V[d] || !P->lam[d] || exo_bloch_operator_1d(n[d], h, bc[d], fd_order / 2, theta[d], D) ||
+            exo_hermitian_eigh(n[d], D, (double *)P->V[d], P->lam[d])) {
+            free(D);
+            exo_cplan_free(P);
+            return NULL;
+        }
+        free(D);
+    }
+    const size_t N = (size_t)n1 * n2 * n3;
+    P->F = (double *)malloc(sizeof(double) * N);
+    if (!P->F) { exo_cplan_free(P); return NULL; }
+    for (int c = 0; c < n3; ++c)
+        for (int b = 0; b < n2; ++b)
+            for (int a = 0; a < n1; ++a)
+                P->F[a + (size_t)n1 * (b + (size_t)n2 * c)] =
+                    exo_kernel_value(P->lam[0][a] + P->lam[1][b] + P->lam[2][c], kernel, omega);
+    return P;
+}
+const double *exo_cplan_eigvecs(const exo_cplan *P, int d) { return (const double *)P->V[d]; }
+const double *exo_cplan_eigvals(const exo_cplan *P, int d) { return P->lam[d]; }
+const double *exo_cplan_F(const exo_cplan *P) { return P->F; }
+
+/* One Bloch solve X = f(L) B by Eq. 8 with its conjugates:
+ *   S_k = V1^H B_k conj(V2),  R = [vec S_1 ... vec S_n3] conj(V3),  Xt = F (.) R,
+ *   U_c = V1 Xt_c V2^T,       X = [vec U_1 ... vec U_n3] V3^T. */
+int exo_csolve(const exo_cplan *P, const double *Bin, double *Xout)
+{
+    const int n1 = P->n[0], n2 = P->n[1], n3 = P->n[2];
+    const size_t n12 = (size_t)n1 * n2, N = n12 * n3;
+    const double complex *V1 = P->V[0], *V2 = P->V[1], *V3 = P->V[2];
+    const double complex *B = (const double complex *)Bin;
+    double complex *X = (double complex *)Xout;
+    double complex *S = (double complex *)malloc(sizeof(double complex) * N);
+    double complex *R = (double complex *)malloc(sizeof(double complex) * N);
+    if (!S || !R) { free(S); free(R); return -1; }
+    #pragma omp parallel for schedule(static)
+    for (int k = 0; k < n3; ++k) {
+        double complex *T = (double complex *)malloc(sizeof(double complex) * n12);
+        const double complex *Bk = B + n12 * k;
+        for (int j = 0; j < n2; ++j)
+            for (int a = 0; a < n1; ++a) {
+                double complex s = 0.0;
+                for (int i = 0; i < n1; ++i) s += conj(V1[i + (size_t)n1 * a]) * Bk[i + (size_t)n1 * j];
+                T[a + (size_t)n1 * j] = s;
+            }
+        for (int b = 0; b < n2; ++b)
+            for (int a = 0; a < n1; ++a) {
+                double complex s = 0.0;
+                for (int j = 0; j < n2; ++j) s += T[a + (size_t)n1 * j] * conj(V2[j + (size_t)n2 * b]);
+                S[a + (size_t)n1 * b + n12 * k] = s;
+            }
+        free(T);
+    }
+    #pragma omp parallel for schedule(static)
+    for (int c = 0; c < n3; ++c) {
+        double complex *Rc = R + n12 * c;
+        for (size_t q = 0; q < n12; ++q) Rc[q] = 0.0;
+        for (int k = 0; k < n3; ++k) {
+            const double complex v = conj(V3[k + (size_t)n3 * c]);
+            const double complex *Sk = S + n12 * k;
+            for (size_t q = 0; q < n12; ++q) Rc[q] += v * Sk[q];
+        }
+        const double *Fc = P->F + n12 * c;
+        for (size_t q = 0; q < n12; ++q) Rc[q] *= Fc[q];
+    }
+    #pragma omp parallel for schedule(static)
+    for (int c = 0; c < n3; ++c) {
+        double complex *T = (double complex *)malloc(sizeof(double complex) * n12);
+        const double complex *Xc = R + n12 * c;
+        for (int b = 0; b < n2; ++b)
+            for (int i = 0; i < n1; ++i) {
+                double complex s = 0.0;
+                for (int a = 0; a < n1; ++a) s += V1[i + (size_t)n1 * a] * Xc[a + (size_t)n1 * b];
+                T[i + (size_t)n1 * b] = s;
+            }
+        for (int j = 0; j < n2; ++j)
+            for (int i = 0; i < n1; ++i) {
+                double complex s = 0.0;
+                for (int b = 0; b < n2; ++b) s += T[i + (size_t)n1 * b] * V2[j + (size_t)n2 * b];
+                S[i + (size_t)n1 * j + n12 * c] = s;
+            }
+        free(T);
+    }
+    #pragma omp parallel for schedule(static)
+    for (int k = 0; k < n3; ++k) {
+        double complex *Xk = X + n12 * k;
+        for (size_t q = 0; q < n12; ++q) Xk[q] = 0.0;
+        for (int c = 0; c < n3; ++c) {
+            const double complex v = V3[k + (size_t)n3 * c];
+            const double complex *Uc = S + n12 * c;
+            for (size_t q = 0; q < n12; ++q) Xk[q] += v * Uc[q];
+        }
+    }
+    free(S); free(R);
+    return 0;
+}
+
+/* Eq. 1 for one pair of wavevectors (q of psi_occ, k of psi_in; the plan carries k - q):
+ *   out_n(r) = - sum_{m < n_occ} f_m psi_m(r) phi_mn(r),  phi_mn = f(L_{k-q}) (conj(psi_m) psi_n),
+ * for the output columns cols[0..ncols) (all n_in when cols == NULL). */
+int exo_cexx_apply(const exo_cplan *P, const double *psi_occ, int n_occ, const double *f, const double *psi_in,
+                   int n_in, const int *cols, int ncols, double *outv)
+{
+    const size_t N = (size_t)P->n[0] * P->n[1] * P->n[2];
+    const double complex *po = (const double complex *)psi_occ, *pi = (const double complex *)psi_in;
+    double complex *out = (double complex *)outv;
+    double complex *rho = (double complex *)malloc(sizeof(double complex) * N);
+    double complex *phi = (double complex *)malloc(sizeof(double complex) * N);
+    if (!rho || !phi) { free(rho); free(phi); return -1; }
+    if (!cols) ncols = n_in;
+    for (int t = 0; t < ncols; ++t) {
+        const int n = cols ? cols[t] : t;
+        if (n < 0 || n >= n_in) { free(rho); free(phi); return -2; }
+        const double complex *pn = pi + N * (size_t)n;
+        double complex *o = out + N * (size_t)t;
+        for (size_t r = 0; r < N; ++r) o[r] = 0.0;
+        for (int m = 0; m < n_occ; ++m) {
+            const double complex *pm = po + N * (size_t)m;
+            for (size_t r = 0; r < N; ++r) rho[r] = (g_mutation == 4) ? pm[r] * pn[r] : conj(pm[r]) * pn[r];
+            if (exo_csolve(P, (const double *)rho, (double *)phi)) { free(rho); free(phi); return -1; }
+            for (size_t r = 0; r < N; ++r) o[r] -= f[m] * pm[r] * phi[r];
+        }
+    }
+    free(rho); free(phi);
+    return 0;
+}
+
+/* E = 1/4 sum_n f_n dV Re sum_r conj(psi_n(r)) vx_n(r), Neumaier-compensated. */
+double exo_cenergy(const exo_cplan *P, const double *psi, int n, const double *f, const double *vx)
+{
+    const size_t N = (size_t)P->n[0] * P->n[1] * P->n[2];
+    const double complex *ps = (const double complex *)psi, *v = (const double complex *)vx;
+    exo_ksum acc = {0.0, 0.0};
+    for (int j = 0; j < n; ++j) {
+        exo_ksum dot = {0.0, 0.0};
+        for (size_t r = 0; r < N; ++r) ks_add(&dot, creal(conj(ps[N * j + r]) * v[N * j + r]));
+        ks_add(&acc, 0.25 * f[j] * P->dV * (dot.s + dot.c));
+    }
+    return acc.s + acc.c;
+}
+
+/* Complex ACE: M = dV Psi^H W, -(M + M^H)/2 = L L^H (plain Cholesky, column by column),
+ * xi = W L^{-H} (row by row forward substitution).  Returns 0 or 1 + failing pivot. */
+int exo_cace(int N, int n, double dV, const double *Psiv, const double *Wv, double *Mv, double *Lv, double *xiv)
+{
+    const double complex *Psi = (const double complex *)Psiv, *W = (const double complex *)Wv;
+    double complex *M = (double complex *)Mv, *L = (double complex *)Lv, *xi = (double complex *)xiv;
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+            double complex s = 0.0;
+            for (int r = 0; r < N; ++r) s += conj(Psi[(size_t)N * i + r]) * W[(size_t)N * j + r];
+            M[i + (size_t)n * j] = dV * s;
+        }
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i)
+            L[i + (size_t)n * j] = (i >= j) ? -0.5 * (M[i + (size_t)n * j] + conj(M[j + (size_t)n * i])) : 0.0;
+    for (int j = 0; j < n; ++j) {
+        double d = creal(L[j + (size_t)n * j]);
+        for (int k = 0; k < j; ++k) d -= creal(L[j + (size_t)n * k] * conj(L[j + (size_t)n * k]));
+        if (!(d > 0.0)) return j + 1;
+        const double ljj = sqrt(d);
+        L[j + (size_t)n * j] = ljj;
+        for (int i = j + 1; i < n; ++i) {
+            double complex s = L[i + (size_t)n * j];
+            for (int k = 0; k < j; ++k) s -= L[i + (size_t)n * k] * conj(L[j + (size_t)n * k]);
+            L[i + (size_t)n * j] = s / ljj;
+        }
+    }
+    for (int r = 0; r < N; ++r)
+        for (int j = 0; j < n; ++j) {
+            double complex s = W[(size_t)N * j + r];
+            for (int k = 0; k < j; ++k) s -= xi[(size_t)N * k + r] * conj(L[j + (size_t)n * k]);
+            xi[(size_t)N * j + r] = s / L[j + (size_t)n * j];
+        }
+    return 0;
+}
