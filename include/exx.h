@@ -270,6 +270,44 @@ int exx_plan_get_timing(exx_plan plan, int kind, double *ms_h, long *launches_h)
 int exx_gram_noalloc(int N, double dV, const double *Psi, int n, long ld, const double *W, long ld_w,
                      double *M, exx_stream_t stream);
 
+/* ---- Complex (Bloch) path: Eq. 1 with Brillouin-zone wavevectors --------------------------
+ * The pair problems of Eqs. 2-3 for rho = conj(psi_{m q}) phi_{n k} are solved with Bloch
+ * boundary conditions at k - q along the periodic axes and Dirichlet conditions along the
+ * others (Sec. II, below Eq. 3), FP64 on the CUDA cores.  Complex arrays are interleaved
+ * (re, im) doubles; orbital blocks are N x n complex, column-major, leading dimensions
+ * counted in complex elements.  Grids of at most 2^20 points.
+ *
+ * exx_plan_create_bloch: as exx_plan_create, plus theta[3], the Bloch phase across one
+ * period of each axis (theta_d = (k - q)_d L_d; ignored on Dirichlet axes).  Periodic axes use
+ * the plane-wave eigenbases u_p(j) = exp(i phi_p j)/sqrt(n), phi_p = (2 pi p + theta)/n, with
+ * eigenvalues (w0 + 2 sum_k w_k cos(k phi_p))/h^2.  COULOMB is UNSUPPORTED only when every
+ * axis is periodic and every theta is 0 (mod 2 pi).  The plan serves only the calls below. */
+int exx_plan_create_bloch(exx_plan *out, int Nx, int Ny, int Nz, double h, const int bc[3],
+                          int fd_order, int kernel, double omega, const double theta[3]);
+
+/* One q-term of Eq. 1 for the plan's k - q:
+ *   out_n (+)= - sum_{m < n_occ} f_m psi_m (.) phi_mn,  phi_mn = f(L_{k-q}) (conj(psi_m) (.) psi_n),
+ * psi_m = columns of Psi_occ (orbitals at q, weights f_m = w_q g_{m q}, device doubles),
+ * psi_n = columns of Psi_in (functions at k).  accumulate = 0 overwrites out, 1 adds to it
+ * (sum the q-terms with one Bloch plan per k - q).  Every ordered pair is solved. */
+int exx_apply_complex(exx_plan plan, const double *Psi_occ, int n_occ, long ld_occ, const double *f,
+                      const double *Psi_in, int n_in, long ld_in, double *out, long ld_out,
+                      int accumulate, exx_stream_t stream);
+
+/* E = 1/4 sum_n f_n dV Re <psi_n, VxPsi_n> (HOST *E_x_h; synchronizes `stream`). */
+int exx_energy_complex(exx_plan plan, const double *Psi, int n, long ld, const double *f,
+                       const double *VxPsi, long ld_v, double *E_x_h, exx_stream_t stream);
+
+/* Complex ACE (Sec. III.A): M = dV Psi^H W, -(M + M^H)/2 = L L^H, xi = W L^{-H}; the
+ * compressed operator is -dV xi xi^H.  n <= 96 (one-CTA Cholesky).  *info_h = 0 or 1 + the
+ * failing pivot with EXX_ERR_NOT_POSDEF.  Synchronizes `stream`. */
+int ace_build_complex(exx_plan plan, const double *Psi, int n, long ld, const double *W, long ld_w,
+                      double *xi, long ld_xi, int *info_h, exx_stream_t stream);
+
+/* out = -dV xi (xi^H Phi). */
+int ace_apply_complex(exx_plan plan, const double *xi, int n, long ld_xi, const double *Phi, int nphi,
+                      long ld_phi, double *out, long ld_out, exx_stream_t stream);
+
 /* Static text for a status code; never NULL. */
 const char *exx_status_string(int status);
 

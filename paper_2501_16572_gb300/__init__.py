@@ -45,7 +45,8 @@ EXPORTED = ["exx_plan_create", "exx_plan_set_precision", "exx_plan_set_batch", "
             "exx_plan_get", "exx_apply", "exx_energy", "ace_build", "ace_apply", "exx_ace_step_host",
             "exx_apply_batched", "exx_plan_launch_count", "exx_status_string", "exx_last_error",
             "exx_plan_set_timing", "exx_plan_get_timing", "exx_gram_noalloc", "exx_plan_set_shard",
-            "exx_apply_original", "exx_plan_autotune", "exx_plan_get_tuning"]
+            "exx_apply_original", "exx_plan_autotune", "exx_plan_get_tuning", "exx_plan_create_bloch",
+            "exx_apply_complex", "exx_energy_complex", "ace_build_complex", "ace_apply_complex"]
 TIMING_KINDS = ["pass1", "pass2", "pass3", "pass4", "pass5", "accum", "prep", "gemm", "chol", "energy"]
 
 _lib = None
@@ -90,6 +91,12 @@ def load():
     L.exx_apply_batched.argtypes = [ctypes.POINTER(_vp), _i, ctypes.POINTER(ExxApplyArgs), _vp]
     L.exx_apply_original.argtypes = [_vp, _vp, _i, _l, _vp, _vp, _i, _l, _vp, _l, _vp]
     L.exx_plan_autotune.argtypes = [_vp, _vp, _i, _l, _vp, _vp, _i, _l, _vp, _l, _i, _vp]
+    L.exx_plan_create_bloch.argtypes = [ctypes.POINTER(_vp), _i, _i, _i, _d, ctypes.POINTER(_i), _i, _i, _d,
+                                        ctypes.POINTER(_d)]
+    L.exx_apply_complex.argtypes = [_vp, _vp, _i, _l, _vp, _vp, _i, _l, _vp, _l, _i, _vp]
+    L.exx_energy_complex.argtypes = [_vp, _vp, _i, _l, _vp, _vp, _l, ctypes.POINTER(_d), _vp]
+    L.ace_build_complex.argtypes = [_vp, _vp, _i, _l, _vp, _l, _vp, _l, ctypes.POINTER(_i), _vp]
+    L.ace_apply_complex.argtypes = [_vp, _vp, _i, _l, _vp, _i, _l, _vp, _l, _vp]
     L.exx_plan_get_tuning.argtypes = [_vp, ctypes.POINTER(_i), ctypes.POINTER(_d), ctypes.POINTER(_i)]
     L.exx_plan_launch_count.argtypes = [_vp]
     L.exx_plan_launch_count.restype = _l
@@ -127,6 +134,16 @@ def _orb(t, N, name):
     import torch
     if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda:
         raise TypeError(f"{name} must be a float64 CUDA tensor")
+    if t.dim() != 2 or t.shape[1] != N or t.stride(1) != 1:
+        raise ValueError(f"{name} must have shape (n, {N}) with contiguous rows")
+    return t.shape[0], t.stride(0)
+
+
+def _corb(t, N, name):
+    """Validate a (n, N) complex128 CUDA block with contiguous rows; returns (n, ld)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.complex128 or not t.is_cuda:
+        raise TypeError(f"{name} must be a complex128 CUDA tensor")
     if t.dim() != 2 or t.shape[1] != N or t.stride(1) != 1:
         raise ValueError(f"{name} must have shape (n, {N}) with contiguous rows")
     return t.shape[0], t.stride(0)
@@ -242,6 +259,78 @@ class Plan:
         _check(load().exx_plan_get_tuning(self._h, v, ctypes.byref(ms), ctypes.byref(tuned)), "exx_plan_get_tuning")
         return {"pairs_per_batch": v[0], "block_orbitals": v[1], "z_block": v[2], "z_buffers": v[3],
                 "staging": v[4], "ms_per_pair": ms.value, "tuned": tuned.value}
+
+    # -- complex (Bloch) plans ------------------------------------------------------------
+    @classmethod
+    def bloch(cls, n, h, bc, theta, fd_order=12, kernel=EXX_KERNEL_COULOMB, omega=0.0):
+        """A Bloch plan (exx_plan_create_bloch): theta[d] = phase across one period of axis d."""
+        self = cls.__new__(cls)
+        self.n = tuple(int(v) for v in n)
+        self.N = self.n[0] * self.n[1] * self.n[2]
+        self.h = float(h)
+        self.dV = self.h ** 3
+        self.bc = tuple(int(b) for b in bc)
+        self.kernel = int(kernel)
+        self.omega = float(omega)
+        self.precision = EXX_PREC_FP64
+        h_ = _vp()
+        bca = (_i * 3)(*self.bc)
+        th = (_d * 3)(*[float(t) for t in theta])
+        _check(load().exx_plan_create_bloch(ctypes.byref(h_), self.n[0], self.n[1], self.n[2], self.h, bca,
+                                            int(fd_order), self.kernel, self.omega, th), "exx_plan_create_bloch")
+        self._h = h_
+        return self
+
+    def apply_complex(self, psi_occ, f, psi_in, out=None, accumulate=False, stream=None):
+        import torch
+        n_occ, ld_occ = _corb(psi_occ, self.N, "psi_occ")
+        n_in, ld_in = _corb(psi_in, self.N, "psi_in")
+        if f.dtype != torch.float64 or not f.is_cuda or f.numel() < n_occ or not f.is_contiguous():
+            raise ValueError("f must be a contiguous float64 CUDA tensor with n_occ entries")
+        if out is None:
+            out = torch.empty((n_in, self.N), dtype=torch.complex128, device=psi_in.device)
+        n_o, ld_out = _corb(out, self.N, "out")
+        if n_o != n_in:
+            raise ValueError("out must have n_in rows")
+        _check(load().exx_apply_complex(self._h, _ptr(psi_occ), n_occ, ld_occ, _ptr(f), _ptr(psi_in), n_in, ld_in,
+                                        _ptr(out), ld_out, 1 if accumulate else 0, _stream(stream)),
+               "exx_apply_complex")
+        return out
+
+    def energy_complex(self, psi, f, vx, stream=None):
+        n, ld = _corb(psi, self.N, "psi")
+        _, ld_v = _corb(vx, self.N, "vx")
+        e = _d(0.0)
+        _check(load().exx_energy_complex(self._h, _ptr(psi), n, ld, _ptr(f), _ptr(vx), ld_v, ctypes.byref(e),
+                                         _stream(stream)), "exx_energy_complex")
+        return e.value
+
+    def ace_build_complex(self, psi, W, xi=None, stream=None):
+        import torch
+        n, ld = _corb(psi, self.N, "psi")
+        _, ld_w = _corb(W, self.N, "W")
+        if xi is None:
+            xi = torch.empty_like(psi)
+        _, ld_xi = _corb(xi, self.N, "xi")
+        info = _i(0)
+        rc = load().ace_build_complex(self._h, _ptr(psi), n, ld, _ptr(W), ld_w, _ptr(xi), ld_xi, ctypes.byref(info),
+                                      _stream(stream))
+        if rc != EXX_OK:
+            err = ExxError(rc, "ace_build_complex")
+            err.pivot = info.value - 1
+            raise err
+        return xi
+
+    def ace_apply_complex(self, xi, phi, out=None, stream=None):
+        import torch
+        n, ld_xi = _corb(xi, self.N, "xi")
+        nphi, ld_phi = _corb(phi, self.N, "phi")
+        if out is None:
+            out = torch.empty_like(phi)
+        _, ld_out = _corb(out, self.N, "out")
+        _check(load().ace_apply_complex(self._h, _ptr(xi), n, ld_xi, _ptr(phi), nphi, ld_phi, _ptr(out), ld_out,
+                                        _stream(stream)), "ace_apply_complex")
+        return out
 
     def apply_original(self, psi_occ, f, psi_in, out=None, stream=None):
         """exx_apply_original: the same result, one pair at a time with Eq. 8's 4 n_z + 2 GEMMs."""

@@ -70,6 +70,7 @@ static void free_plan_buffers(Plan &P)
     dev_free(P.orig_V);
     dev_free(P.F64n);
     dev_free(P.orig_ws);
+    for (auto *b : {&P.cmats, &P.cFd, &P.cwork, &P.cpairs, &P.cred, &P.cace}) dev_free(*b);
     for (auto *b : {&P.F64, &P.F32, &P.work[0], &P.work[1], &P.work[2], &P.pairs_d, &P.blocks_d,
                     &P.acc_hi, &P.acc_lo, &P.g32, &P.psi32, &P.gemm_ws, &P.small_ws, &P.info_d,
                     &P.red_ws, &P.host_stage_psi, &P.host_stage_f, &P.host_stage_xi, &P.host_stage_w,
@@ -236,6 +237,10 @@ int exx_plan_set_precision(exx_plan plan, int prec)
     Plan *P = as_plan(plan);
     if (!P) return invalid("exx_plan_set_precision: plan is NULL");
     if (prec < EXX_PREC_FP64 || prec > EXX_PREC_BF16X7) return invalid("exx_plan_set_precision: bad precision");
+    if (P->cplx && prec != EXX_PREC_FP64) {
+        set_error("exx_plan_set_precision: Bloch plans run in FP64");
+        return EXX_ERR_UNSUPPORTED;
+    }
     if (prec == EXX_PREC_BF16X7) {
         if (int rc = tc3_upload(*P)) return rc;
     } else if (prec != EXX_PREC_FP64) {
@@ -352,6 +357,10 @@ struct ApplyCall {
 static int apply_prepare(Plan *P, ApplyCall &c, cudaStream_t s)
 {
     if (!P) return invalid("exx_apply: plan is NULL");
+    if (P->cplx) {
+        set_error("exx_apply: a Bloch plan takes complex orbitals (exx_apply_complex)");
+        return EXX_ERR_UNSUPPORTED;
+    }
     if (!c.Psi_occ || !c.f || !c.Psi_in || !c.out) return invalid("exx_apply: NULL array");
     if (c.n_occ < 1 || c.n_in < 1 || c.n_occ > 65536 || c.n_in > 65536) return invalid("exx_apply: orbital counts must be in [1, 65536]");
     if (c.ld_occ < P->N || c.ld_in < P->N || c.ld_out < P->N) return invalid("exx_apply: leading dimensions must be >= N");

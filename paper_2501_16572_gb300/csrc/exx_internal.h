@@ -164,6 +164,11 @@ struct Plan {
     double tune_ms = 0.0;           // the chosen setting's trial time per pair solve
     // original (non-batched) formalism: eigenvectors, f(Lambda) in the natural layout, workspace
     DevBuf orig_V, F64n, orig_ws;
+    // Bloch (complex) plans: phases, eigenvalues, f, contraction matrices and workspace
+    int cplx = 0;
+    double theta[3] = {0.0, 0.0, 0.0};
+    std::vector<double> clam[3], cF;
+    DevBuf cmats, cFd, cwork, cpairs, cred, cace;
     // workspace
     DevBuf work[3];                 // batch buffers (fields x N)
     DevBuf pairs_d, blocks_d;       // schedule on the device
