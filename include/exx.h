@@ -218,8 +218,10 @@ int exx_ace_step_host(exx_plan plan, const double *Psi_h, int n, long ld, int n_
  *   1. Every system is checked and every device allocation is made first (this
  *      synchronizes `stream` when a plan's pair schedule has to be rebuilt).
  *   2. On a stream other than NULL, with timing off on every plan, the launches of
- *      all systems are captured once into one CUDA graph (relaxed capture mode) and
- *      kept in a library-wide cache of 8 graphs, keyed by the plans, their settings
+ *      all systems are captured once into one CUDA graph (relaxed capture mode), the
+ *      systems spread over 8 concurrent branches (system s on branch s mod 8, forked from
+ *      and joined back into `stream`) so that small systems share the GPU, and kept in a
+ *      library-wide cache of 8 graphs, keyed by the plans, their settings
  *      and every pointer, size and leading dimension in args; a later call with the
  *      same key replays the graph: one launch from the host for the whole sequence.
  *      A replay reads whatever the pointed-to buffers hold at that time, so callers

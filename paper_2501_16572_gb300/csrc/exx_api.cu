@@ -438,6 +438,7 @@ struct GraphEntry {
 static std::mutex g_graph_mutex;
 static std::vector<GraphEntry> g_graphs;
 constexpr size_t kMaxGraphs = 8;
+constexpr int kBranches = 8;   // concurrent branches of a batched graph
 
 // Drops every cached graph that launches work of plan P (called before P is freed).
 static void graph_evict_plan(const Plan *P)
@@ -803,15 +804,46 @@ int exx_apply_batched(const exx_plan *plans, int nsys, const exx_apply_args *arg
         ent.plans.push_back(as_plan(plans[i]));
         ent.plans.back()->launches = 0;
     }
-    EXX_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+    // the systems' launch sequences go to kBranches forked streams inside the capture, so
+    // the graph holds independent branches: small systems run concurrently and fill the
+    // SMs that one system alone leaves idle
+    const int nbr = std::min(nsys, kBranches);
+    std::vector<cudaStream_t> side(nbr, nullptr);
+    std::vector<cudaEvent_t> joins(nbr, nullptr);
+    cudaEvent_t fork = nullptr;
+    for (int k = 0; k < nbr; ++k) {
+        EXX_CUDA(cudaStreamCreateWithFlags(&side[k], cudaStreamNonBlocking));
+        EXX_CUDA(cudaEventCreateWithFlags(&joins[k], cudaEventDisableTiming));
+    }
+    EXX_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    auto cleanup = [&]() {
+        for (int k = 0; k < nbr; ++k) {
+            cudaStreamDestroy(side[k]);
+            cudaEventDestroy(joins[k]);
+        }
+        cudaEventDestroy(fork);
+    };
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(e, "exx_apply_batched: cudaStreamBeginCapture");
+    }
     int rc = EXX_OK;
+    if (cudaEventRecord(fork, s) != cudaSuccess) rc = EXX_ERR_CUDA;
+    for (int k = 0; k < nbr && rc == EXX_OK; ++k)
+        if (cudaStreamWaitEvent(side[k], fork, 0) != cudaSuccess) rc = EXX_ERR_CUDA;
     for (int i = 0; i < nsys && rc == EXX_OK; ++i) {
         const long before = ent.plans[i]->launches;
-        rc = apply_launch(ent.plans[i], calls[i], s);
+        rc = apply_launch(ent.plans[i], calls[i], side[i % nbr]);
         ent.launches.push_back(ent.plans[i]->launches - before);
     }
+    for (int k = 0; k < nbr; ++k) {   // join every branch back, also after an error
+        cudaEventRecord(joins[k], side[k]);
+        cudaStreamWaitEvent(s, joins[k], 0);
+    }
     cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    e = cudaStreamEndCapture(s, &graph);
+    cleanup();
     if (rc != EXX_OK) {
         if (graph) cudaGraphDestroy(graph);
         return rc;

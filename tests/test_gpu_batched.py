@@ -1,8 +1,9 @@
 """exx_apply_batched: many independent systems in one call (Sec. II.B's batching of
 pair solves carried across systems), through the C interface.
 
-1. On a side stream the launches of all systems are captured once into a CUDA graph;
-   every output must equal, bit for bit, what exx_apply writes for that system alone,
+1. On a side stream the launches of all systems are captured once into a CUDA graph (the
+   systems on concurrent branches); every output must equal, bit for bit, what exx_apply
+   writes for that system alone,
    on the first call (capture + replay) and on a second call after the inputs were
    refilled in place (replay of the cached graph).
 2. On the legacy default stream the same launches are issued one by one; same outputs.
@@ -70,7 +71,7 @@ def _batched(exx, plans, bufs, systems, stream):
     return [out.clone() for (_, _, out) in bufs]
 
 
-@pytest.mark.parametrize("prec", [0, 4], ids=["fp64", "bf16x10"])
+@pytest.mark.parametrize("prec", [0, 4, 5], ids=["fp64", "bf16x10", "bf16x7"])
 def test_graph_equals_individual_applies_twice(exx, prec):
     systems, plans, bufs = _setup(exx, prec, seed=60)
     ref = _individual(plans, bufs, systems)
