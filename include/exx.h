@@ -127,7 +127,8 @@ int exx_plan_set_shard(exx_plan plan, int rank, int world);
  * rules (out is used as scratch and left holding partial results).  Coordinate descent over
  *   pairs per batch {default, 256, 512, 1024} x orbitals per pair block {8, 16}, then, in
  *   the BF16X7 mode, the pass-B matrix block width and shared-memory buffer count (every
- *   choice that fits) and the slice-pass input staging (on, off);
+ *   choice that fits), then the slice passes' form (serial with up to two CTAs per SM, or
+ *   software-pipelined over tiles with one CTA per SM) with their input staging (auto, off, on);
  * each candidate runs up to three batches of the pair schedule twice (warm-up, then timed
  * with CUDA events on `stream`); the fastest per pair solve is kept in the plan (as by
  * exx_plan_set_batch) and in a process-wide cache keyed by grid, boundary conditions,
@@ -138,10 +139,16 @@ int exx_plan_autotune(exx_plan plan, const double *Psi_occ, int n_occ, long ld_o
                       const double *Psi_in, int n_in, long ld_in, double *out, long ld_out, int flags,
                       exx_stream_t stream);
 
-/* The plan's settings (HOST int[5]: pairs per batch, orbitals per block, pass-B block width,
- * pass-B buffers, slice staging; 0 / -1 = automatic), the autotuner's trial time per pair
+/* The plan's settings (HOST int[6]: pairs per batch, orbitals per block, pass-B block width,
+ * pass-B buffers, slice staging, slice pipeline; 0 / -1 = automatic), the autotuner's trial time per pair
  * solve in ms (0 if never tuned) and *tuned_h = 0 (not tuned), 1 (measured), 2 (cache). */
 int exx_plan_get_tuning(exx_plan plan, int *settings_h, double *ms_per_pair_h, int *tuned_h);
+
+/* Set the same six settings by hand (for instance a choice the autotuner made earlier):
+ * pairs per batch >= 0, block in [0, 32], pass-B block width (a multiple of 16, <= 256) and
+ * buffers (both 0 = automatic, or both set; a pair that does not fit falls back to the
+ * automatic choice), staging and pipeline in {-1, 0, 1}.  EXX_ERR_INVALID_ARG otherwise. */
+int exx_plan_set_tuning(exx_plan plan, const int *settings_h);
 
 /* Free the plan and its device workspace (synchronizes the device first). */
 int exx_plan_destroy(exx_plan plan);

@@ -46,7 +46,8 @@ EXPORTED = ["exx_plan_create", "exx_plan_set_precision", "exx_plan_set_batch", "
             "exx_apply_batched", "exx_plan_launch_count", "exx_status_string", "exx_last_error",
             "exx_plan_set_timing", "exx_plan_get_timing", "exx_gram_noalloc", "exx_plan_set_shard",
             "exx_apply_original", "exx_plan_autotune", "exx_plan_get_tuning", "exx_plan_create_bloch",
-            "exx_apply_complex", "exx_energy_complex", "ace_build_complex", "ace_apply_complex"]
+            "exx_apply_complex", "exx_energy_complex", "ace_build_complex", "ace_apply_complex",
+            "exx_plan_set_tuning"]
 TIMING_KINDS = ["pass1", "pass2", "pass3", "pass4", "pass5", "accum", "prep", "gemm", "chol", "energy"]
 
 _lib = None
@@ -98,6 +99,7 @@ def load():
     L.ace_build_complex.argtypes = [_vp, _vp, _i, _l, _vp, _l, _vp, _l, ctypes.POINTER(_i), _vp]
     L.ace_apply_complex.argtypes = [_vp, _vp, _i, _l, _vp, _i, _l, _vp, _l, _vp]
     L.exx_plan_get_tuning.argtypes = [_vp, ctypes.POINTER(_i), ctypes.POINTER(_d), ctypes.POINTER(_i)]
+    L.exx_plan_set_tuning.argtypes = [_vp, ctypes.POINTER(_i)]
     L.exx_plan_launch_count.argtypes = [_vp]
     L.exx_plan_launch_count.restype = _l
     L.exx_plan_set_timing.argtypes = [_vp, _i]
@@ -252,13 +254,18 @@ class Plan:
                                         _ptr(out), ld_out, 1 if remeasure else 0, _stream(stream)), "exx_plan_autotune")
         return self.tuning()
 
+    def set_tuning(self, pairs_per_batch=0, block_orbitals=0, z_block=0, z_buffers=0, staging=-1, pipeline=-1):
+        v = (_i * 6)(pairs_per_batch, block_orbitals, z_block, z_buffers, staging, pipeline)
+        _check(load().exx_plan_set_tuning(self._h, v), "exx_plan_set_tuning")
+
     def tuning(self):
-        """{'pairs_per_batch', 'block_orbitals', 'z_block', 'z_buffers', 'staging', 'ms_per_pair', 'tuned'}"""
-        v = (_i * 5)()
+        """{'pairs_per_batch', 'block_orbitals', 'z_block', 'z_buffers', 'staging', 'pipeline', 'ms_per_pair',
+        'tuned'}"""
+        v = (_i * 6)()
         ms, tuned = _d(0.0), _i(0)
         _check(load().exx_plan_get_tuning(self._h, v, ctypes.byref(ms), ctypes.byref(tuned)), "exx_plan_get_tuning")
         return {"pairs_per_batch": v[0], "block_orbitals": v[1], "z_block": v[2], "z_buffers": v[3],
-                "staging": v[4], "ms_per_pair": ms.value, "tuned": tuned.value}
+                "staging": v[4], "pipeline": v[5], "ms_per_pair": ms.value, "tuned": tuned.value}
 
     # -- complex (Bloch) plans ------------------------------------------------------------
     @classmethod

@@ -518,7 +518,7 @@ struct TuneKey {
     }
 };
 struct TuneVal {
-    int pairs, block, zwn, znbuf, stage;
+    int pairs, block, zwn, znbuf, stage, pipe;
     double ms;
 };
 static std::mutex g_tune_mutex;
@@ -531,6 +531,7 @@ static void tune_set(Plan &P, const TuneVal &v)
     P.t3_zwn = v.zwn;
     P.t3_znbuf = v.znbuf;
     P.t3_stage = v.stage;
+    P.t3_pipe = v.pipe;
     std::fill(P.sched_key, P.sched_key + 4, -1);
     bump_epoch(P);
 }
@@ -593,7 +594,7 @@ int exx_plan_autotune(exx_plan plan, const double *Psi_occ, int n_occ, long ld_o
     }
     // coordinate descent: pair batch and orbital block, then (three-pass mode) the pass-B
     // matrix blocks and buffers, then the slice-pass staging
-    TuneVal best{0, 0, 0, 0, -1, 1e300};
+    TuneVal best{0, 0, 0, 0, -1, -1, 1e300};
     auto consider = [&](TuneVal v) -> int {
         int rc = EXX_OK;
         v.ms = tune_trial(*P, c, v, s, rc);
@@ -603,14 +604,15 @@ int exx_plan_autotune(exx_plan plan, const double *Psi_occ, int n_occ, long ld_o
     };
     for (int pairs : {0, 256, 512, 1024})
         for (int block : {8, 16})
-            if (int rc = consider({pairs, block, 0, 0, -1, 0.0})) return rc;
+            if (int rc = consider({pairs, block, 0, 0, -1, -1, 0.0})) return rc;
     if (P->prec == EXX_PREC_BF16X7) {
         const TuneVal base = best;
         for (auto &zc : tc3_z_choices(P->n[2]))
-            if (int rc = consider({base.pairs, base.block, zc.first, zc.second, -1, 0.0})) return rc;
+            if (int rc = consider({base.pairs, base.block, zc.first, zc.second, -1, -1, 0.0})) return rc;
         const TuneVal base2 = best;
-        for (int st : {0, 1})
-            if (int rc = consider({base2.pairs, base2.block, base2.zwn, base2.znbuf, st, 0.0})) return rc;
+        for (int pipe : {0, 1})
+            for (int st : {-1, 0, 1})
+                if (int rc = consider({base2.pairs, base2.block, base2.zwn, base2.znbuf, st, pipe, 0.0})) return rc;
     }
     if (best.ms >= 1e300) {
         set_error("exx_plan_autotune: no candidate setting ran");
@@ -632,6 +634,22 @@ int exx_plan_autotune(exx_plan plan, const double *Psi_occ, int n_occ, long ld_o
     return EXX_OK;
 }
 
+int exx_plan_set_tuning(exx_plan plan, const int *settings_h)
+{
+    Plan *P = as_plan(plan);
+    if (!P || !settings_h) return invalid("exx_plan_set_tuning: NULL argument");
+    const int *v = settings_h;
+    if (v[0] < 0 || v[1] < 0 || v[1] > 32 || v[2] < 0 || v[2] > 256 || (v[2] & 15) || v[3] < 0 || v[3] > 64 ||
+        v[4] < -1 || v[4] > 1 || v[5] < -1 || v[5] > 1 || ((v[2] == 0) != (v[3] == 0)))
+        return invalid("exx_plan_set_tuning: settings out of range");
+    tune_set(*P, {v[0], v[1], v[2], v[3], v[4], v[5], 0.0});
+    if (P->prec == EXX_PREC_BF16X7)
+        if (int rc = tc3_upload(*P)) return rc;
+    P->tuned = 0;
+    P->tune_ms = 0.0;
+    return EXX_OK;
+}
+
 int exx_plan_get_tuning(exx_plan plan, int *settings_h, double *ms_per_pair_h, int *tuned_h)
 {
     Plan *P = as_plan(plan);
@@ -641,6 +659,7 @@ int exx_plan_get_tuning(exx_plan plan, int *settings_h, double *ms_per_pair_h, i
     settings_h[2] = P->t3_zwn;
     settings_h[3] = P->t3_znbuf;
     settings_h[4] = P->t3_stage;
+    settings_h[5] = P->t3_pipe;
     *ms_per_pair_h = P->tune_ms;
     *tuned_h = P->tuned;
     return EXX_OK;

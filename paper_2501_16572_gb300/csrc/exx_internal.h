@@ -160,6 +160,7 @@ struct Plan {
     int t3_share01 = 0;             // x and y have the same length and bc: one image serves both
     int t3_zwn = 0, t3_znbuf = 0;   // pass B matrix block width and buffers (0 = automatic)
     int t3_stage = -1;              // slice-pass input staging (-1 = automatic)
+    int t3_pipe = -1;               // slice-pass software pipeline (-1 = automatic)
     int tuned = 0;                  // 1 = measured by exx_plan_autotune, 2 = taken from its cache
     double tune_ms = 0.0;           // the chosen setting's trial time per pair solve
     // original (non-batched) formalism: eigenvectors, f(Lambda) in the natural layout, workspace

@@ -190,6 +190,9 @@ struct SliceArgs {
     int vec;                // rows of n1 floats start 16-byte aligned (n1 % 4 == 0, N % 4 == 0)
     int stage;              // the tile's input arrives in shared memory by bulk copies (R % 4 == 0)
     uint32_t offS, stg_plane;   // staging buffer and its plane stride (bytes)
+    int pipe;               // software pipeline over tiles: GEMM 2 has its own A image (offA2) and
+    uint32_t offA2;         // TMEM columns (t2col), so each GEMM overlaps the other phase's work
+    int t2col;
     int *err;
 };
 
@@ -201,15 +204,15 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 2) slice_pass_kernel(const _
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     uint8_t *sB1 = smem;
     uint8_t *sB2 = a.offB2 ? smem + a.offB2 : smem;
-    uint8_t *sA = smem + a.offA;
+    uint8_t *sA1 = smem + a.offA, *sA2 = smem + a.offA2;
     float *Ysm = reinterpret_cast<float *>(smem + a.offY);
     float *rsb1 = reinterpret_cast<float *>(smem + a.offRs);
     float *rsb2 = rsb1 + kRows;
     float *stg = reinterpret_cast<float *>(smem + a.offS);
     uint64_t *bar_a = reinterpret_cast<uint64_t *>(smem + a.offBar);
-    uint64_t *bar_d = bar_a + 1;
-    uint64_t *stg_full = bar_a + 2, *stg_empty = bar_a + 3;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar_a + 4);
+    uint64_t *bar_d1 = bar_a + 1, *bar_d2 = bar_a + 2;
+    uint64_t *stg_full = bar_a + 3, *stg_empty = bar_a + 4;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar_a + 5);
     int *sflag = reinterpret_cast<int *>(tslot + 1);
 
     for (uint32_t i = tid * 16; i < a.img1_bytes; i += blockDim.x * 16)
@@ -220,7 +223,7 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 2) slice_pass_kernel(const _
     for (uint32_t i = a.offA + tid * 16; i < a.offY; i += blockDim.x * 16)   // A images start as zeros
         *reinterpret_cast<uint4 *>(smem + i) = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
-        for (int i = 0; i < 4; ++i) tc::mbar_init(bar_a + i, 1);
+        for (int i = 0; i < 5; ++i) tc::mbar_init(bar_a + i, 1);
         *sflag = 0;
     }
     if (warp == 0) tc::tmem_alloc(tslot, uint32_t(a.tmem_cols));
@@ -265,7 +268,9 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 2) slice_pass_kernel(const _
         // ---- MMA warp: two GEMMs per tile, each after the compute threads' hand-off ----
         uint32_t ph = 0;
         const uint32_t idesc1 = tc::instr_desc(false, Kp1), idesc2 = tc::instr_desc(false, Kp2);
-        const uint32_t a0 = tc::smem_addr(sA), b1 = tc::smem_addr(sB1), b2 = tc::smem_addr(sB2);
+        const uint32_t a1 = tc::smem_addr(sA1), a2 = tc::smem_addr(sA2), b1 = tc::smem_addr(sB1),
+                       b2 = tc::smem_addr(sB2);
+        const uint32_t t2 = tmem + uint32_t(a.t2col);
         bool bad = false;
         for (long tile = blockIdx.x; tile < a.ntiles && !bad; tile += gridDim.x) {
             for (int g = 0; g < 2 && !bad; ++g) {
@@ -276,13 +281,15 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 2) slice_pass_kernel(const _
                 ph ^= 1u;
                 tc::tc_fence_after();
                 if (!bad && lane == 0) {
-                    if (g == 0)
-                        issue_x7(tmem, tmem + uint32_t(Kp1), a0, a.a_piece1, b1, uint32_t(Kp1) * Kp1 * 2u, sbo1,
+                    if (g == 0) {
+                        issue_x7(tmem, tmem + uint32_t(Kp1), a1, a.a_piece1, b1, uint32_t(Kp1) * Kp1 * 2u, sbo1,
                                  Kp1 / 16, idesc1);
-                    else
-                        issue_x7(tmem, tmem + uint32_t(Kp2), a0, a.a_piece2, b2, uint32_t(Kp2) * Kp2 * 2u, sbo2,
+                        tc::mma_commit(bar_d1);
+                    } else {
+                        issue_x7(t2, t2 + uint32_t(Kp2), a2, a.a_piece2, b2, uint32_t(Kp2) * Kp2 * 2u, sbo2,
                                  Kp2 / 16, idesc2);
-                    tc::mma_commit(bar_d);
+                        tc::mma_commit(bar_d2);
+                    }
                 }
                 __syncwarp();
             }
@@ -297,7 +304,7 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 2) slice_pass_kernel(const _
         const uint32_t lane_q = uint32_t(quarter * 32) << 16;
         const float *cs1 = reinterpret_cast<const float *>(sB1 + size_t(kMatDig) * Kp1 * Kp1 * 2);
         const float *cs2 = reinterpret_cast<const float *>(sB2 + size_t(kMatDig) * Kp2 * Kp2 * 2);
-        uint32_t ph = 0;
+        uint32_t ph1 = 0, ph2 = 0;
         // publish the A image to the MMA warp (and, after the first operand, hand the staging
         // buffer back to the producer); true = stop (error)
         auto handoff = [&](bool release) {
@@ -309,166 +316,224 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 2) slice_pass_kernel(const _
             }
             return stop;
         };
-        auto wait_d = [&]() {
-            if (!tc::mbar_wait_bounded(bar_d, ph, kWaitLimit)) atomicExch(sflag, 1);
+        auto wait_d = [&](uint64_t *bar, uint32_t &ph) {
+            if (!tc::mbar_wait_bounded(bar, ph, kWaitLimit)) atomicExch(sflag, 1);
             ph ^= 1u;
             tc::tc_fence_after();
         };
-        long it = 0;
-        for (long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
-            const long p = tile / a.tpf;
-            const int z0 = int(tile - p * a.tpf) * a.G;
-            const int ns = min(a.G, a.n3 - z0);
-            const int R1 = ns * n2, R2 = ns * n1;
-            // ---- GEMM 1 operand: row (s, j), K = i; sweep 1 finds the row maximum, sweep 2
-            //      (the same loads, mostly from L1) cuts the digits ----
-            {
-                const bool act = srow < R1;
-                const int s = act ? srow / n2 : 0, j = act ? srow - s * n2 : 0;
-                const size_t off = size_t(z0 + s) * R + size_t(j) * n1;
-                const float *x0, *x1 = nullptr;
-                if (a.stage) {   // rows of this tile's slices in the staging buffer
-                    if (!tc::mbar_wait_bounded(stg_full, uint32_t(it & 1), kWaitLimit)) atomicExch(sflag, 1);
-                    const size_t so = size_t(s) * R + size_t(j) * n1;
-                    x0 = stg + so;
-                    x1 = reinterpret_cast<const float *>(reinterpret_cast<const uint8_t *>(stg) + a.stg_plane) + so;
-                } else if (PAIR) {
-                    const int2 mn = a.pairs[p];
-                    x0 = a.psi + size_t(a.occ_off + mn.x) * a.N + off;
-                    x1 = a.psi + size_t(mn.y) * a.N + off;
-                } else {
-                    x0 = a.in + size_t(p) * a.N + off;
-                }
-                // unit u: elements 4u..4u+3 of the row (hi, and with LO the product's rounding error)
-                auto unit = [&](int k0, float (&h)[4], float (&l)[4], auto LO) {
-                    float u0[4], u1[4];
-                    if (a.vec && k0 + 4 <= n1) {
-                        const float4 v = *reinterpret_cast<const float4 *>(x0 + k0);
-                        u0[0] = v.x; u0[1] = v.y; u0[2] = v.z; u0[3] = v.w;
-                        if (PAIR) {
-                            const float4 w = *reinterpret_cast<const float4 *>(x1 + k0);
-                            u1[0] = w.x; u1[1] = w.y; u1[2] = w.z; u1[3] = w.w;
-                        }
+        struct TileInfo {
+            long p;
+            int z0, R1, R2;
+        };
+        auto info = [&](long tile) {
+            TileInfo t;
+            t.p = tile / a.tpf;
+            t.z0 = int(tile - t.p * a.tpf) * a.G;
+            const int ns = min(a.G, a.n3 - t.z0);
+            t.R1 = ns * n2;
+            t.R2 = ns * n1;
+            return t;
+        };
+        // the four phases of a tile
+        auto slice1 = [&](const TileInfo &ti, long it) {
+            const long p = ti.p;
+            const int z0 = ti.z0, R1 = ti.R1;
+                // ---- GEMM 1 operand: row (s, j), K = i; sweep 1 finds the row maximum, sweep 2
+                //      (the same loads, mostly from L1) cuts the digits ----
+                {
+                    const bool act = srow < R1;
+                    const int s = act ? srow / n2 : 0, j = act ? srow - s * n2 : 0;
+                    const size_t off = size_t(z0 + s) * R + size_t(j) * n1;
+                    const float *x0, *x1 = nullptr;
+                    if (a.stage) {   // rows of this tile's slices in the staging buffer
+                        if (!tc::mbar_wait_bounded(stg_full, uint32_t(it & 1), kWaitLimit)) atomicExch(sflag, 1);
+                        const size_t so = size_t(s) * R + size_t(j) * n1;
+                        x0 = stg + so;
+                        x1 = reinterpret_cast<const float *>(reinterpret_cast<const uint8_t *>(stg) + a.stg_plane) + so;
+                    } else if (PAIR) {
+                        const int2 mn = a.pairs[p];
+                        x0 = a.psi + size_t(a.occ_off + mn.x) * a.N + off;
+                        x1 = a.psi + size_t(mn.y) * a.N + off;
                     } else {
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const bool ok = k0 + e < n1;
-                            u0[e] = ok ? x0[k0 + e] : 0.f;
-                            if (PAIR) u1[e] = ok ? x1[k0 + e] : 0.f;
-                        }
+                        x0 = a.in + size_t(p) * a.N + off;
                     }
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        if (PAIR) {
-                            h[e] = u0[e] * u1[e];
-                            l[e] = decltype(LO)::value ? fmaf(u0[e], u1[e], -h[e]) : 0.f;
+                    // unit u: elements 4u..4u+3 of the row (hi, and with LO the product's rounding error)
+                    auto unit = [&](int k0, float (&h)[4], float (&l)[4], auto LO) {
+                        float u0[4], u1[4];
+                        if (a.vec && k0 + 4 <= n1) {
+                            const float4 v = *reinterpret_cast<const float4 *>(x0 + k0);
+                            u0[0] = v.x; u0[1] = v.y; u0[2] = v.z; u0[3] = v.w;
+                            if (PAIR) {
+                                const float4 w = *reinterpret_cast<const float4 *>(x1 + k0);
+                                u1[0] = w.x; u1[1] = w.y; u1[2] = w.z; u1[3] = w.w;
+                            }
                         } else {
-                            h[e] = u0[e];
-                            l[e] = 0.f;
+    #pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const bool ok = k0 + e < n1;
+                                u0[e] = ok ? x0[k0 + e] : 0.f;
+                                if (PAIR) u1[e] = ok ? x1[k0 + e] : 0.f;
+                            }
                         }
-                    }
-                };
-                float mx = 0.f;
-                if (act)
-                    for (int k0 = 4 * sq; k0 < n1; k0 += 4 * TPR) {
-                        float h[4], l[4];
-                        unit(k0, h, l, std::false_type{});
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) mx = fmaxf(mx, fabsf(h[e]));
-                    }
-#pragma unroll
-                for (int o = 1; o < TPR; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-                float sc, inv;
-                row_scales(mx, sc, inv);
-                if (act) {
-                    if (sq == 0) rsb1[srow] = inv;
-                    for (int k0 = 4 * sq; k0 < n1; k0 += 4 * TPR) {
-                        float h[4], l[4];
-                        unit(k0, h, l, std::true_type{});
-                        store_digits4(sA, a.a_piece1, img_at(srow, k0 >> 3, sbo1) + uint32_t(k0 & 7) * 2u, h, l, sc);
-                    }
-                }
-            }
-            if (handoff(true)) break;
-            wait_d();
-            // ---- GEMM 1 result -> transposed tile Y[(s, i')][j] ----
-            {
-                const bool act = drow < R1;
-                const int s = act ? drow / n2 : 0, j = act ? drow - s * n2 : 0;
-                const float rs = act ? rsb1[drow] : 0.f;
-                float *yb = Ysm + size_t(s) * n1 * a.Pj + j;
-                for (int u4 = dq; u4 < Kp1 / 4; u4 += TPR) {
-                    float v0[4], v1[4];
-                    tmem_pair4(tmem + lane_q + uint32_t(4 * u4), tmem + lane_q + uint32_t(Kp1 + 4 * u4), v0, v1);
-                    const float4 c4 = *reinterpret_cast<const float4 *>(cs1 + 4 * u4);
-                    const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
-                    if (act) {
-#pragma unroll
+    #pragma unroll
                         for (int e = 0; e < 4; ++e) {
-                            const int col = 4 * u4 + e;
-                            if (col < n1) yb[size_t(col) * a.Pj] = (v0[e] + v1[e]) * (rs * cv[e]);
+                            if (PAIR) {
+                                h[e] = u0[e] * u1[e];
+                                l[e] = decltype(LO)::value ? fmaf(u0[e], u1[e], -h[e]) : 0.f;
+                            } else {
+                                h[e] = u0[e];
+                                l[e] = 0.f;
+                            }
                         }
-                    }
-                }
-                tc::tc_fence_before();
-            }
-            tc::bar_sync(1, NT);
-            // ---- GEMM 2 operand: row (s, i'), K = j, from the transposed tile ----
-            {
-                const bool act = srow < R2;
-                const float *yr = Ysm + size_t(act ? srow : 0) * a.Pj;
-                auto unit = [&](int k0, float (&h)[4]) {
-                    const float4 v = *reinterpret_cast<const float4 *>(yr + k0);
-                    h[0] = v.x; h[1] = v.y; h[2] = v.z; h[3] = v.w;
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        if (k0 + e >= n2) h[e] = 0.f;   // pitch padding
-                };
-                float mx = 0.f;
-                if (act)
-                    for (int k0 = 4 * sq; k0 < n2; k0 += 4 * TPR) {
-                        float h[4];
-                        unit(k0, h);
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) mx = fmaxf(mx, fabsf(h[e]));
-                    }
-#pragma unroll
-                for (int o = 1; o < TPR; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-                float sc, inv;
-                row_scales(mx, sc, inv);
-                if (act) {
-                    if (sq == 0) rsb2[srow] = inv;
-                    for (int k0 = 4 * sq; k0 < n2; k0 += 4 * TPR) {
-                        float h[4];
-                        const float l[4] = {0.f, 0.f, 0.f, 0.f};
-                        unit(k0, h);
-                        store_digits4(sA, a.a_piece2, img_at(srow, k0 >> 3, sbo2) + uint32_t(k0 & 7) * 2u, h, l, sc);
-                    }
-                }
-            }
-            if (handoff(false)) break;
-            wait_d();
-            // ---- GEMM 2 result -> the field at (z0 + s, j', i') ----
-            {
-                const bool act = drow < R2;
-                const int s = act ? drow / n1 : 0, ip = act ? drow - s * n1 : 0;
-                const float rs = act ? rsb2[drow] : 0.f;
-                float *o = a.out + size_t(p) * a.N + size_t(z0 + s) * R + ip;
-                for (int u4 = dq; u4 < Kp2 / 4; u4 += TPR) {
-                    float v0[4], v1[4];
-                    tmem_pair4(tmem + lane_q + uint32_t(4 * u4), tmem + lane_q + uint32_t(Kp2 + 4 * u4), v0, v1);
-                    const float4 c4 = *reinterpret_cast<const float4 *>(cs2 + 4 * u4);
-                    const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+                    };
+                    float mx = 0.f;
+                    if (act)
+                        for (int k0 = 4 * sq; k0 < n1; k0 += 4 * TPR) {
+                            float h[4], l[4];
+                            unit(k0, h, l, std::false_type{});
+    #pragma unroll
+                            for (int e = 0; e < 4; ++e) mx = fmaxf(mx, fabsf(h[e]));
+                        }
+    #pragma unroll
+                    for (int o = 1; o < TPR; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                    float sc, inv;
+                    row_scales(mx, sc, inv);
                     if (act) {
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int col = 4 * u4 + e;
-                            if (col < n2) o[size_t(col) * n1] = (v0[e] + v1[e]) * (rs * cv[e]);
+                        if (sq == 0) rsb1[srow] = inv;
+                        for (int k0 = 4 * sq; k0 < n1; k0 += 4 * TPR) {
+                            float h[4], l[4];
+                            unit(k0, h, l, std::true_type{});
+                            store_digits4(sA1, a.a_piece1, img_at(srow, k0 >> 3, sbo1) + uint32_t(k0 & 7) * 2u, h, l, sc);
                         }
                     }
                 }
-                tc::tc_fence_before();
+        };
+        auto drain1 = [&](const TileInfo &ti) {
+            const int R1 = ti.R1;
+            wait_d(bar_d1, ph1);
+                // ---- GEMM 1 result -> transposed tile Y[(s, i')][j] ----
+                {
+                    const bool act = drow < R1;
+                    const int s = act ? drow / n2 : 0, j = act ? drow - s * n2 : 0;
+                    const float rs = act ? rsb1[drow] : 0.f;
+                    float *yb = Ysm + size_t(s) * n1 * a.Pj + j;
+                    for (int u4 = dq; u4 < Kp1 / 4; u4 += TPR) {
+                        float v0[4], v1[4];
+                        tmem_pair4(tmem + lane_q + uint32_t(4 * u4), tmem + lane_q + uint32_t(Kp1 + 4 * u4), v0, v1);
+                        const float4 c4 = *reinterpret_cast<const float4 *>(cs1 + 4 * u4);
+                        const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+                        if (act) {
+    #pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const int col = 4 * u4 + e;
+                                if (col < n1) yb[size_t(col) * a.Pj] = (v0[e] + v1[e]) * (rs * cv[e]);
+                            }
+                        }
+                    }
+                    tc::tc_fence_before();
+                }
+        };
+        auto slice2 = [&](const TileInfo &ti) {
+            const int R2 = ti.R2;
+                // ---- GEMM 2 operand: row (s, i'), K = j, from the transposed tile ----
+                {
+                    const bool act = srow < R2;
+                    const float *yr = Ysm + size_t(act ? srow : 0) * a.Pj;
+                    auto unit = [&](int k0, float (&h)[4]) {
+                        const float4 v = *reinterpret_cast<const float4 *>(yr + k0);
+                        h[0] = v.x; h[1] = v.y; h[2] = v.z; h[3] = v.w;
+    #pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (k0 + e >= n2) h[e] = 0.f;   // pitch padding
+                    };
+                    float mx = 0.f;
+                    if (act)
+                        for (int k0 = 4 * sq; k0 < n2; k0 += 4 * TPR) {
+                            float h[4];
+                            unit(k0, h);
+    #pragma unroll
+                            for (int e = 0; e < 4; ++e) mx = fmaxf(mx, fabsf(h[e]));
+                        }
+    #pragma unroll
+                    for (int o = 1; o < TPR; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                    float sc, inv;
+                    row_scales(mx, sc, inv);
+                    if (act) {
+                        if (sq == 0) rsb2[srow] = inv;
+                        for (int k0 = 4 * sq; k0 < n2; k0 += 4 * TPR) {
+                            float h[4];
+                            const float l[4] = {0.f, 0.f, 0.f, 0.f};
+                            unit(k0, h);
+                            store_digits4(sA2, a.a_piece2, img_at(srow, k0 >> 3, sbo2) + uint32_t(k0 & 7) * 2u, h, l, sc);
+                        }
+                    }
+                }
+        };
+        auto drain2 = [&](const TileInfo &ti) {
+            const long p = ti.p;
+            const int z0 = ti.z0, R2 = ti.R2;
+            wait_d(bar_d2, ph2);
+                // ---- GEMM 2 result -> the field at (z0 + s, j', i') ----
+                {
+                    const bool act = drow < R2;
+                    const int s = act ? drow / n1 : 0, ip = act ? drow - s * n1 : 0;
+                    const float rs = act ? rsb2[drow] : 0.f;
+                    float *o = a.out + size_t(p) * a.N + size_t(z0 + s) * R + ip;
+                    for (int u4 = dq; u4 < Kp2 / 4; u4 += TPR) {
+                        float v0[4], v1[4];
+                        tmem_pair4(tmem + lane_q + uint32_t(a.t2col + 4 * u4), tmem + lane_q + uint32_t(a.t2col + Kp2 + 4 * u4), v0, v1);
+                        const float4 c4 = *reinterpret_cast<const float4 *>(cs2 + 4 * u4);
+                        const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+                        if (act) {
+    #pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const int col = 4 * u4 + e;
+                                if (col < n2) o[size_t(col) * n1] = (v0[e] + v1[e]) * (rs * cv[e]);
+                            }
+                        }
+                    }
+                    tc::tc_fence_before();
+                }
+        };
+        if (!a.pipe) {
+            long it = 0;
+            for (long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
+                const TileInfo ti = info(tile);
+                slice1(ti, it);
+                if (handoff(true)) break;
+                drain1(ti);
+                tc::bar_sync(1, NT);
+                slice2(ti);
+                if (handoff(false)) break;
+                drain2(ti);
             }
+        } else {
+            // GEMM 1 of tile t runs while the threads drain GEMM 2 of tile t-1; GEMM 2 of t
+            // runs while they cut the first operand of tile t+1
+            long it = 0;
+            long tile = blockIdx.x;
+            bool have_prev = false, stop = false;
+            TileInfo prev{};
+            if (tile < a.ntiles) {
+                slice1(info(tile), it);
+                stop = handoff(true);
+            }
+            for (; tile < a.ntiles && !stop; tile += gridDim.x, ++it) {
+                const TileInfo ti = info(tile);
+                if (have_prev) drain2(prev);
+                drain1(ti);
+                tc::bar_sync(1, NT);
+                slice2(ti);
+                if ((stop = handoff(false))) break;
+                const long next = tile + gridDim.x;
+                if (next < a.ntiles) {
+                    slice1(info(next), it + 1);
+                    if ((stop = handoff(true))) break;
+                }
+                prev = ti;
+                have_prev = true;
+            }
+            if (!stop && have_prev) drain2(prev);
         }
     }
     tc::tc_fence_before();
@@ -847,12 +912,13 @@ void build_block(uint8_t *img, int WN, int Kp, int n0, int nout, int nk, Coef co
 
 struct SliceLayout {
     size_t smem;
-    uint32_t offB2, offA, offY, offRs, offBar, a_piece1, a_piece2, offS, stg_plane;
-    int G, Pj, tmem_cols, stage;
+    uint32_t offB2, offA, offA2, offY, offRs, offBar, a_piece1, a_piece2, offS, stg_plane;
+    int G, Pj, tmem_cols, stage, pipe, t2col;
 };
 
-// pair: pass A (two staged planes) or pass C (one)
-SliceLayout slice_layout(const Plan &P, bool pair = true)
+// pair: pass A (two staged planes) or pass C (one).  pipe: separate A images and TMEM
+// columns for the two GEMMs (software pipeline over tiles, one CTA per SM with staging).
+SliceLayout slice_layout_for(const Plan &P, bool pair, bool pipe)
 {
     SliceLayout L{};
     const int n1 = P.n[0], n2 = P.n[1];
@@ -873,15 +939,23 @@ SliceLayout slice_layout(const Plan &P, bool pair = true)
     const int R1 = L.G * n2, R2 = L.G * n1;
     L.a_piece1 = uint32_t(pad8i(R1)) * Kp1 * 2u;
     L.a_piece2 = uint32_t(pad8i(R2)) * Kp2 * 2u;
-    const size_t abytes = std::max(3 * size_t(L.a_piece1), 3 * size_t(L.a_piece2));
     // the MMA reads 128 rows of every digit plane: the last plane's reach past the image
     // must stay inside this CTA's shared memory (rows past the tile are never read back)
-    const size_t reach = std::max(2 * size_t(L.a_piece1) + size_t(kRows) * Kp1 * 2,
-                                  2 * size_t(L.a_piece2) + size_t(kRows) * Kp2 * 2);
-    off += abytes;
+    const size_t reach1 = 2 * size_t(L.a_piece1) + size_t(kRows) * Kp1 * 2;
+    const size_t reach2 = 2 * size_t(L.a_piece2) + size_t(kRows) * Kp2 * 2;
+    size_t end_reach;
+    if (pipe) {
+        L.offA2 = uint32_t(align_up(L.offA + 3 * size_t(L.a_piece1), 1024));
+        off = L.offA2 + 3 * size_t(L.a_piece2);
+        end_reach = std::max(L.offA + reach1, L.offA2 + reach2);
+    } else {
+        L.offA2 = L.offA;
+        off += std::max(3 * size_t(L.a_piece1), 3 * size_t(L.a_piece2));
+        end_reach = L.offA + std::max(reach1, reach2);
+    }
     L.offY = uint32_t(align_up(off, 16));
     off = L.offY + (size_t(L.G) * n1 * L.Pj + 8) * 4;
-    off = std::max(off, size_t(L.offA) + reach);
+    off = std::max(off, end_reach);
     L.offRs = uint32_t(align_up(off, 16));
     off = L.offRs + 2 * kRows * 4;
     L.offBar = uint32_t(align_up(off, 16));
@@ -892,13 +966,30 @@ SliceLayout slice_layout(const Plan &P, bool pair = true)
     L.offS = uint32_t(align_up(off, 128));
     const size_t with_stage = L.offS + size_t(pair ? 2 : 1) * L.stg_plane;
     // staging hides the load latency of one CTA per SM; a second CTA per SM hides it too,
-    // so the buffer is used only where it does not cost that second CTA
+    // so the buffer is used only where it does not cost that second CTA (and always when
+    // pipelined: one CTA per SM by design)
     const size_t two_per_sm = 233472 / 2 - 1024;
-    L.stage = (R % 4 == 0 && with_stage <= kSmemLimit && (with_stage <= two_per_sm || off > two_per_sm)) ? 1 : 0;
+    L.stage = (R % 4 == 0 && with_stage <= kSmemLimit &&
+               (pipe || with_stage <= two_per_sm || off > two_per_sm)) ? 1 : 0;
     if (P.t3_stage >= 0) L.stage = (P.t3_stage && R % 4 == 0 && with_stage <= kSmemLimit) ? 1 : 0;   // tuned
     L.smem = L.stage ? with_stage : off;
-    L.tmem_cols = tmem_pow2(2 * std::max(Kp1, Kp2));
+    L.pipe = pipe ? 1 : 0;
+    L.t2col = pipe ? 2 * Kp1 : 0;
+    L.tmem_cols = tmem_pow2(pipe ? 2 * Kp1 + 2 * Kp2 : 2 * std::max(Kp1, Kp2));
     return L;
+}
+
+// The plan's choice: pipelined when tuned so, or (automatic) when it fits and the serial form
+// cannot run two CTAs per SM.
+SliceLayout slice_layout(const Plan &P, bool pair = true)
+{
+    const SliceLayout ser = slice_layout_for(P, pair, false);
+    const SliceLayout pip = slice_layout_for(P, pair, true);
+    const bool pip_ok = pip.smem <= kSmemLimit && pip.tmem_cols <= 512;
+    if (P.t3_pipe == 1 && pip_ok) return pip;
+    if (P.t3_pipe == 0 || !pip_ok) return ser;
+    const bool ser_two = ser.smem + 1024 <= 233472 / 2 && ser.tmem_cols <= 256;
+    return ser_two ? ser : pip;
 }
 
 struct ZLayout {
@@ -1115,6 +1206,9 @@ int tc3_solve_batch(Plan &P, const int2 *pairs_d, int nfields, float *bufA, floa
         a.stage = L.stage;
         a.offS = L.offS;
         a.stg_plane = L.stg_plane;
+        a.pipe = L.pipe;
+        a.offA2 = L.offA2;
+        a.t2col = L.t2col;
         a.err = static_cast<int *>(P.err_d.p);
         size_t smem = L.smem;
         auto kern = pair ? slice_pass_kernel<true, kTPRs> : slice_pass_kernel<false, kTPRs>;

@@ -143,3 +143,42 @@ def test_bf16x7_slab_grid_sampled_columns(exx, slab64):
     orc, ref = _oracle(s, cols=cols)
     got = vx.cpu().numpy()[cols]
     assert pm.rel(got, ref) < TOL_V
+
+
+FORMS = [dict(pipeline=1, staging=-1), dict(pipeline=1, staging=0), dict(pipeline=0, staging=1),
+         dict(pipeline=0, staging=0)]
+
+
+@pytest.mark.parametrize("form", FORMS, ids=lambda f: f"pipe{f['pipeline']}_stage{f['staging']}")
+@pytest.mark.parametrize("case", [dict(n=(14, 12, 10), bc=(0, 1, 0), n_orb=6, kernel=0),
+                                  dict(n=(24, 24, 9), bc=(1, 0, 1), n_orb=5, kernel=0),
+                                  dict(n=(17, 19, 23), bc=(0, 0, 0), n_orb=7, kernel=0)],
+                         ids=lambda c: "x".join(map(str, c["n"])))
+def test_bf16x7_slice_forms(exx, case, form):
+    """Every form of the slice passes (software-pipelined over tiles or serial; input staged
+    through shared memory or loaded directly) gives the same results within the targets."""
+    s = synth.small_system(h=0.4, seed=21, **case)
+    plan = exx.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    plan.set_precision(exx.EXX_PREC_BF16X7)
+    plan.set_tuning(pairs_per_batch=4 if form["pipeline"] else 0, **form)
+    psi = torch.from_numpy(s.psi).cuda()
+    f = torch.from_numpy(s.f).cuda()
+    vx = plan.apply(psi[:s.n_occ], f, psi)
+    e = plan.energy(psi[:s.n_occ], f, vx)
+    orc, ref = _oracle(s)
+    e_ref = orc.energy(s.psi[:s.n_occ], s.f, ref)
+    assert pm.rel(vx.cpu().numpy(), ref) < TOL_V
+    assert abs(e - e_ref) < TOL_E * abs(e_ref)
+
+
+def test_bf16x7_slab_grid_pipelined(exx, slab64):
+    s = slab64
+    plan = exx.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    plan.set_precision(exx.EXX_PREC_BF16X7)
+    plan.set_tuning(pipeline=1)
+    psi = torch.from_numpy(s.psi).cuda()
+    f = torch.from_numpy(s.f).cuda()
+    vx = plan.apply(psi[:s.n_occ], f, psi)
+    cols = [5, 60]
+    orc, ref = _oracle(s, cols=cols)
+    assert pm.rel(vx.cpu().numpy()[cols], ref) < TOL_V
