@@ -74,15 +74,28 @@ __device__ __forceinline__ float rnd_grid(float x)
     return __fadd_rn(__fadd_rn(x, kMagic), -kMagic);
 }
 
-// Three base-512 digits of (hi + lo) * s, |hi s| < 256: every residual is exact, lo enters
-// once (one FMA rounding, far below the last digit).
-__device__ __forceinline__ void digits3(float hi, float lo, float s, float &d0, float &d1, float &d2)
+// Three base-512 digits of (hi + lo) * s, |hi s| < 256, for two elements at once: every
+// residual is exact and lo enters once (one FMA rounding, far below the last digit).  The
+// packed FP32x2 instructions of sm_100+ take one issue slot for both lanes (the issue rate,
+// not the FP32 pipe, bounds these kernels); each rounds as its scalar form, and a - b is
+// written fma(b, -1, a), which rounds once like the subtraction.
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.f), a); }
+template <int G>
+__device__ __forceinline__ float2 rnd_grid2(float2 x)
 {
-    const float t = hi * s;
-    d0 = rnd_grid<0>(t);
-    const float r1 = fmaf(lo, s, t - d0);
-    d1 = rnd_grid<9>(r1);
-    d2 = rnd_grid<18>(r1 - d1);
+    constexpr float kMagic = 12582912.f / float(1u << G);
+    return __fadd2_rn(__fadd2_rn(x, f2(kMagic)), f2(-kMagic));
+}
+template <bool LO>
+__device__ __forceinline__ void digits3x2(float2 hi, float2 lo, float2 s, float2 &d0, float2 &d1, float2 &d2)
+{
+    const float2 t = __fmul2_rn(hi, s);
+    d0 = rnd_grid2<0>(t);
+    const float2 r0 = sub2(t, d0);
+    const float2 r1 = LO ? __ffma2_rn(lo, s, r0) : r0;
+    d1 = rnd_grid2<9>(r1);
+    d2 = rnd_grid2<18>(sub2(r1, d1));
 }
 
 // Row scale s = 2^(8 - e) and its inverse, with m = f 2^e, f in [0.5, 1): |x s| < 256.
@@ -123,15 +136,20 @@ __device__ __forceinline__ void issue_x7(uint32_t d_lead, uint32_t d_rest, uint3
 
 // Digits of four consecutive elements (hi + lo) * s of one row: 8 bytes in each of the three
 // digit planes (plane stride `piece`) at byte offset o.
+// LO = false: l is zero and skipped.
+template <bool LO = true>
 __device__ __forceinline__ void store_digits4(uint8_t *img, uint32_t piece, uint32_t o, const float (&h)[4],
                                               const float (&l)[4], float s)
 {
-    float d[3][4];
+    float2 d[3][2];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) digits3(h[e], l[e], s, d[0][e], d[1][e], d[2][e]);
+    for (int e = 0; e < 2; ++e)
+        digits3x2<LO>(make_float2(h[2 * e], h[2 * e + 1]), make_float2(l[2 * e], l[2 * e + 1]), f2(s), d[0][e],
+                      d[1][e], d[2][e]);
 #pragma unroll
     for (int q = 0; q < 3; ++q)
-        *reinterpret_cast<uint2 *>(img + q * piece + o) = make_uint2(pack2(d[q][0], d[q][1]), pack2(d[q][2], d[q][3]));
+        *reinterpret_cast<uint2 *>(img + q * piece + o) =
+            make_uint2(pack2(d[q][0].x, d[q][0].y), pack2(d[q][1].x, d[q][1].y));
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
@@ -164,6 +182,19 @@ __device__ __forceinline__ void tmem_pair4(uint32_t lead, uint32_t rest, float (
         a[e] = __uint_as_float(r0[e]);
         b[e] = __uint_as_float(r1[e]);
     }
+}
+
+// One drained unit: (lead + rest) * (rs * cs[e]) for four consecutive columns.
+__device__ __forceinline__ void tmem_unit(uint32_t lead, uint32_t rest, float rs, const float *cs, float (&v)[4])
+{
+    float v0[4], v1[4];
+    tmem_pair4(lead, rest, v0, v1);
+    const float4 c4 = *reinterpret_cast<const float4 *>(cs);
+    const float2 w01 = __fmul2_rn(__fadd2_rn(make_float2(v0[0], v0[1]), make_float2(v1[0], v1[1])),
+                                  __fmul2_rn(f2(rs), make_float2(c4.x, c4.y)));
+    const float2 w23 = __fmul2_rn(__fadd2_rn(make_float2(v0[2], v0[3]), make_float2(v1[2], v1[3])),
+                                  __fmul2_rn(f2(rs), make_float2(c4.z, c4.w)));
+    v[0] = w01.x; v[1] = w01.y; v[2] = w23.x; v[3] = w23.y;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -376,13 +407,18 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 2) slice_pass_kernel(const _
                             }
                         }
     #pragma unroll
-                        for (int e = 0; e < 4; ++e) {
+                        for (int e = 0; e < 2; ++e) {
                             if (PAIR) {
-                                h[e] = u0[e] * u1[e];
-                                l[e] = decltype(LO)::value ? fmaf(u0[e], u1[e], -h[e]) : 0.f;
+                                const float2 x = make_float2(u0[2 * e], u0[2 * e + 1]);
+                                const float2 y = make_float2(u1[2 * e], u1[2 * e + 1]);
+                                const float2 hh = __fmul2_rn(x, y);
+                                const float2 ll = decltype(LO)::value ? __ffma2_rn(x, y, __fmul2_rn(hh, f2(-1.f)))
+                                                                      : f2(0.f);
+                                h[2 * e] = hh.x; h[2 * e + 1] = hh.y;
+                                l[2 * e] = ll.x; l[2 * e + 1] = ll.y;
                             } else {
-                                h[e] = u0[e];
-                                l[e] = 0.f;
+                                h[2 * e] = u0[2 * e]; h[2 * e + 1] = u0[2 * e + 1];
+                                l[2 * e] = 0.f; l[2 * e + 1] = 0.f;
                             }
                         }
                     };
@@ -403,7 +439,7 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 2) slice_pass_kernel(const _
                         for (int k0 = 4 * sq; k0 < n1; k0 += 4 * TPR) {
                             float h[4], l[4];
                             unit(k0, h, l, std::true_type{});
-                            store_digits4(sA1, a.a_piece1, img_at(srow, k0 >> 3, sbo1) + uint32_t(k0 & 7) * 2u, h, l, sc);
+                            store_digits4<PAIR>(sA1, a.a_piece1, img_at(srow, k0 >> 3, sbo1) + uint32_t(k0 & 7) * 2u, h, l, sc);
                         }
                     }
                 }
@@ -417,16 +453,16 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 2) slice_pass_kernel(const _
                     const int s = act ? drow / n2 : 0, j = act ? drow - s * n2 : 0;
                     const float rs = act ? rsb1[drow] : 0.f;
                     float *yb = Ysm + size_t(s) * n1 * a.Pj + j;
-                    for (int u4 = dq; u4 < Kp1 / 4; u4 += TPR) {
-                        float v0[4], v1[4];
-                        tmem_pair4(tmem + lane_q + uint32_t(4 * u4), tmem + lane_q + uint32_t(Kp1 + 4 * u4), v0, v1);
-                        const float4 c4 = *reinterpret_cast<const float4 *>(cs1 + 4 * u4);
-                        const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+                    const int nu = quarter * 32 < R1 ? Kp1 / 4 : 0;   // uniform: quarters without rows skip
+                    for (int u4 = dq; u4 < nu; u4 += TPR) {
+                        float v[4];
+                        tmem_unit(tmem + lane_q + uint32_t(4 * u4), tmem + lane_q + uint32_t(Kp1 + 4 * u4), rs,
+                                  cs1 + 4 * u4, v);
                         if (act) {
     #pragma unroll
                             for (int e = 0; e < 4; ++e) {
                                 const int col = 4 * u4 + e;
-                                if (col < n1) yb[size_t(col) * a.Pj] = (v0[e] + v1[e]) * (rs * cv[e]);
+                                if (col < n1) yb[size_t(col) * a.Pj] = v[e];
                             }
                         }
                     }
@@ -464,7 +500,7 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 2) slice_pass_kernel(const _
                             float h[4];
                             const float l[4] = {0.f, 0.f, 0.f, 0.f};
                             unit(k0, h);
-                            store_digits4(sA2, a.a_piece2, img_at(srow, k0 >> 3, sbo2) + uint32_t(k0 & 7) * 2u, h, l, sc);
+                            store_digits4<false>(sA2, a.a_piece2, img_at(srow, k0 >> 3, sbo2) + uint32_t(k0 & 7) * 2u, h, l, sc);
                         }
                     }
                 }
@@ -479,16 +515,16 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 2) slice_pass_kernel(const _
                     const int s = act ? drow / n1 : 0, ip = act ? drow - s * n1 : 0;
                     const float rs = act ? rsb2[drow] : 0.f;
                     float *o = a.out + size_t(p) * a.N + size_t(z0 + s) * R + ip;
-                    for (int u4 = dq; u4 < Kp2 / 4; u4 += TPR) {
-                        float v0[4], v1[4];
-                        tmem_pair4(tmem + lane_q + uint32_t(a.t2col + 4 * u4), tmem + lane_q + uint32_t(a.t2col + Kp2 + 4 * u4), v0, v1);
-                        const float4 c4 = *reinterpret_cast<const float4 *>(cs2 + 4 * u4);
-                        const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+                    const int nu = quarter * 32 < R2 ? Kp2 / 4 : 0;
+                    for (int u4 = dq; u4 < nu; u4 += TPR) {
+                        float v[4];
+                        tmem_unit(tmem + lane_q + uint32_t(a.t2col + 4 * u4),
+                                  tmem + lane_q + uint32_t(a.t2col + Kp2 + 4 * u4), rs, cs2 + 4 * u4, v);
                         if (act) {
     #pragma unroll
                             for (int e = 0; e < 4; ++e) {
                                 const int col = 4 * u4 + e;
-                                if (col < n2) o[size_t(col) * n1] = (v0[e] + v1[e]) * (rs * cv[e]);
+                                if (col < n2) o[size_t(col) * n1] = v[e];
                             }
                         }
                     }
@@ -770,7 +806,7 @@ __global__ void __launch_bounds__(kRows * TPR + 64, (UPT <= 4 ? 2 : 1)) zpass_ke
                     const int z0 = 4 * (dq + g * TPR);
                     if (z0 < n3) {
                         const float l[4] = {0.f, 0.f, 0.f, 0.f};
-                        store_digits4(sA, a_piece, img_at(row, z0 >> 3, sbo) + uint32_t(z0 & 7) * 2u, x[g], l, sc);
+                        store_digits4<false>(sA, a_piece, img_at(row, z0 >> 3, sbo) + uint32_t(z0 & 7) * 2u, x[g], l, sc);
                     }
                 }
             }
@@ -799,20 +835,32 @@ __global__ void __launch_bounds__(kRows * TPR + 64, (UPT <= 4 ? 2 : 1)) zpass_ke
                 const int c0 = 4 * u4;
                 if (!act || c0 >= n3) continue;
                 uint32_t lo16[4], hi16[4], lb[4];
+                const float4 cf4 = *reinterpret_cast<const float4 *>(csF + c0);
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const float scl = rs_f * csF[c0 + e];
-                    const float h0 = v0[e] + v1[e];
-                    const float bp = h0 - v0[e];
-                    const float l0 = ((v0[e] - (h0 - bp)) + (v1[e] - bp)) * scl;
-                    const float h = h0 * scl;
-                    const float prh = h * fh[g][e];   // zero past n3 (f = 0 there)
-                    const float prl = fmaf(h, fh[g][e], -prh) + fmaf(h, fl[g][e], l0 * fh[g][e]);
-                    mx2 = fmaxf(mx2, fabsf(prh));
-                    const uint32_t hb = __float_as_uint(prh);
-                    lo16[e] = hb & 0xffffu;
-                    hi16[e] = hb >> 16;
-                    lb[e] = uint32_t(__bfloat16_as_ushort(__float2bfloat16_rn(prl)));
+                for (int e2 = 0; e2 < 2; ++e2) {
+                    // TwoSum of the accumulators, times the scales, times f (hi and lo)
+                    const float2 a0 = make_float2(v0[2 * e2], v0[2 * e2 + 1]);
+                    const float2 a1 = make_float2(v1[2 * e2], v1[2 * e2 + 1]);
+                    const float2 fhh = make_float2(fh[g][2 * e2], fh[g][2 * e2 + 1]);
+                    const float2 fll = make_float2(fl[g][2 * e2], fl[g][2 * e2 + 1]);
+                    const float2 scl = __fmul2_rn(f2(rs_f), e2 ? make_float2(cf4.z, cf4.w) : make_float2(cf4.x, cf4.y));
+                    const float2 h0 = __fadd2_rn(a0, a1);
+                    const float2 bp = sub2(h0, a0);
+                    const float2 l0 = __fmul2_rn(__fadd2_rn(sub2(a0, sub2(h0, bp)), sub2(a1, bp)), scl);
+                    const float2 h = __fmul2_rn(h0, scl);
+                    const float2 prh = __fmul2_rn(h, fhh);   // zero past n3 (f = 0 there)
+                    const float2 prl = __fadd2_rn(__ffma2_rn(h, fhh, __fmul2_rn(prh, f2(-1.f))),
+                                                  __ffma2_rn(h, fll, __fmul2_rn(l0, fhh)));
+                    const float ph[2] = {prh.x, prh.y}, pl[2] = {prl.x, prl.y};
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const int e = 2 * e2 + q;
+                        mx2 = fmaxf(mx2, fabsf(ph[q]));
+                        const uint32_t hb = __float_as_uint(ph[q]);
+                        lo16[e] = hb & 0xffffu;
+                        hi16[e] = hb >> 16;
+                        lb[e] = uint32_t(__bfloat16_as_ushort(__float2bfloat16_rn(pl[q])));
+                    }
                 }
                 const uint32_t o = img_at(row, c0 >> 3, sbo) + uint32_t(c0 & 7) * 2u;
                 *reinterpret_cast<uint2 *>(sA + o) = make_uint2(lo16[0] | (lo16[1] << 16), lo16[2] | (lo16[3] << 16));
@@ -854,13 +902,13 @@ __global__ void __launch_bounds__(kRows * TPR + 64, (UPT <= 4 ? 2 : 1)) zpass_ke
             for (int g = 0; g < UPT; ++g) {
                 const int u4 = dq + g * TPR;
                 if (u4 >= a.NC / 4) break;
-                float v0[4], v1[4];
-                tmem_pair4(tmem + lane_q + uint32_t(4 * u4), tmem + lane_q + uint32_t(a.NC + 4 * u4), v0, v1);
+                float v[4];
+                tmem_unit(tmem + lane_q + uint32_t(4 * u4), tmem + lane_q + uint32_t(a.NC + 4 * u4), rs_i, csI + 4 * u4, v);
                 if (!act) continue;
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const int z = 4 * u4 + e;
-                    if (z < n3) dst[size_t(z) * R] = (v0[e] + v1[e]) * (rs_i * csI[z]);
+                    if (z < n3) dst[size_t(z) * R] = v[e];
                 }
             }
             tc::tc_fence_before();
