@@ -37,11 +37,12 @@ int exx_debug_tc_gemm(int tf32, int n, int k, const float *A, const float *B, fl
  * (field, row in field) (Granlund & Montgomery 1994, Fig. 4.1), host-side.  d >= 1. */
 int exx_debug_fastdiv(unsigned d, int count, const unsigned *n, unsigned *q);
 
-/* Failure detection without a fault: launches one kernel whose mbarrier wait (the same
- * bounded wait the pass kernels use) polls a barrier that nothing completes.  The poll
- * limit runs out, the kernel records it in an error word and returns; *status_h is then
- * EXX_ERR_TIMEOUT (EXX_OK would mean the wait completed).  The context stays usable.
- * Returns EXX_ERR_CUDA without a GPU. */
+/* Failure detection without a fault: launches one kernel whose two mbarrier waits (the
+ * same bounded waits the pass kernels use: the polled one of the five-pass kernels, 4096
+ * polls, and the wall-time one of the three-pass kernels, here 2 ms) wait on a barrier that
+ * nothing completes.  Each limit runs out, the kernel records it in an error word and
+ * returns; *status_h is then EXX_ERR_TIMEOUT when both waits gave up (EXX_OK otherwise).
+ * The context stays usable.  Returns EXX_ERR_CUDA without a GPU. */
 int exx_debug_wait_timeout(int *status_h);
 
 #ifdef __cplusplus

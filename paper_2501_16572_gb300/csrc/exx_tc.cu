@@ -1622,14 +1622,16 @@ int tc_check_error(Plan &P, cudaStream_t s)
 }
 
 namespace {
-// The bounded wait of the pass kernels on a barrier that nothing completes: the poll limit
-// runs out, the kernel records the timeout in the error word and returns normally.
-__global__ void tc_wait_timeout_kernel(uint32_t limit, int *err)
+// The bounded waits of the pass kernels on a barrier that nothing completes: the poll limit
+// (five-pass kernels) or the wall-time limit (three-pass kernels) runs out, the kernel
+// records the timeout in the error word (bit 0: polled wait, bit 1: timed wait) and returns.
+__global__ void tc_wait_timeout_kernel(uint32_t limit, uint64_t limit_ns, int *err)
 {
     __shared__ uint64_t bar;
     if (threadIdx.x == 0) tc::mbar_init(&bar, 1);
     __syncthreads();
-    if (!tc::mbar_wait_bounded(&bar, 0, limit) && threadIdx.x == 0) atomicExch(err, 1);
+    if (!tc::mbar_wait_bounded(&bar, 0, limit) && threadIdx.x == 0) atomicOr(err, 1);
+    if (!tc::mbar_wait_timed(&bar, 0, limit_ns) && threadIdx.x == 0) atomicOr(err, 2);
 }
 }  // namespace
 
@@ -1639,15 +1641,16 @@ int tc_wait_timeout_probe(int *status_h)
     EXX_CUDA(cudaMalloc(&err, sizeof(int)));
     cudaError_t e = cudaMemset(err, 0, sizeof(int));
     if (e == cudaSuccess) {
-        tc_wait_timeout_kernel<<<1, 32>>>(1u << 12, err);
+        tc_wait_timeout_kernel<<<1, 32>>>(1u << 12, 2000000ull, err);
         e = cudaGetLastError();
     }
     int h = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost);
     cudaFree(err);
     if (e != cudaSuccess) return cuda_fail(e, "tc_wait_timeout_probe");
-    *status_h = h ? EXX_ERR_TIMEOUT : EXX_OK;
-    if (h) set_error("a bounded mbarrier wait ran out (wait-timeout probe)");
+    // both waits must give up: status EXX_ERR_TIMEOUT only when both did
+    *status_h = h == 3 ? EXX_ERR_TIMEOUT : EXX_OK;
+    if (h == 3) set_error("both bounded mbarrier waits ran out (wait-timeout probe)");
     return EXX_OK;
 }
 

@@ -44,7 +44,7 @@ namespace exx {
 namespace {
 
 constexpr int kRows = 128;              // tile rows = TMEM lanes
-constexpr uint32_t kWaitLimit = 1u << 22;
+constexpr uint64_t kWaitNs = 1000000000ull;   // every barrier wait gives up after 1 s
 constexpr int kMatDig = 4;              // digits of the 1D matrices
 constexpr size_t kSmemLimit = 232448;   // dynamic shared memory per CTA (227 KB)
 
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 2) slice_pass_kernel(const _
         if (a.stage && lane == 0) {
             long it = 0;
             for (long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
-                if (it > 0 && !tc::mbar_wait_bounded(stg_empty, uint32_t((it - 1) & 1), kWaitLimit)) {
+                if (it > 0 && !tc::mbar_wait_timed(stg_empty, uint32_t((it - 1) & 1), kWaitNs)) {
                     atomicExch(sflag, 1);
                     break;
                 }
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 2) slice_pass_kernel(const _
                 }
             }
             // no copy may still target shared memory at exit: the last fill has landed
-            if (it > 0 && !tc::mbar_wait_bounded(stg_full, uint32_t((it - 1) & 1), kWaitLimit)) atomicExch(sflag, 1);
+            if (it > 0 && !tc::mbar_wait_timed(stg_full, uint32_t((it - 1) & 1), kWaitNs)) atomicExch(sflag, 1);
         }
     } else if (warp == NT / 32) {
         // ---- MMA warp: two GEMMs per tile, each after the compute threads' hand-off ----
@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 2) slice_pass_kernel(const _
         bool bad = false;
         for (long tile = blockIdx.x; tile < a.ntiles && !bad; tile += gridDim.x) {
             for (int g = 0; g < 2 && !bad; ++g) {
-                if (!tc::mbar_wait_bounded(bar_a, ph, kWaitLimit)) {
+                if (!tc::mbar_wait_timed(bar_a, ph, kWaitNs)) {
                     atomicExch(sflag, 1);
                     bad = true;
                 }
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 2) slice_pass_kernel(const _
             return stop;
         };
         auto wait_d = [&](uint64_t *bar, uint32_t &ph) {
-            if (!tc::mbar_wait_bounded(bar, ph, kWaitLimit)) atomicExch(sflag, 1);
+            if (!tc::mbar_wait_timed(bar, ph, kWaitNs)) atomicExch(sflag, 1);
             ph ^= 1u;
             tc::tc_fence_after();
         };
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 2) slice_pass_kernel(const _
                     const size_t off = size_t(z0 + s) * R + size_t(j) * n1;
                     const float *x0, *x1 = nullptr;
                     if (a.stage) {   // rows of this tile's slices in the staging buffer
-                        if (!tc::mbar_wait_bounded(stg_full, uint32_t(it & 1), kWaitLimit)) atomicExch(sflag, 1);
+                        if (!tc::mbar_wait_timed(stg_full, uint32_t(it & 1), kWaitNs)) atomicExch(sflag, 1);
                         const size_t so = size_t(s) * R + size_t(j) * n1;
                         x0 = stg + so;
                         x1 = reinterpret_cast<const float *>(reinterpret_cast<const uint8_t *>(stg) + a.stg_plane) + so;
@@ -681,7 +681,7 @@ __global__ void __launch_bounds__(kRows * TPR + 64, (UPT <= 4 ? 2 : 1)) zpass_ke
                     bulk_load(sB + size_t(j) * a.blk_bytes, block_src(j), a.blk_bytes, bfull + j);
                 }
                 for (int j = 0; j < 2 * NB; ++j)   // no copy may still target shared memory at exit
-                    if (!tc::mbar_wait_bounded(bfull + j, 0, kWaitLimit)) atomicExch(sflag, 1);
+                    if (!tc::mbar_wait_timed(bfull + j, 0, kWaitNs)) atomicExch(sflag, 1);
             } else {
                 long seq = 0;
                 bool bad = false;
@@ -689,7 +689,7 @@ __global__ void __launch_bounds__(kRows * TPR + 64, (UPT <= 4 ? 2 : 1)) zpass_ke
                     for (int j = 0; j < 2 * NB; ++j, ++seq) {
                         const int slot = int(seq % a.nbuf);
                         const long use = seq / a.nbuf;
-                        if (use > 0 && !tc::mbar_wait_bounded(bempty + slot, uint32_t((use - 1) & 1), kWaitLimit)) {
+                        if (use > 0 && !tc::mbar_wait_timed(bempty + slot, uint32_t((use - 1) & 1), kWaitNs)) {
                             atomicExch(sflag, 1);
                             bad = true;
                             break;
@@ -701,7 +701,7 @@ __global__ void __launch_bounds__(kRows * TPR + 64, (UPT <= 4 ? 2 : 1)) zpass_ke
                 // every issued copy has landed before exit: the last fill of each slot
                 for (int slot = 0; slot < a.nbuf; ++slot) {
                     const long nf = seq > slot ? (seq - 1 - slot) / a.nbuf + 1 : 0;   // fills of this slot
-                    if (nf > 0 && !tc::mbar_wait_bounded(bfull + slot, uint32_t((nf - 1) & 1), kWaitLimit))
+                    if (nf > 0 && !tc::mbar_wait_timed(bfull + slot, uint32_t((nf - 1) & 1), kWaitNs))
                         atomicExch(sflag, 1);
                 }
             }
@@ -716,7 +716,7 @@ __global__ void __launch_bounds__(kRows * TPR + 64, (UPT <= 4 ? 2 : 1)) zpass_ke
         bool first = true;
         for (long tile = blockIdx.x; tile < a.ntiles && !bad; tile += gridDim.x) {
             for (int g = 0; g < 2 && !bad; ++g) {
-                if (!tc::mbar_wait_bounded(bar_a, ph, kWaitLimit)) {
+                if (!tc::mbar_wait_timed(bar_a, ph, kWaitNs)) {
                     atomicExch(sflag, 1);
                     bad = true;
                 }
@@ -736,7 +736,7 @@ __global__ void __launch_bounds__(kRows * TPR + 64, (UPT <= 4 ? 2 : 1)) zpass_ke
                         par = uint32_t((seq / a.nbuf) & 1);
                         need = true;
                     }
-                    if (need && !tc::mbar_wait_bounded(bfull + slot, par, kWaitLimit)) {
+                    if (need && !tc::mbar_wait_timed(bfull + slot, par, kWaitNs)) {
                         atomicExch(sflag, 1);
                         bad = true;
                         break;
@@ -780,7 +780,7 @@ __global__ void __launch_bounds__(kRows * TPR + 64, (UPT <= 4 ? 2 : 1)) zpass_ke
             return stop;
         };
         auto wait_d = [&]() {
-            if (!tc::mbar_wait_bounded(bar_d, ph, kWaitLimit)) atomicExch(sflag, 1);
+            if (!tc::mbar_wait_timed(bar_d, ph, kWaitNs)) atomicExch(sflag, 1);
             ph ^= 1u;
             tc::tc_fence_after();
         };
