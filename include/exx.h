@@ -126,8 +126,8 @@ int exx_plan_set_shard(exx_plan plan, int rank, int world);
  * shapes), measured on this grid with the caller's own data: exx_apply's arguments and
  * rules (out is used as scratch and left holding partial results).  Coordinate descent over
  *   pairs per batch {default, 256, 512, 1024} x orbitals per pair block {8, 16}, then, in
- *   the BF16X7 mode, the pass-B matrix block width and shared-memory buffer count (every
- *   choice that fits), then the slice passes' form (serial with up to two CTAs per SM, or
+ *   the BF16X7 mode, the pass-B matrix streaming (output blocks or K-chunks, their width
+ *   and shared-memory buffer count: every choice that fits), then the slice passes' form (serial with up to two CTAs per SM, or
  *   software-pipelined over tiles with one CTA per SM) with their input staging (auto, off, on);
  * each candidate runs up to three batches of the pair schedule twice (warm-up, then timed
  * with CUDA events on `stream`); the fastest per pair solve is kept in the plan (as by
@@ -139,13 +139,15 @@ int exx_plan_autotune(exx_plan plan, const double *Psi_occ, int n_occ, long ld_o
                       const double *Psi_in, int n_in, long ld_in, double *out, long ld_out, int flags,
                       exx_stream_t stream);
 
-/* The plan's settings (HOST int[6]: pairs per batch, orbitals per block, pass-B block width,
+/* The plan's settings (HOST int[6]: pairs per batch, orbitals per block, pass-B block width
+ * (> 0: output blocks of that many columns; < 0: K-chunks of that many contraction indices),
  * pass-B buffers, slice staging, slice pipeline; 0 / -1 = automatic), the autotuner's trial time per pair
  * solve in ms (0 if never tuned) and *tuned_h = 0 (not tuned), 1 (measured), 2 (cache). */
 int exx_plan_get_tuning(exx_plan plan, int *settings_h, double *ms_per_pair_h, int *tuned_h);
 
 /* Set the same six settings by hand (for instance a choice the autotuner made earlier):
- * pairs per batch >= 0, block in [0, 32], pass-B block width (a multiple of 16, <= 256) and
+ * pairs per batch >= 0, block in [0, 32], pass-B block width (|width| a multiple of 16,
+ * <= 256; negative = K-chunks) and
  * buffers (both 0 = automatic, or both set; a pair that does not fit falls back to the
  * automatic choice), staging and pipeline in {-1, 0, 1}.  EXX_ERR_INVALID_ARG otherwise. */
 int exx_plan_set_tuning(exx_plan plan, const int *settings_h);

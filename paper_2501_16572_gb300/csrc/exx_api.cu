@@ -7,6 +7,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -639,7 +640,7 @@ int exx_plan_set_tuning(exx_plan plan, const int *settings_h)
     Plan *P = as_plan(plan);
     if (!P || !settings_h) return invalid("exx_plan_set_tuning: NULL argument");
     const int *v = settings_h;
-    if (v[0] < 0 || v[1] < 0 || v[1] > 32 || v[2] < 0 || v[2] > 256 || (v[2] & 15) || v[3] < 0 || v[3] > 64 ||
+    if (v[0] < 0 || v[1] < 0 || v[1] > 32 || v[2] < -256 || v[2] > 256 || (std::abs(v[2]) & 15) || v[3] < 0 || v[3] > 64 ||
         v[4] < -1 || v[4] > 1 || v[5] < -1 || v[5] > 1 || ((v[2] == 0) != (v[3] == 0)))
         return invalid("exx_plan_set_tuning: settings out of range");
     tune_set(*P, {v[0], v[1], v[2], v[3], v[4], v[5], 0.0});

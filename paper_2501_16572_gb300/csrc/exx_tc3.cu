@@ -114,24 +114,31 @@ __device__ __forceinline__ uint32_t pack2(float a, float b)
     return __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);
 }
 
-// Issue the 7 digit products of one GEMM: d0 p0 into TMEM column d_lead, the rest into
-// d_rest.  A digits i at a_base + i a_piece, C digits j at b_base + j b_piece, K-major,
-// LBO 128 bytes, SBO sbo, ksteps steps of 16 along K.
-__device__ __forceinline__ void issue_x7(uint32_t d_lead, uint32_t d_rest, uint32_t a_base, uint32_t a_piece,
-                                         uint32_t b_base, uint32_t b_piece, uint32_t sbo, int ksteps,
-                                         uint32_t idesc)
+// Issue the 7 digit products of one GEMM (or of one K-chunk of it): d0 p0 into TMEM column
+// d_lead, the rest into d_rest.  A digits i at a_base + i a_piece (SBO a_sbo), C digits j at
+// b_base + j b_piece (SBO b_sbo), K-major, LBO 128 bytes, ksteps steps of 16 along K.  The
+// first step overwrites both accumulators unless `accumulate` (a later K-chunk).
+__device__ __forceinline__ void issue_x7g(uint32_t d_lead, uint32_t d_rest, uint32_t a_base, uint32_t a_piece,
+                                          uint32_t a_sbo, uint32_t b_base, uint32_t b_piece, uint32_t b_sbo,
+                                          int ksteps, uint32_t idesc, bool accumulate)
 {
     const int PA[7] = {0, 0, 1, 0, 1, 2, 0};
     const int PB[7] = {0, 1, 0, 2, 1, 0, 3};
     for (int ks = 0; ks < ksteps; ++ks) {
 #pragma unroll
         for (int t = 0; t < 7; ++t) {
-            const uint64_t ad = tc::smem_desc(a_base + uint32_t(PA[t]) * a_piece + uint32_t(ks) * 256u, 128u, sbo);
-            const uint64_t bd = tc::smem_desc(b_base + uint32_t(PB[t]) * b_piece + uint32_t(ks) * 256u, 128u, sbo);
-            const uint32_t acc = t == 0 ? (ks > 0 ? 1u : 0u) : ((ks > 0 || t > 1) ? 1u : 0u);
-            tc::mma_bf16(t == 0 ? d_lead : d_rest, ad, bd, idesc, acc);
+            const uint64_t ad = tc::smem_desc(a_base + uint32_t(PA[t]) * a_piece + uint32_t(ks) * 256u, 128u, a_sbo);
+            const uint64_t bd = tc::smem_desc(b_base + uint32_t(PB[t]) * b_piece + uint32_t(ks) * 256u, 128u, b_sbo);
+            const bool acc = accumulate || ks > 0 || (t > 1);
+            tc::mma_bf16(t == 0 ? d_lead : d_rest, ad, bd, idesc, (t == 0 ? (accumulate || ks > 0) : acc) ? 1u : 0u);
         }
     }
+}
+__device__ __forceinline__ void issue_x7(uint32_t d_lead, uint32_t d_rest, uint32_t a_base, uint32_t a_piece,
+                                         uint32_t b_base, uint32_t b_piece, uint32_t sbo, int ksteps,
+                                         uint32_t idesc)
+{
+    issue_x7g(d_lead, d_rest, a_base, a_piece, sbo, b_base, b_piece, sbo, ksteps, idesc, false);
 }
 
 // Digits of four consecutive elements (hi + lo) * s of one row: 8 bytes in each of the three
@@ -597,7 +604,8 @@ struct ZArgs {
     const float *Fh, *Fl;        // f(Lambda) hi and lo, natural layout (c R + r)
     const uint8_t *imgF, *imgI;  // NB blocks each, blk_bytes apart
     uint32_t blk_bytes;
-    int NB, WN, NC;              // NC = NB WN columns per accumulator
+    int NB, WN, NC;              // NC = NB WN columns per accumulator (output blocks), or
+    int kchunk, KC;              // kchunk: NB blocks of all NC outputs x KC contraction indices
     int nbuf, resident;
     uint32_t offB, offCs, offMax, offBar;
     int tmem_cols;
@@ -642,13 +650,14 @@ __global__ void __launch_bounds__(kRows * TPR + 64, (UPT <= 4 ? 2 : 1)) zpass_ke
     const int Kp = a.Kp, WN = a.WN, NB = a.NB;
     const uint32_t sbo = uint32_t(Kp) * 16u;
     const uint32_t a_piece = uint32_t(kRows) * Kp * 2u;
-    const uint32_t b_piece = uint32_t(WN) * Kp * 2u;
+    const uint32_t b_piece = a.kchunk ? uint32_t(a.NC) * a.KC * 2u : uint32_t(WN) * Kp * 2u;
+    const uint32_t b_sbo = a.kchunk ? uint32_t(a.KC) * 16u : sbo;
     const uint32_t cs_off = uint32_t(kMatDig) * b_piece;   // column scales inside a block
 
     for (uint32_t i = tid * 16; i < 3u * a_piece; i += blockDim.x * 16)
         *reinterpret_cast<uint4 *>(sA + i) = make_uint4(0, 0, 0, 0);
     for (int i = tid; i < a.NC; i += blockDim.x) {
-        const int nb = i / WN, c = i - nb * WN;
+        const int nb = a.kchunk ? 0 : i / WN, c = i - nb * WN;
         csF[i] = reinterpret_cast<const float *>(a.imgF + size_t(nb) * a.blk_bytes + cs_off)[c];
         csI[i] = reinterpret_cast<const float *>(a.imgI + size_t(nb) * a.blk_bytes + cs_off)[c];
     }
@@ -709,7 +718,7 @@ __global__ void __launch_bounds__(kRows * TPR + 64, (UPT <= 4 ? 2 : 1)) zpass_ke
     } else if (warp == NT / 32) {
         // ---- MMA warp ----
         uint32_t ph = 0;
-        const uint32_t idesc = tc::instr_desc(false, WN);
+        const uint32_t idesc = tc::instr_desc(false, a.kchunk ? a.NC : WN);
         const uint32_t a0 = tc::smem_addr(sA), b0 = tc::smem_addr(sB);
         long seq = 0;
         bool bad = false;
@@ -743,8 +752,13 @@ __global__ void __launch_bounds__(kRows * TPR + 64, (UPT <= 4 ? 2 : 1)) zpass_ke
                     }
                     tc::tc_fence_after();
                     if (lane == 0) {
-                        issue_x7(tmem + uint32_t(nb * WN), tmem + uint32_t(a.NC + nb * WN), a0, a_piece,
-                                 b0 + uint32_t(slot) * a.blk_bytes, b_piece, sbo, Kp / 16, idesc);
+                        if (a.kchunk)   // K-chunk nb: all outputs, contraction indices nb KC ..
+                            issue_x7g(tmem, tmem + uint32_t(a.NC), a0 + uint32_t(nb * a.KC) * 16u, a_piece, sbo,
+                                      b0 + uint32_t(slot) * a.blk_bytes, b_piece, b_sbo,
+                                      (min(Kp, (nb + 1) * a.KC) - nb * a.KC) / 16, idesc, nb > 0);
+                        else
+                            issue_x7(tmem + uint32_t(nb * WN), tmem + uint32_t(a.NC + nb * WN), a0, a_piece,
+                                     b0 + uint32_t(slot) * a.blk_bytes, b_piece, sbo, Kp / 16, idesc);
                         if (!a.resident) tc::mma_commit(bempty + slot);
                     }
                     __syncwarp();
@@ -924,11 +938,12 @@ __global__ void __launch_bounds__(kRows * TPR + 64, (UPT <= 4 ? 2 : 1)) zpass_ke
 }
 
 // ---- host: matrix images -----------------------------------------------------------------
-// Image of C(n, k), n < nout rows (outputs), k < nk (contraction), in a WN x Kp block:
-// 4 base-512 digit planes (rows scaled by their largest entry to [128, 256)), then WN
-// column scales (the inverse row scales).
+// Image of C(n, k), n < nout rows (outputs), k < nk (contraction), in a WN x Kp block of
+// rows n0.. and contraction indices k0..: 4 base-512 digit planes (every row scaled by the
+// largest entry of the whole row, so the K-chunks of a row share one scale), then WN column
+// scales (the inverse row scales).
 template <class Coef>
-void build_block(uint8_t *img, int WN, int Kp, int n0, int nout, int nk, Coef coef)
+void build_block(uint8_t *img, int WN, int Kp, int n0, int nout, int nk, Coef coef, int k0 = 0)
 {
     const uint32_t sbo = uint32_t(Kp) * 16u;
     const size_t piece = size_t(WN) * Kp * 2;
@@ -942,15 +957,16 @@ void build_block(uint8_t *img, int WN, int Kp, int n0, int nout, int nk, Coef co
         if (mx > 0.0) std::frexp(mx, &e);
         const double sc = std::ldexp(1.0, 8 - e);
         cs[n] = float(std::ldexp(1.0, e - 8));
-        for (int k = 0; k < nk; ++k) {
+        for (int k = k0; k < std::min(nk, k0 + Kp); ++k) {
             double t = coef(gn, k) * sc;
+            const int kl = k - k0;
             for (int q = 0; q < kMatDig; ++q) {   // t = p0 + p1 2^-9 + p2 2^-18 + p3 2^-27
                 const double dq = std::nearbyint(t);
                 const float v = float(std::ldexp(dq, -9 * q));   // |dq| <= 256: exact in bf16
                 uint32_t u;
                 std::memcpy(&u, &v, 4);
                 const uint16_t hb = uint16_t(u >> 16);
-                std::memcpy(img + piece * q + img_at(n, k / 8, sbo) + size_t(k % 8) * 2, &hb, 2);
+                std::memcpy(img + piece * q + img_at(n, kl / 8, sbo) + size_t(kl % 8) * 2, &hb, 2);
                 t = (t - dq) * 512.0;
             }
         }
@@ -1043,41 +1059,56 @@ SliceLayout slice_layout(const Plan &P, bool pair = true)
 struct ZLayout {
     size_t smem;
     uint32_t offB, offCs, offMax, offBar, blk_bytes;
-    int NB, WN, NC, nbuf, resident, tmem_cols;
+    int NB, WN, NC, nbuf, resident, tmem_cols, kchunk, KC;
 };
 
 constexpr int kTPRz = 4;
 constexpr int kTPRs = 4;
 
-// Matrix blocks: all 2 NB resident when they fit; else streamed through 2 (or 3) buffers,
-// the fewest blocks (widest N) that fit first (measured: wider blocks with two buffers beat
-// narrower ones with three).
+// Matrix blocks of pass B.  All 2 NB output blocks resident when they fit; else streamed
+// through 2 (or 3) buffers, as K-chunks (every MMA covers all NC outputs, so the A image is
+// read once per K-step and digit product) or as output blocks (WN outputs, the full K).
+// want_wn > 0 asks for output blocks of want_wn columns, want_wn < 0 for K-chunks of
+// -want_wn contraction indices, with want_nbuf buffers; 0 = the first that fits in the order
+// resident, K-chunks / 2 buffers, output blocks / 2, K-chunks / 3, output blocks / 3.
 bool z_layout(int n3, ZLayout &L, int want_wn = 0, int want_nbuf = 0)
 {
     const int Kp = pad16i(n3);
     const size_t abytes = 3 * size_t(kRows) * Kp * 2;
-    for (int pass = 0; pass < 3; ++pass) {   // resident; streamed, 2 buffers; streamed, 3 buffers
+    auto fits = [&](int NB, int WN, int NC, int kchunk, int KC, int nbuf, int resident) {
+        const size_t blk = kchunk ? mat_image_bytes(NC, KC) : mat_image_bytes(WN, Kp);
+        size_t off = align_up(abytes, 1024);
+        const uint32_t offB = uint32_t(off);
+        off += size_t(nbuf) * blk;
+        const uint32_t offCs = uint32_t(align_up(off, 16));
+        off = offCs + 2 * size_t(NC) * 4;
+        const uint32_t offMax = uint32_t(align_up(off, 16));
+        off = offMax + size_t(kTPRz) * kRows * 4;
+        const uint32_t offBar = uint32_t(align_up(off, 16));
+        off = offBar + 16 + 16 * size_t(nbuf) + 16;
+        if (off > kSmemLimit || 2 * NC > 512) return false;
+        L = {off, offB, offCs, offMax, offBar, uint32_t(blk), NB, WN, NC, nbuf, resident, tmem_pow2(2 * NC),
+             kchunk, KC};
+        return true;
+    };
+    for (int pass = 0; pass < 5; ++pass) {
+        const bool chunk = pass == 1 || pass == 3;
+        const int nbuf_s = pass <= 2 ? 2 : 3;
         for (int NB = 1; NB <= 16; ++NB) {
-            const int WN = pad16i((n3 + NB - 1) / NB);
-            if (WN * (NB - 1) >= n3) continue;   // no empty block
-            const size_t blk = mat_image_bytes(WN, Kp);
-            const int nbuf = pass == 0 ? 2 * NB : (pass == 1 ? 2 : 3);
-            if (pass > 0 && nbuf >= 2 * NB) continue;
-            if (want_wn && (WN != want_wn || nbuf != want_nbuf)) continue;   // a tuned choice
-            size_t off = align_up(abytes, 1024);
-            const uint32_t offB = uint32_t(off);
-            off += size_t(nbuf) * blk;
-            const uint32_t offCs = uint32_t(align_up(off, 16));
-            off = offCs + 2 * size_t(NB) * WN * 4;
-            const uint32_t offMax = uint32_t(align_up(off, 16));
-            off = offMax + size_t(kTPRz) * kRows * 4;
-            const uint32_t offBar = uint32_t(align_up(off, 16));
-            off = offBar + 16 + 16 * size_t(nbuf) + 16;
-            const int NC = NB * WN;
-            if (off <= kSmemLimit && 2 * NC <= 512) {
-                L = {off, offB, offCs, offMax, offBar, uint32_t(blk), NB, WN, NC, nbuf, pass == 0 ? 1 : 0,
-                     tmem_pow2(2 * NC)};
-                return true;
+            if (chunk) {
+                if (NB < 2) continue;
+                const int KC = pad16i((Kp + NB - 1) / NB);
+                if (KC * (NB - 1) >= Kp) continue;   // no empty chunk
+                if (nbuf_s >= 2 * NB) continue;
+                if (want_wn && (want_wn != -KC || want_nbuf != nbuf_s)) continue;
+                if (fits(NB, Kp, Kp, 1, KC, nbuf_s, 0)) return true;
+            } else {
+                const int WN = pad16i((n3 + NB - 1) / NB);
+                if (WN * (NB - 1) >= n3) continue;   // no empty block
+                const int nbuf = pass == 0 ? 2 * NB : nbuf_s;
+                if (pass > 0 && nbuf >= 2 * NB) continue;
+                if (want_wn && (WN != want_wn || nbuf != want_nbuf)) continue;   // a tuned choice
+                if (fits(NB, WN, NB * WN, 0, 0, nbuf, pass == 0 ? 1 : 0)) return true;
             }
         }
     }
@@ -1086,19 +1117,23 @@ bool z_layout(int n3, ZLayout &L, int want_wn = 0, int want_nbuf = 0)
 
 }  // namespace
 
-// The (block width, buffers) choices of pass B that fit for an axis of n3 points.
+// The (block width, buffers) choices of pass B that fit for an axis of n3 points; a
+// negative width is a K-chunk of that many contraction indices.
 std::vector<std::pair<int, int>> tc3_z_choices(int n3)
 {
     std::vector<std::pair<int, int>> out;
+    const int Kp = pad16i(n3);
     for (int NB = 1; NB <= 16; ++NB) {
         const int WN = pad16i((n3 + NB - 1) / NB);
-        for (int nbuf : {2 * NB, 2, 3}) {
-            ZLayout L;
-            if (z_layout(n3, L, WN, nbuf)) {
-                std::pair<int, int> c{WN, L.nbuf};
-                if (std::find(out.begin(), out.end(), c) == out.end()) out.push_back(c);
+        const int KC = pad16i((Kp + NB - 1) / NB);
+        for (int nbuf : {2 * NB, 2, 3})
+            for (int w : {WN, -KC}) {
+                ZLayout L;
+                if (z_layout(n3, L, w, nbuf)) {
+                    std::pair<int, int> c{L.kchunk ? -L.KC : L.WN, L.nbuf};
+                    if (std::find(out.begin(), out.end(), c) == out.end()) out.push_back(c);
+                }
             }
-        }
     }
     return out;
 }
@@ -1189,10 +1224,16 @@ int tc3_upload(Plan &P)
         const std::vector<double> &V = P.V[2];
         for (int inv = 0; inv < 2; ++inv) {
             std::vector<uint8_t> img(size_t(Z.NB) * Z.blk_bytes, 0);
-            for (int nb = 0; nb < Z.NB; ++nb)
-                build_block(img.data() + size_t(nb) * Z.blk_bytes, Z.WN, Kp, nb * Z.WN, nd, nd, [&](int n, int k) {
-                    return inv ? V[size_t(n) + size_t(nd) * k] : V[size_t(k) + size_t(nd) * n];
-                });
+            auto coef = [&](int n, int k) {
+                return inv ? V[size_t(n) + size_t(nd) * k] : V[size_t(k) + size_t(nd) * n];
+            };
+            for (int nb = 0; nb < Z.NB; ++nb) {
+                uint8_t *dst = img.data() + size_t(nb) * Z.blk_bytes;
+                if (Z.kchunk)   // all outputs, contraction indices nb KC ..
+                    build_block(dst, Z.NC, Z.KC, 0, nd, nd, coef, nb * Z.KC);
+                else
+                    build_block(dst, Z.WN, Kp, nb * Z.WN, nd, nd, coef);
+            }
             DevBuf &b = P.t3img[2][inv];
             if (int rc = dev_reserve(b, img.size())) return rc;
             EXX_CUDA(cudaMemcpy(b.p, img.data(), img.size(), cudaMemcpyHostToDevice));
@@ -1293,6 +1334,8 @@ int tc3_solve_batch(Plan &P, const int2 *pairs_d, int nfields, float *bufA, floa
         a.NB = Z.NB;
         a.WN = Z.WN;
         a.NC = Z.NC;
+        a.kchunk = Z.kchunk;
+        a.KC = Z.KC;
         a.nbuf = Z.nbuf;
         a.resident = Z.resident;
         a.offB = Z.offB;

@@ -182,3 +182,25 @@ def test_bf16x7_slab_grid_pipelined(exx, slab64):
     cols = [5, 60]
     orc, ref = _oracle(s, cols=cols)
     assert pm.rel(vx.cpu().numpy()[cols], ref) < TOL_V
+
+
+@pytest.mark.parametrize("case", [dict(n=(16, 20, 144), bc=(1, 1, 0), forms=[(-48, 2), (48, 2)]),
+                                  dict(n=(10, 8, 200), bc=(1, 0, 0), forms=[(-16, 2), (16, 2)])],
+                         ids=lambda c: "x".join(map(str, c["n"])))
+def test_bf16x7_z_streaming_forms(exx, case):
+    """Pass B with its matrices streamed as K-chunks (full-width MMAs) and as output blocks
+    gives the same results within the targets."""
+    s = synth.small_system(h=0.3, seed=33, n_orb=4, kernel=1, omega=0.106, n=case["n"], bc=case["bc"])
+    orc, ref = _oracle(s)
+    e_ref = orc.energy(s.psi[:s.n_occ], s.f, ref)
+    psi = torch.from_numpy(s.psi).cuda()
+    f = torch.from_numpy(s.f).cuda()
+    for zb, nbuf in case["forms"]:
+        plan = exx.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+        plan.set_precision(exx.EXX_PREC_BF16X7)
+        plan.set_tuning(z_block=zb, z_buffers=nbuf)
+        assert plan.tuning()["z_block"] == zb
+        vx = plan.apply(psi[:s.n_occ], f, psi)
+        e = plan.energy(psi[:s.n_occ], f, vx)
+        assert pm.rel(vx.cpu().numpy(), ref) < TOL_V, (zb, nbuf)
+        assert abs(e - e_ref) < TOL_E * abs(e_ref), (zb, nbuf)
