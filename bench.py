@@ -69,8 +69,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="library default settings instead of the autotuner's")
     ap.add_argument("--n-orb", type=int, default=128)
+    ap.add_argument("--slab-orbitals", type=int, default=1024,
+                    help="orbitals of the slab workload (occupied: 800/1024 of them); smaller values "
+                         "make small cases of the same grid for profiling")
     ap.add_argument("--batch", type=int, default=0, help="pairs per batch (0 = library default)")
-    ap.add_argument("--workload", default="slab", choices=["slab", "periodic48", "batch48", "sweep", "precision"])
+    ap.add_argument("--workload", default="slab", choices=["slab", "periodic48", "batch48", "sweep", "precision", "capacity"])
     return ap.parse_args()
 
 
@@ -213,6 +216,10 @@ def workload(args):
     import synth
     if args.workload == "periodic48":
         return synth.config2(args.n_orb), WORKLOAD, True
+    if args.slab_orbitals != 1024:
+        n = args.slab_orbitals
+        s = synth.config5(n_orb=n, n_occ=max(1, (n * 800) // 1024))
+        return s, SLAB_WORKLOAD.replace("1024 orbitals, 800", f"{n} orbitals, {s.n_occ}"), False
     return synth.config5(), SLAB_WORKLOAD, False
 
 
@@ -864,6 +871,67 @@ def run_reference(args):
     print(json.dumps(rec), flush=True)
 
 
+def run_capacity(args):
+    """Capacity run on the paper-scale mixed-boundary slab (117 x 117 x 119, 1848 orbitals,
+    1440 occupied): one timed step (exx_apply + exx_energy + ace_build) in the fastest
+    precision form that supports the grid, the device memory it held, and the VxPsi error of
+    two sampled output columns (one occupied, one empty) against the CPU oracle."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2501_16572_gb300 as exx
+    import synth
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    t0 = time.perf_counter()
+    s = synth.capacity_slab()
+    t_gen = time.perf_counter() - t0
+    free0, total = torch.cuda.mem_get_info(dev)
+    psi = torch.from_numpy(s.psi).to(dev)
+    f = torch.from_numpy(s.f).to(dev)
+    prec_name = args.prec if args.prec != "auto" else pick_precision(exx, s, dev)
+    plan = exx.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    plan.set_precision(prec_code(exx, prec_name))
+    W = torch.empty_like(psi)
+    xi = torch.empty_like(psi)
+    stream = torch.cuda.current_stream()
+    plan.set_timing(True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    plan.apply(psi[:s.n_occ], f, psi, out=W)
+    ev[1].record(stream)
+    e_x = plan.energy(psi[:s.n_occ], f, W)
+    plan.ace_build(psi, W, xi=xi)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    step_ms, apply_ms = ev[0].elapsed_time(ev[2]), ev[0].elapsed_time(ev[1])
+    kt = plan.timing()
+    free1, _ = torch.cuda.mem_get_info(dev)
+    cols = [7, s.n_orb - 5]
+    t1 = time.perf_counter()
+    orc = oracle.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
+    ref = orc.exx_apply(s.psi[:s.n_occ], s.f, s.psi, cols=cols)
+    t_orc = time.perf_counter() - t1
+    got = W[cols].cpu().numpy()
+    err = {f"col{c}": float(np.linalg.norm(got[i] - ref[i]) / np.linalg.norm(ref[i])) for i, c in enumerate(cols)}
+    rec = {"workload": s.name, "grid": list(s.n), "n_orb": s.n_orb, "n_occ": s.n_occ,
+           "unique_pair_solves": s.unique_pairs(), "precision": prec_name,
+           "ms_per_step": step_ms, "exx_apply_ms": apply_ms, "value": s.unique_pairs() / (apply_ms * 1e-3),
+           "unit": UNIT + " (exx_apply)", "E_x": e_x,
+           "kernel_times_ms": {k: round(v[0], 3) for k, v in kt.items() if v[1]},
+           "device_bytes_held": int(free0 - free1), "device_bytes_total": int(total),
+           "vxpsi_rel_vs_oracle": err, "oracle_seconds": t_orc, "oracle_threads": oracle.num_threads(),
+           "input_generation_s": t_gen}
+    plan.close()
+    print(json.dumps(rec), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
@@ -874,5 +942,7 @@ if __name__ == "__main__":
         run_sweep(a)
     elif a.workload == "precision":
         run_precision(a)
+    elif a.workload == "capacity":
+        run_capacity(a)
     else:
         run_ours(a)

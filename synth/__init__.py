@@ -228,6 +228,14 @@ def config5(n_orb=1024, n_occ=800):
                        fermi_index=779, n_occ=n_occ)
 
 
+def capacity_slab(n_orb=1848, n_occ=1440):
+    """Paper-scale mixed-boundary slab 117x117x119 (periodic x,y, Dirichlet z, top 30% of z
+    vacuum), h=0.2, screened, 1848 orbitals of which the first 1440 are occupied."""
+    return make_system("slab117x117x119_erfc_1848", (117, 117, 119), 0.2, (1, 1, 0), n_orb,
+                       KERNEL_ERFC, HSE_OMEGA, "fd", SEED_BASE + 6, slab_axis=2,
+                       fermi_index=1400, n_occ=n_occ)
+
+
 def small_system(n=(10, 9, 8), h=0.4, bc=(0, 1, 0), n_orb=6, kernel=KERNEL_COULOMB,
                  omega=0.0, seed=7, fd_order=12, occ="fd", n_occ=None):
     """Small seeded system for fast tests (ragged, non-cubic grids allowed)."""
