@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="library default settings instead of the autotuner's")
+    ap.add_argument("--set-tuning", default="",
+                    help="six comma-separated settings for exx_plan_set_tuning instead of the autotuner "
+                         "(pairs per batch, block orbitals, z block, z buffers, staging, pipeline)")
     ap.add_argument("--n-orb", type=int, default=128)
     ap.add_argument("--slab-orbitals", type=int, default=1024,
                     help="orbitals of the slab workload (occupied: 800/1024 of them); smaller values "
@@ -259,7 +262,11 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     # the library's autotuner picks the batch, block and kernel settings on this grid (untimed)
     tuning = None
-    if not args.batch and not args.no_tune:
+    if args.set_tuning:
+        v = [int(x) for x in args.set_tuning.split(",")]
+        plan.set_tuning(*v)
+        tuning = plan.tuning()
+    elif not args.batch and not args.no_tune:
         t0 = time.perf_counter()
         tuning = plan.autotune(psi[:occ], f, psi, out=W)
         tuning["seconds"] = time.perf_counter() - t0

@@ -675,6 +675,7 @@ int exx_energy(exx_plan plan, const double *Psi_occ, int n_occ, long ld, const d
     if (n_occ < 1 || ld < P->N || ld_v < P->N) return invalid("exx_energy: bad sizes");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (int rc = tc_check_error(*P, s)) return rc;   // a bounded wait of an earlier exx_apply ran out
+    P->launches = 0;
     return energy_fp64(*P, Psi_occ, n_occ, ld, f, VxPsi, ld_v, E_x_h, s);
 }
 

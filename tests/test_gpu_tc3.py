@@ -204,3 +204,16 @@ def test_bf16x7_z_streaming_forms(exx, case):
         e = plan.energy(psi[:s.n_occ], f, vx)
         assert pm.rel(vx.cpu().numpy(), ref) < TOL_V, (zb, nbuf)
         assert abs(e - e_ref) < TOL_E * abs(e_ref), (zb, nbuf)
+
+
+def test_launch_count_is_per_call(exx):
+    """exx_plan_launch_count reports the launches of the last call only: an energy call after an
+    apply counts its own reduction kernels, not the apply's."""
+    s = synth.small_system(n=(14, 12, 10), h=0.4, bc=(0, 1, 0), n_orb=6, kernel=0, seed=21)
+    plan, psi, f, vx, e = _run(exx, s)
+    n_energy = plan.launch_count()
+    plan.apply(psi[:s.n_occ], f, psi, out=vx)
+    n_apply = plan.launch_count()
+    assert 1 <= n_energy <= 4 < n_apply
+    plan.energy(psi[:s.n_occ], f, vx)
+    assert plan.launch_count() == n_energy
