@@ -1114,11 +1114,14 @@ __device__ __forceinline__ void sub_product(float &s, float &c, float gh, float 
 
 __device__ __forceinline__ int diag_idx(int i, int j, int nI) { return i * nI - (i * (i - 1)) / 2 + (j - i); }
 
-constexpr int kAccBlock = 8;   // widest block edge of the one-sweep form (the default edge)
+constexpr int kAccBlock = 8;    // widest block edge whose one-sweep J sums live in registers
+constexpr int kAccWide = 16;   // widest edge of the one-sweep form with the J sums in shared memory
 
 // One launch per batch: CUDA block (x, y) = 256 grid points of the outputs of Block y.
-// Blocks of one batch have disjoint outputs, so no atomics are needed.
-template <bool HL>
+// Blocks of one batch have disjoint outputs, so no atomics are needed.  WIDE: plans with
+// 16-orbital blocks keep the J-side sums of a block in shared memory ([j][thread], 32 KB
+// per CTA), so each pair field is still read once without spending registers on them.
+template <bool HL, bool WIDE>
 __global__ void __launch_bounds__(256, 6) tc_accum_kernel(long N, const Block *blocks, const float *__restrict__ V,
                                                        long lo_off, const float *__restrict__ g,
                                                        const float *__restrict__ g_lo, float *__restrict__ acc_hi,
@@ -1138,6 +1141,36 @@ __global__ void __launch_bounds__(256, 6) tc_accum_kernel(long N, const Block *b
         acc_lo[size_t(t) * N + r] = c - (hs - s);
         acc_hi[size_t(t) * N + r] = hs;
     };
+    if constexpr (WIDE) {
+        if (b.kind == BLK_SYM_OFF && b.nJ > kAccBlock && b.nJ <= kAccWide) {
+            __shared__ float shs[kAccWide][256], shc[kAccWide][256];
+            const int t = threadIdx.x;
+            for (int j = 0; j < b.nJ; ++j) {
+                shs[j][t] = acc_hi[size_t(b.J0 + j) * N + r];
+                shc[j][t] = acc_lo[size_t(b.J0 + j) * N + r];
+            }
+#pragma unroll 1
+            for (int i = 0; i < b.nI; ++i) {
+                const int oi = b.I0 + i;
+                const float gih = g[size_t(oi) * N + r], gil = g_lo[size_t(oi) * N + r];
+                float si = acc_hi[size_t(oi) * N + r], ci = acc_lo[size_t(oi) * N + r];
+#pragma unroll 4
+                for (int j = 0; j < b.nJ; ++j) {
+                    const size_t fo = size_t(i * b.nJ + j) * N;
+                    const float vh = vh_at(fo), vl = vl_at(fo);
+                    float sj = shs[j][t], cj = shc[j][t];
+                    sub_product(sj, cj, gih, gil, vh, vl);
+                    shs[j][t] = sj;
+                    shc[j][t] = cj;
+                    const size_t src = size_t(b.J0 + j) * N + r;
+                    sub_product(si, ci, g[src], g_lo[src], vh, vl);
+                }
+                finish(oi, si, ci);
+            }
+            for (int j = 0; j < b.nJ; ++j) finish(b.J0 + j, shs[j][t], shc[j][t]);
+            return;
+        }
+    }
     if (b.kind == BLK_SYM_OFF && b.nJ <= kAccBlock) {
         // Both sides in one sweep over the block's fields: field (i, j) adds to output J0+j
         // (source I0+i) and to output I0+i (source J0+j), so each field is read from memory
@@ -1584,10 +1617,18 @@ int tc_accumulate(Plan &P, const Block *blocks_d, int nblocks, const float *V, c
     int tb = timing_begin(P, EXX_TIMING_ACCUM, s);
     const float *g = static_cast<const float *>(P.g32.p), *g_lo = g + size_t(P.tc_n_occ) * P.N;
     float *ah = static_cast<float *>(P.acc_hi.p), *al = static_cast<float *>(P.acc_lo.p);
-    if (prec_info(P.prec).hl)
-        tc_accum_kernel<true><<<grid, 256, 0, s>>>(P.N, blocks_d, V, P.tc_lo_off, g, g_lo, ah, al);
-    else
-        tc_accum_kernel<false><<<grid, 256, 0, s>>>(P.N, blocks_d, V, 0, g, g_lo, ah, al);
+    const bool wide = P.block_orbitals > kAccBlock;
+    if (prec_info(P.prec).hl) {
+        if (wide)
+            tc_accum_kernel<true, true><<<grid, 256, 0, s>>>(P.N, blocks_d, V, P.tc_lo_off, g, g_lo, ah, al);
+        else
+            tc_accum_kernel<true, false><<<grid, 256, 0, s>>>(P.N, blocks_d, V, P.tc_lo_off, g, g_lo, ah, al);
+    } else {
+        if (wide)
+            tc_accum_kernel<false, true><<<grid, 256, 0, s>>>(P.N, blocks_d, V, 0, g, g_lo, ah, al);
+        else
+            tc_accum_kernel<false, false><<<grid, 256, 0, s>>>(P.N, blocks_d, V, 0, g, g_lo, ah, al);
+    }
     timing_end(P, tb, s);
     EXX_LAUNCH("tc_accum_kernel");
     P.launches++;
