@@ -346,6 +346,8 @@ def run_ours(args):
         rec["kernel_times_ms"] = {k: round(v[0] / K, 4) for k, v in ktimes.items()}
         rec["roofline"] = roofline(s, prec_name, dom, dom_ms, dom_n, K, peaks)
         rec["roofline_apply"] = roofline_apply(s, prec_name, apply_total_ms / K, peaks)
+        rec["tensor_roofline"] = tensor_roofline(s, prec_name, apply_total_ms / K, peaks)
+    rec["ordered_pair_solves_per_s"] = value * ordered / unique
     rec["clocks"] = clk
     W_split = W.clone()
     # -- FP64 path on sampled output columns (the slab) or on all of them (48^3) --
@@ -369,6 +371,11 @@ def run_ours(args):
                        "value": world * rate64, "unit": UNIT,
                        "sample": f"{len(cols)} output column(s) x {occ} occupied partners on the FP64 path; value "
                                  "= its solve rate x unique/ordered pairs of the workload"}
+        fl64 = 4.0 * s.N * sum(s.n) * solves64 / (ms64 / 1e3) / 1e12
+        pk64 = 152 * 2 * 2 * 2.07e9 / 1e12
+        rec["fp64"]["roofline"] = {"bound": "alu", "achieved": fl64, "peak": pk64, "unit": "TFLOP/s",
+                                   "frac": fl64 / pk64, "peak_source": FP64_PEAK_NOTE + " (derived, not measured)",
+                                   "rule": "4 N (n1 + n2 + n3) flops per pair solve over the FP64 apply time"}
         rec["split_vs_fp64_speedup"] = value / (world * rate64)
         rec["vxpsi_rel_fro_vs_fp64_sampled"] = float(torch.linalg.norm(W_split[cols] - ref64) / torch.linalg.norm(ref64))
         p64.close()
@@ -739,6 +746,29 @@ def roofline_apply(s, prec, apply_ms, peaks):
     return {"bound": "hbm", "achieved": achieved, "peak": pk, "unit": "GB/s", "frac": achieved / pk,
             "bytes_per_apply": staged + compulsory,
             "rule": "16 N B per unique pair (staged FP32 pipeline) + 8 N B per orbital read and per output written"}
+
+
+# digit products executed per mode product, and the tensor dtype's share of the bf16 peak
+TENSOR_PRODUCTS = {"bf16x7": (7, 1.0), "bf16x10": (10, 1.0), "bf16x6": (7, 1.0), "tf32x3": (3, 0.5),
+                   "bf16x3": (3, 1.0)}
+
+
+def tensor_roofline(s, prec, apply_ms, peaks):
+    """The apply's mode products against the tensor-core roof: algorithmic flops 4 N (n1+n2+n3)
+    per unique pair (the six mode products), executed flops = algorithmic x the digit products
+    of one mode product, over the exx_apply time, against the measured sustained bf16 rate
+    (TF32X3: half of it, the nominal dense ratio)."""
+    algo = 4.0 * s.N * sum(s.n) * s.unique_pairs()
+    out = {"algorithmic_tflops": algo / (apply_ms / 1e3) / 1e12,
+           "algorithmic_flops_per_apply": algo, "rule": "4 N (n1 + n2 + n3) flops per unique pair"}
+    if prec in TENSOR_PRODUCTS:
+        nprod, ratio = TENSOR_PRODUCTS[prec]
+        pk = peaks.get("bf16_tflops_sustained", 1700.0) * ratio
+        ex = algo * nprod / (apply_ms / 1e3) / 1e12
+        out.update({"bound": "tensor", "digit_products": nprod, "executed_tflops": ex, "peak": pk, "unit": "TFLOP/s",
+                    "frac": ex / pk, "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
+                    + (" x 0.5 (tf32 nominal ratio)" if ratio != 1.0 else "")})
+    return out
 
 
 def e2e(plan, s, steps, world):

@@ -57,3 +57,27 @@ def test_roofline_bytes_follow_the_staged_fp32_rule():
     assert r["kernel"].startswith("zpass_kernel")
     ra = b.roofline_apply(s, "bf16x7", 10.0, {"hbm_gbs": 6000.0})
     assert ra["bytes_per_apply"] == 16 * s.N * 8256 + 8 * s.N * 256
+
+
+def test_tensor_roofline_counts_the_digit_products():
+    """Algorithmic flops of the six mode products, 4 N (n1 + n2 + n3) per unique pair; the
+    executed tensor flops multiply them by the digit products of one mode product (BF16X7: 7)
+    and divide by the measured sustained bf16 rate (TF32X3: half of it)."""
+    b = _bench()
+
+    class S:
+        n = (72, 72, 144)
+        N = 72 * 72 * 144
+
+        def unique_pairs(self):
+            return 499600
+
+    s = S()
+    algo = 4.0 * s.N * (72 + 72 + 144) * 499600
+    r = b.tensor_roofline(s, "bf16x7", 1000.0, {"bf16_tflops_sustained": 1700.0})
+    assert abs(r["algorithmic_tflops"] - algo / 1e12) < 1e-9
+    assert abs(r["executed_tflops"] - 7 * algo / 1e12) < 1e-9
+    assert abs(r["frac"] - 7 * algo / 1e12 / 1700.0) < 1e-12
+    rt = b.tensor_roofline(s, "tf32x3", 1000.0, {"bf16_tflops_sustained": 1700.0})
+    assert rt["peak"] == 850.0 and rt["digit_products"] == 3
+    assert "executed_tflops" not in b.tensor_roofline(s, "fp64", 1000.0, {})
