@@ -67,6 +67,8 @@ static void free_plan_buffers(Plan &P)
         for (auto &b : row) dev_free(b);
     for (auto &row : P.t3img)
         for (auto &b : row) dev_free(b);
+    for (auto &row : P.t3imgc)
+        for (auto &b : row) dev_free(b);
     dev_free(P.F32n);
     dev_free(P.orig_V);
     dev_free(P.F64n);

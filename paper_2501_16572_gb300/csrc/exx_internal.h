@@ -156,6 +156,7 @@ struct Plan {
     // three-pass mode (EXX_PREC_BF16X7): per axis forward and inverse digit images (z in
     // N-blocks), f(Lambda) in the natural layout as FP32 hi and lo planes
     DevBuf t3img[3][2];
+    DevBuf t3imgc[2][2];            // x and y images as K-chunks, when the slice passes stream them
     DevBuf F32n;
     int t3_share01 = 0;             // x and y have the same length and bc: one image serves both
     int t3_zwn = 0, t3_znbuf = 0;   // pass B matrix block width and buffers (0 = automatic)

@@ -231,6 +231,10 @@ struct SliceArgs {
     int pipe;               // software pipeline over tiles: GEMM 2 has its own A image (offA2) and
     uint32_t offA2;         // TMEM columns (t2col), so each GEMM overlaps the other phase's work
     int t2col;
+    int bstream;            // the x/y matrices stream as K-chunks of KC (nkc1, nkc2 per GEMM) through
+    int KC, nkc1, nkc2;     // two buffers of buf_bytes at offset 0, their column scales at offCS
+    uint32_t offCS, buf_bytes, chunk1_bytes, chunk2_bytes;
+    const uint8_t *img1c, *img2c;
     int *err;
 };
 
@@ -250,18 +254,27 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 2) slice_pass_kernel(const _
     uint64_t *bar_a = reinterpret_cast<uint64_t *>(smem + a.offBar);
     uint64_t *bar_d1 = bar_a + 1, *bar_d2 = bar_a + 2;
     uint64_t *stg_full = bar_a + 3, *stg_empty = bar_a + 4;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar_a + 5);
+    uint64_t *bfull = bar_a + 5, *bempty = bar_a + 7;   // matrix-chunk buffers (bstream)
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar_a + 9);
     int *sflag = reinterpret_cast<int *>(tslot + 1);
+    float *csS = reinterpret_cast<float *>(smem + a.offCS);   // column scales (bstream)
 
-    for (uint32_t i = tid * 16; i < a.img1_bytes; i += blockDim.x * 16)
-        *reinterpret_cast<uint4 *>(sB1 + i) = *reinterpret_cast<const uint4 *>(a.img1 + i);
-    if (a.offB2)
-        for (uint32_t i = tid * 16; i < a.img2_bytes; i += blockDim.x * 16)
-            *reinterpret_cast<uint4 *>(sB2 + i) = *reinterpret_cast<const uint4 *>(a.img2 + i);
+    if (!a.bstream) {
+        for (uint32_t i = tid * 16; i < a.img1_bytes; i += blockDim.x * 16)
+            *reinterpret_cast<uint4 *>(sB1 + i) = *reinterpret_cast<const uint4 *>(a.img1 + i);
+        if (a.offB2)
+            for (uint32_t i = tid * 16; i < a.img2_bytes; i += blockDim.x * 16)
+                *reinterpret_cast<uint4 *>(sB2 + i) = *reinterpret_cast<const uint4 *>(a.img2 + i);
+    } else {   // every chunk of an image carries the same column scales: take chunk 0's
+        const float *c1 = reinterpret_cast<const float *>(a.img1c + size_t(kMatDig) * a.Kp1 * a.KC * 2);
+        const float *c2 = reinterpret_cast<const float *>(a.img2c + size_t(kMatDig) * a.Kp2 * a.KC * 2);
+        for (int i = tid; i < a.Kp1; i += blockDim.x) csS[i] = c1[i];
+        for (int i = tid; i < a.Kp2; i += blockDim.x) csS[a.Kp1 + i] = c2[i];
+    }
     for (uint32_t i = a.offA + tid * 16; i < a.offY; i += blockDim.x * 16)   // A images start as zeros
         *reinterpret_cast<uint4 *>(smem + i) = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
-        for (int i = 0; i < 5; ++i) tc::mbar_init(bar_a + i, 1);
+        for (int i = 0; i < 9; ++i) tc::mbar_init(bar_a + i, 1);
         *sflag = 0;
     }
     if (warp == 0) tc::tmem_alloc(tslot, uint32_t(a.tmem_cols));
@@ -302,6 +315,32 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 2) slice_pass_kernel(const _
             // no copy may still target shared memory at exit: the last fill has landed
             if (it > 0 && !tc::mbar_wait_timed(stg_full, uint32_t((it - 1) & 1), kWaitNs)) atomicExch(sflag, 1);
         }
+        if (a.bstream && lane == 0) {
+            // matrix K-chunks in the MMA warp's order: per tile GEMM 1's chunks, then GEMM 2's
+            long seq = 0;
+            bool bad = false;
+            for (long tile = blockIdx.x; tile < a.ntiles && !bad; tile += gridDim.x)
+                for (int g = 0; g < 2 && !bad; ++g) {
+                    const int nkc = g ? a.nkc2 : a.nkc1;
+                    const uint32_t cb = g ? a.chunk2_bytes : a.chunk1_bytes;
+                    const uint8_t *img = g ? a.img2c : a.img1c;
+                    for (int kc = 0; kc < nkc; ++kc, ++seq) {
+                        const int slot = int(seq & 1);
+                        const long use = seq >> 1;
+                        if (use > 0 && !tc::mbar_wait_timed(bempty + slot, uint32_t((use - 1) & 1), kWaitNs)) {
+                            atomicExch(sflag, 1);
+                            bad = true;
+                            break;
+                        }
+                        tc::mbar_arrive_expect_tx(bfull + slot, cb);
+                        bulk_load(smem + size_t(slot) * a.buf_bytes, img + size_t(kc) * cb, cb, bfull + slot);
+                    }
+                }
+            for (int slot = 0; slot < 2; ++slot) {   // every issued copy has landed before exit
+                const long nf = seq > slot ? (seq - 1 - slot) / 2 + 1 : 0;
+                if (nf > 0 && !tc::mbar_wait_timed(bfull + slot, uint32_t((nf - 1) & 1), kWaitNs)) atomicExch(sflag, 1);
+            }
+        }
     } else if (warp == NT / 32) {
         // ---- MMA warp: two GEMMs per tile, each after the compute threads' hand-off ----
         uint32_t ph = 0;
@@ -310,6 +349,7 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 2) slice_pass_kernel(const _
                        b2 = tc::smem_addr(sB2);
         const uint32_t t2 = tmem + uint32_t(a.t2col);
         bool bad = false;
+        long seq = 0;   // matrix chunks consumed (bstream)
         for (long tile = blockIdx.x; tile < a.ntiles && !bad; tile += gridDim.x) {
             for (int g = 0; g < 2 && !bad; ++g) {
                 if (!tc::mbar_wait_timed(bar_a, ph, kWaitNs)) {
@@ -318,6 +358,32 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 2) slice_pass_kernel(const _
                 }
                 ph ^= 1u;
                 tc::tc_fence_after();
+                if (a.bstream && !bad) {
+                    // K-chunk kc of the contraction: A columns kc KC .., all outputs of the chunk
+                    const int Kp = g ? Kp2 : Kp1, nkc = g ? a.nkc2 : a.nkc1;
+                    const uint32_t ab = g ? a2 : a1, apiece = g ? a.a_piece2 : a.a_piece1, asbo = g ? sbo2 : sbo1;
+                    const uint32_t d0 = g ? t2 : tmem;
+                    for (int kc = 0; kc < nkc && !bad; ++kc, ++seq) {
+                        const int slot = int(seq & 1);
+                        if (!tc::mbar_wait_timed(bfull + slot, uint32_t((seq >> 1) & 1), kWaitNs)) {
+                            atomicExch(sflag, 1);
+                            bad = true;
+                            break;
+                        }
+                        tc::tc_fence_after();
+                        if (lane == 0) {
+                            issue_x7g(d0, d0 + uint32_t(Kp), ab + uint32_t(kc * a.KC) * 16u, apiece, asbo,
+                                      tc::smem_addr(smem) + uint32_t(slot) * a.buf_bytes, uint32_t(Kp) * a.KC * 2u,
+                                      uint32_t(a.KC) * 16u, (min(Kp, (kc + 1) * a.KC) - kc * a.KC) / 16,
+                                      g ? idesc2 : idesc1, kc > 0);
+                            tc::mma_commit(bempty + slot);
+                        }
+                        __syncwarp();
+                    }
+                    if (!bad && lane == 0) tc::mma_commit(g ? bar_d2 : bar_d1);
+                    __syncwarp();
+                    continue;
+                }
                 if (!bad && lane == 0) {
                     if (g == 0) {
                         issue_x7(tmem, tmem + uint32_t(Kp1), a1, a.a_piece1, b1, uint32_t(Kp1) * Kp1 * 2u, sbo1,
@@ -340,8 +406,8 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 2) slice_pass_kernel(const _
         const int quarter = warp & 3, dq = warp >> 2;
         const int drow = quarter * 32 + lane;
         const uint32_t lane_q = uint32_t(quarter * 32) << 16;
-        const float *cs1 = reinterpret_cast<const float *>(sB1 + size_t(kMatDig) * Kp1 * Kp1 * 2);
-        const float *cs2 = reinterpret_cast<const float *>(sB2 + size_t(kMatDig) * Kp2 * Kp2 * 2);
+        const float *cs1 = a.bstream ? csS : reinterpret_cast<const float *>(sB1 + size_t(kMatDig) * Kp1 * Kp1 * 2);
+        const float *cs2 = a.bstream ? csS + Kp1 : reinterpret_cast<const float *>(sB2 + size_t(kMatDig) * Kp2 * Kp2 * 2);
         uint32_t ph1 = 0, ph2 = 0;
         // publish the A image to the MMA warp (and, after the first operand, hand the staging
         // buffer back to the producer); true = stop (error)
@@ -978,11 +1044,15 @@ struct SliceLayout {
     size_t smem;
     uint32_t offB2, offA, offA2, offY, offRs, offBar, a_piece1, a_piece2, offS, stg_plane;
     int G, Pj, tmem_cols, stage, pipe, t2col;
+    int bstream, KC, nkc1, nkc2;
+    uint32_t offCS, buf_bytes, chunk1_bytes, chunk2_bytes;
 };
 
 // pair: pass A (two staged planes) or pass C (one).  pipe: separate A images and TMEM
 // columns for the two GEMMs (software pipeline over tiles, one CTA per SM with staging).
-SliceLayout slice_layout_for(const Plan &P, bool pair, bool pipe)
+// bstream: the x/y matrix images stream through two buffers as K-chunks of KC (for slices whose
+// resident images do not fit next to the A images and the transposed tile).
+SliceLayout slice_layout_for(const Plan &P, bool pair, bool pipe, bool bstream = false, int KC = 0)
 {
     SliceLayout L{};
     const int n1 = P.n[0], n2 = P.n[1];
@@ -991,12 +1061,24 @@ SliceLayout slice_layout_for(const Plan &P, bool pair, bool pipe)
     L.Pj = (n2 + 3) & ~3;
     if (((L.Pj / 4) & 1) == 0) L.Pj += 4;   // odd number of 16-byte units: conflict-free rows
     const bool share = P.t3_share01 != 0;
-    size_t off = mat_image_bytes(Kp1, Kp1);
+    size_t off;
     L.offB2 = 0;
-    if (!share) {
-        off = align_up(off, 1024);
-        L.offB2 = uint32_t(off);
-        off += mat_image_bytes(Kp2, Kp2);
+    if (bstream) {
+        L.bstream = 1;
+        L.KC = KC;
+        L.nkc1 = (Kp1 + KC - 1) / KC;
+        L.nkc2 = (Kp2 + KC - 1) / KC;
+        L.chunk1_bytes = uint32_t(mat_image_bytes(Kp1, KC));
+        L.chunk2_bytes = uint32_t(mat_image_bytes(Kp2, KC));
+        L.buf_bytes = uint32_t(align_up(std::max(L.chunk1_bytes, L.chunk2_bytes), 1024));
+        off = 2 * size_t(L.buf_bytes);
+    } else {
+        off = mat_image_bytes(Kp1, Kp1);
+        if (!share) {
+            off = align_up(off, 1024);
+            L.offB2 = uint32_t(off);
+            off += mat_image_bytes(Kp2, Kp2);
+        }
     }
     off = align_up(off, 1024);
     L.offA = uint32_t(off);
@@ -1022,8 +1104,10 @@ SliceLayout slice_layout_for(const Plan &P, bool pair, bool pipe)
     off = std::max(off, end_reach);
     L.offRs = uint32_t(align_up(off, 16));
     off = L.offRs + 2 * kRows * 4;
+    L.offCS = uint32_t(align_up(off, 16));   // column scales of streamed images
+    off = L.offCS + size_t(Kp1 + Kp2) * 4;
     L.offBar = uint32_t(align_up(off, 16));
-    off = L.offBar + 64;
+    off = L.offBar + 128;                      // 9 mbarriers, the TMEM slot, the error flag
     // staging of the tile's input slices, when rows of slices are 16-byte aligned
     const long R = long(n1) * n2;
     L.stg_plane = uint32_t(align_up(size_t(L.G) * R * 4, 128));
@@ -1036,6 +1120,7 @@ SliceLayout slice_layout_for(const Plan &P, bool pair, bool pipe)
     L.stage = (R % 4 == 0 && with_stage <= kSmemLimit &&
                (pipe || with_stage <= two_per_sm || off > two_per_sm)) ? 1 : 0;
     if (P.t3_stage >= 0) L.stage = (P.t3_stage && R % 4 == 0 && with_stage <= kSmemLimit) ? 1 : 0;   // tuned
+    if (bstream) L.stage = 0;   // the producer warp streams the matrices instead
     L.smem = L.stage ? with_stage : off;
     L.pipe = pipe ? 1 : 0;
     L.t2col = pipe ? 2 * Kp1 : 0;
@@ -1050,6 +1135,14 @@ SliceLayout slice_layout(const Plan &P, bool pair = true)
     const SliceLayout ser = slice_layout_for(P, pair, false);
     const SliceLayout pip = slice_layout_for(P, pair, true);
     const bool pip_ok = pip.smem <= kSmemLimit && pip.tmem_cols <= 512;
+    if (ser.smem > kSmemLimit && !pip_ok) {
+        // the resident images do not fit: stream them, widest chunk first (serial form)
+        for (int KC : {64, 48, 32, 16}) {
+            const SliceLayout b = slice_layout_for(P, pair, false, true, KC);
+            if (b.smem <= kSmemLimit) return b;
+        }
+        return ser;   // unsupported: tc3_supported reports it
+    }
     if (P.t3_pipe == 1 && pip_ok) return pip;
     if (P.t3_pipe == 0 || !pip_ok) return ser;
     const bool ser_two = ser.smem + 1024 <= 233472 / 2 && ser.tmem_cols <= 256;
@@ -1216,6 +1309,26 @@ int tc3_upload(Plan &P)
             EXX_CUDA(cudaMemcpy(b.p, img.data(), img.size(), cudaMemcpyHostToDevice));
         }
     }
+    // x and y as K-chunks when the slice passes stream them (every chunk: all outputs)
+    {
+        const SliceLayout L = slice_layout(P, true);
+        if (L.bstream)
+            for (int d = 0; d < 2; ++d) {
+                const int nd = P.n[d], Kp = pad16i(nd), nkc = (Kp + L.KC - 1) / L.KC;
+                const size_t cb = mat_image_bytes(Kp, L.KC);
+                const std::vector<double> &V = P.V[d];
+                for (int inv = 0; inv < 2; ++inv) {
+                    std::vector<uint8_t> img(size_t(nkc) * cb, 0);
+                    auto coef = [&](int n, int k) {
+                        return inv ? V[size_t(n) + size_t(nd) * k] : V[size_t(k) + size_t(nd) * n];
+                    };
+                    for (int kc = 0; kc < nkc; ++kc) build_block(img.data() + size_t(kc) * cb, Kp, L.KC, 0, nd, nd, coef, kc * L.KC);
+                    DevBuf &b = P.t3imgc[d][inv];
+                    if (int rc = dev_reserve(b, img.size())) return rc;
+                    EXX_CUDA(cudaMemcpy(b.p, img.data(), img.size(), cudaMemcpyHostToDevice));
+                }
+            }
+    }
     // z: NB blocks of WN outputs each
     ZLayout Z;
     if (!z_layout(P.n[2], Z, P.t3_zwn, P.t3_znbuf)) z_layout(P.n[2], Z);
@@ -1298,6 +1411,16 @@ int tc3_solve_batch(Plan &P, const int2 *pairs_d, int nfields, float *bufA, floa
         a.pipe = L.pipe;
         a.offA2 = L.offA2;
         a.t2col = L.t2col;
+        a.bstream = L.bstream;
+        a.KC = L.KC;
+        a.nkc1 = L.nkc1;
+        a.nkc2 = L.nkc2;
+        a.offCS = L.offCS;
+        a.buf_bytes = L.buf_bytes;
+        a.chunk1_bytes = L.chunk1_bytes;
+        a.chunk2_bytes = L.chunk2_bytes;
+        a.img1c = static_cast<const uint8_t *>(P.t3imgc[0][inv].p);
+        a.img2c = static_cast<const uint8_t *>(P.t3imgc[1][inv].p);
         a.err = static_cast<int *>(P.err_d.p);
         size_t smem = L.smem;
         auto kern = pair ? slice_pass_kernel<true, kTPRs> : slice_pass_kernel<false, kTPRs>;

@@ -217,3 +217,19 @@ def test_launch_count_is_per_call(exx):
     assert 1 <= n_energy <= 4 < n_apply
     plan.energy(psi[:s.n_occ], f, vx)
     assert plan.launch_count() == n_energy
+
+
+STREAMED = [dict(n=(117, 117, 24), bc=(1, 1, 0)), dict(n=(120, 90, 20), bc=(0, 1, 1)),
+            dict(n=(112, 112, 16), bc=(1, 1, 1))]
+
+
+@pytest.mark.parametrize("case", STREAMED, ids=lambda c: "x".join(map(str, c["n"])))
+def test_bf16x7_streamed_slice_matrices(exx, case):
+    """Slices too wide for resident x/y matrix images (up to 128 points): the slice passes stream
+    the matrices as K-chunks through shared memory; results within the targets."""
+    s = synth.small_system(h=0.3, seed=41, n_orb=4, kernel=1, omega=0.106, **case)
+    plan, psi, f, vx, e = _run(exx, s)
+    orc, ref = _oracle(s)
+    e_ref = orc.energy(s.psi[:s.n_occ], s.f, ref)
+    assert pm.rel(vx.cpu().numpy(), ref) < TOL_V
+    assert abs(e - e_ref) < TOL_E * abs(e_ref)
