@@ -833,17 +833,10 @@ def golden_energy(s):
         g = json.load(open(path))
     except Exception:
         return None
-    import numpy as np
     sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
     import make_slab_energy as mk
-    key, _ = mk.recipe_key(s)
-    if g.get("key") != key:
+    if not mk.stored_matches(g, s, s.psi):
         return None
-    fp = mk.fingerprint(s.psi)
-    for name in ("sum_sq", "sum_w"):
-        a, b = np.array(fp[name]), np.array(g["fingerprint"][name])
-        if a.shape != b.shape or np.max(np.abs(a - b)) > 1e-12 * max(1.0, np.max(np.abs(b))):
-            return None
     return g["E_x"]
 
 

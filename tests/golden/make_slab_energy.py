@@ -10,12 +10,12 @@ adds the block results:
     orbitals of J gives out_n = -sum_{m in I} f_m psi_m V_mn, and twice the oracle energy of
     (J, out) is the contribution of the pairs (m, n) and (n, m), m in I, n in J.
 The partial sums are checkpointed (one line per block or block pair), so an interrupted run
-resumes.  The record is keyed by the input recipe (workload name, seed, sizes and a hash of
-the synthetic-input module's source) and carries a fingerprint of Psi (sums over every
-orbital of psi^2 and of psi times a fixed weight): inputs regenerated on another machine
+resumes.  The record holds the input recipe (workload name, seed, sizes, and for information
+a hash of the synthetic-input module's source) and a fingerprint of Psi (sums over every
+orbital of psi^2 and of psi times a fixed weight).  Inputs regenerated on another machine
 may differ in the last bits (the exponentials and the QR factorisation are library code),
-so a reader compares the fingerprint within 1e-12 before using the stored energy; a
-relative input change of 1e-15 moves E_x by about 1e-15.
+so a reader (stored_matches) compares the recipe fields and the fingerprint within 1e-12
+before using the stored energy; a relative input change of 1e-15 moves E_x by about 1e-15.
 
 Usage: python tests/golden/make_slab_energy.py [--block 40] [--threads N]
 """
@@ -45,6 +45,28 @@ def recipe_key(s):
     rec = f"{s.name}|{s.n}|{s.h}|{s.bc}|{s.fd_order}|{s.kernel}|{s.omega}|{s.n_orb}|{s.n_occ}|" \
           f"seed={synth.SEED_BASE + 5}|synth={hashlib.sha256(src).hexdigest()[:16]}"
     return hashlib.sha256(rec.encode()).hexdigest()[:24], rec
+
+
+def recipe_fields(s):
+    """The recipe without the hash of the synthetic-input module: what a reader compares.  The
+    module hash in the record is informational (an addition to synth/ that leaves this
+    workload's generator untouched changes it); the fingerprint of Psi decides whether the
+    regenerated inputs are the stored ones."""
+    return recipe_key(s)[1].split("|synth=")[0]
+
+
+def stored_matches(g, s, psi=None, tol=1e-12):
+    """True when the record g was made from the recipe of s and, if psi is given, its
+    fingerprint matches psi's within tol (relative to the largest stored value)."""
+    if g.get("recipe", "").split("|synth=")[0] != recipe_fields(s):
+        return False
+    if psi is not None:
+        fp = fingerprint(psi)
+        for name in ("sum_sq", "sum_w"):
+            a, b = np.array(fp[name]), np.array(g["fingerprint"][name])
+            if a.shape != b.shape or np.max(np.abs(a - b)) > tol * max(1.0, np.max(np.abs(b))):
+                return False
+    return True
 
 
 def fingerprint(psi):

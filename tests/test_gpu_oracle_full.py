@@ -8,7 +8,8 @@ comparison with the library's own FP64 path):
   the oracle's xi from the oracle's W.
 * 48^3 periodic screened, 256 orbitals: the same for the FP64 path and BF16X7.
 * 72 x 72 x 144 slab, 1024 orbitals (800 occupied): sampled output columns (one occupied,
-  one empty) over all 800 partners, with the error inside the vacuum (top 30% of z).
+  one empty) over all 800 partners, with the error inside the vacuum (top 30% of z), and
+  E_x against the oracle's full energy stored in tests/golden/.
 
 Besides the relative Frobenius norm, every comparison reports the largest absolute error
 of each column divided by that column's largest entry.
@@ -115,6 +116,26 @@ def test_config3_all_columns_against_oracle(exx):
         assert ee < tol_e
 
 
+def stored_slab_energy(s):
+    """The oracle's full E_x of the slab workload from tests/golden/slab72x72x144_energy.json
+    (written by make_slab_energy.py, which calls only oracle/), when its input recipe and the
+    fingerprint of the regenerated Psi match; None when the file is absent."""
+    import json
+    import os
+    import sys
+    here = os.path.join(os.path.dirname(__file__), "golden")
+    path = os.path.join(here, "slab72x72x144_energy.json")
+    if not os.path.exists(path):
+        return None
+    sys.path.insert(0, here)
+    import make_slab_energy as mk
+    g = json.load(open(path))
+    assert mk.stored_matches(g, s), "stored slab energy was made from another input recipe"
+    if not mk.stored_matches(g, s, s.psi):
+        pytest.skip("regenerated inputs differ from the stored ones beyond 1e-12 (fingerprint)")
+    return g["E_x"]
+
+
 def test_slab_sampled_columns_and_vacuum(exx):
     s = synth.config5()
     cols = [17, 901]                 # an occupied and an unoccupied output orbital
@@ -129,8 +150,14 @@ def test_slab_sampled_columns_and_vacuum(exx):
     p = exx.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
     p.set_precision(exx.EXX_PREC_BF16X7)
     W = p.apply(psi[:s.n_occ], f, psi)
+    e_x = p.energy(psi[:s.n_occ], f, W)
     got = W.cpu().numpy()[cols]
     p.close()
+    stored = stored_slab_energy(s)
+    if stored is not None:       # the full oracle energy (320,400 unique pair solves), stored
+        e_rel = abs(e_x - stored) / abs(stored)
+        print(f"slab bf16x7: E_x {e_x:.12f}, stored oracle {stored:.12f}, rel {e_rel:.2e}")
+        assert e_rel < TOL_E
     ev = pm.rel(got, ref)
     ev_vac = pm.rel(got[:, vac], ref[:, vac])
     cm = col_max_rel(got, ref)

@@ -178,3 +178,26 @@ def test_fast_division_matches_integer_division(lib):
         assert lib.exx_debug_fastdiv(d, len(n), n.ctypes.data_as(U), q.ctypes.data_as(U)) == 0
         assert np.array_equal(q.astype(np.uint64), n.astype(np.uint64) // d), d
     assert lib.exx_debug_fastdiv(0, 0, None, None) != 0
+
+
+def test_stored_slab_energy_matches_the_input_recipe():
+    """The stored full-oracle energy of the slab workload belongs to the current synthetic-input
+    recipe (workload, sizes, seed and a hash of synth/), and is a plausible exchange energy."""
+    import json
+    import os
+    import sys
+    here = os.path.join(os.path.dirname(__file__), "golden")
+    path = os.path.join(here, "slab72x72x144_energy.json")
+    if not os.path.exists(path):
+        pytest.skip("the stored slab energy has not been written yet")
+    sys.path.insert(0, here)
+    import make_slab_energy as mk
+    import synth
+
+    class Recipe:   # the fields recipe_key reads, without generating 6 GB of orbitals
+        name, n, h, bc, fd_order = "slab72x72x144_erfc_1024", (72, 72, 144), 0.2, (1, 1, 0), 12
+        kernel, omega, n_orb, n_occ = synth.KERNEL_ERFC, synth.HSE_OMEGA, 1024, 800
+    g = json.load(open(path))
+    assert mk.stored_matches(g, Recipe())
+    assert g["unique_pair_solves"] == 800 * 801 // 2
+    assert g["E_x"] < 0 and len(g["fingerprint"]["sum_sq"]) == 1024
