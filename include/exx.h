@@ -85,8 +85,10 @@ enum { EXX_KERNEL_COULOMB = 0, EXX_KERNEL_ERFC = 1, EXX_KERNEL_ERFC_PAPER16PI = 
  *            FP32 intermediates; base-512 digits: three per data row, four per matrix row;
  *            the leading product summed exactly in one TMEM accumulator, the six others
  *            in a second; the fully modal middle kept as FP32 hi + lo; ~27 bits per
- *            product.  Needs Nx, Ny <= 128 (EXX_ERR_UNSUPPORTED otherwise; the z axis is
- *            streamed in blocks and may have up to about 208 points).
+ *            product.  Needs Nx, Ny <= 128 (EXX_ERR_UNSUPPORTED otherwise) and up to
+ *            about 208 points along z; matrices too large to stay in shared memory (the
+ *            z matrices of long axes, the x/y matrices of slices wider than about 108
+ *            points) stream through it as K-chunks.
  * Pair densities and the accumulation over pairs are compensated in every mode. */
 enum { EXX_PREC_FP64 = 0, EXX_PREC_BF16X3 = 1, EXX_PREC_TF32X3 = 2, EXX_PREC_BF16X6 = 3,
        EXX_PREC_BF16X10 = 4, EXX_PREC_BF16X7 = 5 };
