@@ -764,8 +764,13 @@ int exx_ace_step_host(exx_plan plan, const double *Psi_h, int n, long ld, int n_
     double *W = static_cast<double *>(P->host_stage_w.p);
     double *xi = static_cast<double *>(P->host_stage_xi.p);
     double *f = static_cast<double *>(P->host_stage_f.p);
-    EXX_CUDA(cudaMemcpy2DAsync(Psi, size_t(P->N) * sizeof(double), Psi_h, size_t(ld) * sizeof(double),
-                               size_t(P->N) * sizeof(double), n, cudaMemcpyHostToDevice, s));
+    // one contiguous copy when the host columns are packed (a pitched copy moves row by row
+    // and runs far below the host link's bandwidth)
+    if (ld == P->N)
+        EXX_CUDA(cudaMemcpyAsync(Psi, Psi_h, cols, cudaMemcpyHostToDevice, s));
+    else
+        EXX_CUDA(cudaMemcpy2DAsync(Psi, size_t(P->N) * sizeof(double), Psi_h, size_t(ld) * sizeof(double),
+                                   size_t(P->N) * sizeof(double), n, cudaMemcpyHostToDevice, s));
     EXX_CUDA(cudaMemcpyAsync(f, f_h, size_t(n_occ) * sizeof(double), cudaMemcpyHostToDevice, s));
     long launches = 0;
     if (int rc = exx_apply(plan, Psi, n_occ, P->N, f, Psi, n, P->N, W, P->N, stream)) return rc;
@@ -776,8 +781,11 @@ int exx_ace_step_host(exx_plan plan, const double *Psi_h, int n, long ld, int n_
     launches += P->launches;
     P->launches = launches;
     if (rc) return rc;
-    EXX_CUDA(cudaMemcpy2DAsync(xi_h, size_t(ld_xi) * sizeof(double), xi, size_t(P->N) * sizeof(double),
-                               size_t(P->N) * sizeof(double), n, cudaMemcpyDeviceToHost, s));
+    if (ld_xi == P->N)
+        EXX_CUDA(cudaMemcpyAsync(xi_h, xi, cols, cudaMemcpyDeviceToHost, s));
+    else
+        EXX_CUDA(cudaMemcpy2DAsync(xi_h, size_t(ld_xi) * sizeof(double), xi, size_t(P->N) * sizeof(double),
+                                   size_t(P->N) * sizeof(double), n, cudaMemcpyDeviceToHost, s));
     EXX_CUDA(cudaStreamSynchronize(s));
     return EXX_OK;
 }
