@@ -11,7 +11,10 @@
 // five-pass modes).  Passes A and C do two GEMMs per tile of whole z-slices: the first
 // contracts x over rows (slice, y), the tile is transposed through shared memory, the
 // second contracts y over rows (slice, a).  Pass B does the forward GEMM, the f(Lambda)
-// scaling and the inverse GEMM on chip.  Only FP32 values cross HBM between passes.
+// scaling and the inverse GEMM on chip.  Only FP32 values cross HBM between passes.  The 1D
+// matrix images stay in shared memory when they fit; otherwise (long z axes, slices wider
+// than about 108 points) a producer warp streams them through two buffers as K-chunks, every
+// chunk holding all outputs of its contraction indices.
 //
 // Arithmetic of one mode product D[row][n] = sum_k A[row][k] C[n][k]:
 //  * every data row gets a power-of-two scale from its largest entry and is cut into three
