@@ -651,8 +651,9 @@ __global__ void __launch_bounds__(kRows * TPR + 64, 1) tc_pass_kernel(const __gr
         }
         tc::cp_async_wait_all();   // no copy may still target shared memory at exit
         if (use_tma) {   // nor a box: only the last fill of a buffer can be unconsumed (after a stop)
-            if (fills0 > 0) tc::mbar_wait_bounded(full, uint32_t((fills0 - 1) & 1), kWaitLimit);
-            if (fills1 > 0) tc::mbar_wait_bounded(full + 1, uint32_t((fills1 - 1) & 1), kWaitLimit);
+            if (fills0 > 0 && !tc::mbar_wait_bounded(full, uint32_t((fills0 - 1) & 1), kWaitLimit)) atomicExch(sflag, 1);
+            if (fills1 > 0 && !tc::mbar_wait_bounded(full + 1, uint32_t((fills1 - 1) & 1), kWaitLimit))
+                atomicExch(sflag, 1);
         }
     } else if (tid >= NT) {
         // ---- MMA warp: one hand-off per GEMM, in the compute threads' order ----
