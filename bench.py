@@ -646,7 +646,7 @@ def run_precision(args):
     f = torch.from_numpy(s.f).cuda()
     stream = torch.cuda.current_stream()
     res = {}
-    for name in ("fp64", "bf16x10", "bf16x6", "tf32x3", "bf16x3"):
+    for name in ("fp64", "bf16x7", "bf16x10", "bf16x6", "tf32x3", "bf16x3"):
         p = exx.Plan(s.n, s.h, s.bc, s.fd_order, s.kernel, s.omega)
         p.set_precision(prec_code(exx, name))
         W = torch.empty_like(psi)
@@ -662,10 +662,10 @@ def run_precision(args):
         table.append({"precision": name, "exx_apply_ms": ms, "pair_solves_per_s": s.unique_pairs() / (ms / 1e3),
                       "vxpsi_rel_fro_vs_fp64": rel(W, W64), "xi_rel_fro_vs_fp64": rel(xi, xi64),
                       "E_x_rel_vs_fp64": abs(e - e64) / abs(e64), "E_x": e})
-    b10 = [r for r in table if r["precision"] == "bf16x10"][0]
-    rec = {"metric": METRIC, "value": b10["pair_solves_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-           "warmup": 1, "ms_per_step": b10["exx_apply_ms"], "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "bf16x10", "data": "synthetic (seeded Gaussian + plane-wave orbitals, orthonormalised)",
+    b7 = [r for r in table if r["precision"] == "bf16x7"][0]   # the default mode
+    rec = {"metric": METRIC, "value": b7["pair_solves_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": 1, "ms_per_step": b7["exx_apply_ms"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "bf16x7", "data": "synthetic (seeded Gaussian + plane-wave orbitals, orthonormalised)",
            "config": {"workload": "precision study: 48x48x48 periodic grid, erfc omega=0.106, 256 orbitals, "
                                   "Fermi-Dirac occupations; exx_apply timed per precision",
                       "unique_pair_solves": s.unique_pairs(), "l2": "not flushed (back-to-back applies)"},
