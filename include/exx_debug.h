@@ -37,6 +37,14 @@ int exx_debug_tc_gemm(int tf32, int n, int k, const float *A, const float *B, fl
  * (field, row in field) (Granlund & Montgomery 1994, Fig. 4.1), host-side.  d >= 1. */
 int exx_debug_fastdiv(unsigned d, int count, const unsigned *n, unsigned *q);
 
+/* The automatic BF16X7 (three-pass) layouts of an n1 x n2 x n3 grid, host-side (no device):
+ * out (HOST int[16]) = supported; shared memory of pass A and pass C; pass A streams its x/y
+ * matrices and their chunk width; the same for pass C; pass A pipelined; pass A staged; pass B
+ * shared memory (0 = none fits); pass B K-chunks; its chunk or block width; its buffers; its
+ * matrices resident; units per thread; the shared-memory limit.  share01 = 1 when x and y have
+ * the same length and boundary condition (one image serves both).  Sizes in [2, 256]. */
+int exx_debug_tc3_layout(int n1, int n2, int n3, int share01, int *out);
+
 /* Failure detection without a fault: launches one kernel whose two mbarrier waits (the
  * same bounded waits the pass kernels use: the polled one of the five-pass kernels, 4096
  * polls, and the wall-time one of the three-pass kernels, here 2 ms) wait on a barrier that

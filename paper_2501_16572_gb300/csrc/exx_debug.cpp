@@ -6,6 +6,13 @@
 
 extern "C" {
 
+int exx_debug_tc3_layout(int n1, int n2, int n3, int share01, int *out)
+{
+    if (n1 < 2 || n2 < 2 || n3 < 2 || n1 > 256 || n2 > 256 || n3 > 256 || !out) return EXX_ERR_INVALID_ARG;
+    exx::tc3_debug_layout(n1, n2, n3, share01 != 0, out);
+    return EXX_OK;
+}
+
 int exx_debug_fd_weights(int p, double *w)
 {
     if (p < 1 || p > 12 || !w) return EXX_ERR_INVALID_ARG;

@@ -1495,4 +1495,38 @@ int tc3_solve_batch(Plan &P, const int2 *pairs_d, int nfields, float *bufA, floa
     return EXX_OK;
 }
 
+// Host only: the automatic BF16X7 layouts of an n1 x n2 x n3 grid (no device involved).
+// out[0] supported; [1] [2] shared memory of pass A / pass C; [3] [4] pass A streams its x/y
+// matrices, chunk width; [5] [6] the same for pass C; [7] pass A pipelined, [8] staged;
+// [9] pass B shared memory (0: none fits); [10] pass B K-chunks; [11] chunk or block width;
+// [12] buffers; [13] resident; [14] units per thread; [15] the shared-memory limit.
+void tc3_debug_layout(int n1, int n2, int n3, int share01, int *out)
+{
+    Plan P;
+    P.n[0] = n1;
+    P.n[1] = n2;
+    P.n[2] = n3;
+    P.t3_share01 = share01;
+    std::string why;
+    out[0] = tc3_supported(P, &why) ? 1 : 0;
+    const SliceLayout A = slice_layout(P, true), C = slice_layout(P, false);
+    out[1] = int(A.smem);
+    out[2] = int(C.smem);
+    out[3] = A.bstream;
+    out[4] = A.KC;
+    out[5] = C.bstream;
+    out[6] = C.KC;
+    out[7] = A.pipe;
+    out[8] = A.stage;
+    ZLayout Z{};
+    const bool zok = z_layout(n3, Z);
+    out[9] = zok ? int(Z.smem) : 0;
+    out[10] = Z.kchunk;
+    out[11] = Z.kchunk ? Z.KC : Z.WN;
+    out[12] = Z.nbuf;
+    out[13] = Z.resident;
+    out[14] = z_upt(n3);
+    out[15] = int(kSmemLimit);
+}
+
 }  // namespace exx

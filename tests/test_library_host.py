@@ -201,3 +201,37 @@ def test_stored_slab_energy_matches_the_input_recipe():
     assert mk.stored_matches(g, Recipe())
     assert g["unique_pair_solves"] == 800 * 801 // 2
     assert g["E_x"] < 0 and len(g["fingerprint"]["sum_sq"]) == 1024
+
+
+def _tc3_layout(lib, n1, n2, n3, share):
+    out = (ctypes.c_int * 16)()
+    lib.exx_debug_tc3_layout.argtypes = [ctypes.c_int] * 4 + [ctypes.c_void_p]
+    assert lib.exx_debug_tc3_layout(n1, n2, n3, share, out) == 0
+    keys = ["supported", "smem_a", "smem_c", "stream_a", "kc_a", "stream_c", "kc_c", "pipe_a", "stage_a",
+            "smem_b", "kchunk_b", "width_b", "nbuf_b", "resident_b", "upt", "limit"]
+    return dict(zip(keys, list(out)))
+
+
+def test_three_pass_layouts_fit_shared_memory(lib):
+    """Every grid the three-pass mode accepts (x, y <= 128, z <= 208) gets layouts within the
+    shared-memory limit; the two slice passes agree on streaming the x/y matrices; the bench
+    slab keeps its x/y images resident and streams z as K-chunks; the 117-point capacity
+    slices stream their x/y images; wider slices and longer z axes are refused."""
+    sizes = [2, 5, 16, 17, 31, 48, 64, 72, 90, 100, 108, 112, 117, 120, 128]
+    for n1 in sizes:
+        for n2 in sizes:
+            for n3 in (2, 9, 48, 119, 144, 150, 200, 208):
+                for share in ((0, 1) if n1 == n2 else (0,)):
+                    L = _tc3_layout(lib, n1, n2, n3, share)
+                    assert L["supported"] == 1, (n1, n2, n3, L)
+                    assert max(L["smem_a"], L["smem_c"], L["smem_b"]) <= L["limit"], (n1, n2, n3, L)
+                    assert (L["stream_a"], L["kc_a"]) == (L["stream_c"], L["kc_c"]), (n1, n2, n3)
+                    if L["stream_a"]:
+                        assert L["kc_a"] in (16, 32, 48, 64) and L["stage_a"] == 0
+                    assert L["upt"] * 4 * 4 >= n3
+    slab = _tc3_layout(lib, 72, 72, 144, 1)
+    assert slab["stream_a"] == 0 and slab["kchunk_b"] == 1 and slab["width_b"] == 48 and slab["nbuf_b"] == 2
+    cap = _tc3_layout(lib, 117, 117, 119, 1)
+    assert cap["stream_a"] == 1 and cap["kc_a"] == 32
+    assert _tc3_layout(lib, 130, 8, 8, 0)["supported"] == 0
+    assert _tc3_layout(lib, 16, 16, 240, 1)["supported"] == 0
