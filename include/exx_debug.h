@@ -45,6 +45,16 @@ int exx_debug_fastdiv(unsigned d, int count, const unsigned *n, unsigned *q);
  * the same length and boundary condition (one image serves both).  Sizes in [2, 256]. */
 int exx_debug_tc3_layout(int n1, int n2, int n3, int share01, int *out);
 
+/* The base-512 digit image of the 1D matrices, host-side: C (HOST, row-major nout x nk, row n =
+ * output n, column k = contraction index k) cut for a WN x Kp block of rows n0.. and indices
+ * k0.. (a K-chunk when k0 > 0 or Kp < nk), decoded from the tensor-core layout back to values:
+ * digits (HOST float[4][WN][Kp]) holds the four weighted digits of every entry (their sum times
+ * the row's scale is the entry), scales (HOST float[WN]) the column scales.  Every row is
+ * scaled by the largest entry of the whole row, so the chunks of a row share one scale.
+ * WN and Kp multiples of 8. */
+int exx_debug_matrix_digits(int nout, int nk, const double *C, int WN, int Kp, int n0, int k0, float *digits,
+                            float *scales);
+
 /* Failure detection without a fault: launches one kernel whose two mbarrier waits (the
  * same bounded waits the pass kernels use: the polled one of the five-pass kernels, 4096
  * polls, and the wall-time one of the three-pass kernels, here 2 ms) wait on a barrier that

@@ -13,6 +13,15 @@ int exx_debug_tc3_layout(int n1, int n2, int n3, int share01, int *out)
     return EXX_OK;
 }
 
+int exx_debug_matrix_digits(int nout, int nk, const double *C, int WN, int Kp, int n0, int k0, float *digits,
+                            float *scales)
+{
+    if (nout < 1 || nk < 1 || WN < 1 || Kp < 8 || Kp % 8 || WN % 8 || n0 < 0 || k0 < 0 || !C || !digits || !scales)
+        return EXX_ERR_INVALID_ARG;
+    exx::tc3_debug_matrix_digits(nout, nk, C, WN, Kp, n0, k0, digits, scales);
+    return EXX_OK;
+}
+
 int exx_debug_fd_weights(int p, double *w)
 {
     if (p < 1 || p > 12 || !w) return EXX_ERR_INVALID_ARG;

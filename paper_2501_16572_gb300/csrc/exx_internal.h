@@ -220,6 +220,8 @@ int tc3_upload(Plan &P);
 int tc3_solve_batch(Plan &P, const int2 *pairs_d, int nfields, float *bufA, float *bufB, cudaStream_t s);
 std::vector<std::pair<int, int>> tc3_z_choices(int n3);
 void tc3_debug_layout(int n1, int n2, int n3, int share01, int *out);
+void tc3_debug_matrix_digits(int nout, int nk, const double *C, int WN, int Kp, int n0, int k0, float *digits,
+                             float *scales);
 int tc_unit_gemm(int tf32, int n, int k, const float *A, const float *B, float *D, int *err);
 int tc_wait_timeout_probe(int *status_h);
 

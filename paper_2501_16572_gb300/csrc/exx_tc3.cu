@@ -1529,4 +1529,25 @@ void tc3_debug_layout(int n1, int n2, int n3, int share01, int *out)
     out[15] = int(kSmemLimit);
 }
 
+// Host only: the digit image of C(n, k) (row-major nout x nk, HOST) in a WN x Kp block of rows
+// n0.. and contraction indices k0.., decoded back to values: digits[q][n][k] (the weighted
+// digit q of row n, index k of the block) and the WN column scales.
+void tc3_debug_matrix_digits(int nout, int nk, const double *C, int WN, int Kp, int n0, int k0, float *digits,
+                             float *scales)
+{
+    std::vector<uint8_t> img(mat_image_bytes(WN, Kp), 0);
+    build_block(img.data(), WN, Kp, n0, nout, nk, [&](int n, int k) { return C[size_t(n) * nk + k]; }, k0);
+    const size_t piece = size_t(WN) * Kp * 2;
+    const uint32_t sbo = uint32_t(Kp) * 16u;
+    for (int q = 0; q < kMatDig; ++q)
+        for (int n = 0; n < WN; ++n)
+            for (int k = 0; k < Kp; ++k) {
+                uint16_t hb;
+                std::memcpy(&hb, img.data() + piece * q + img_at(n, k / 8, sbo) + size_t(k % 8) * 2, 2);
+                const uint32_t u = uint32_t(hb) << 16;
+                std::memcpy(digits + (size_t(q) * WN + n) * Kp + k, &u, 4);
+            }
+    std::memcpy(scales, img.data() + piece * kMatDig, size_t(WN) * 4);
+}
+
 }  // namespace exx

@@ -235,3 +235,44 @@ def test_three_pass_layouts_fit_shared_memory(lib):
     assert cap["stream_a"] == 1 and cap["kc_a"] == 32
     assert _tc3_layout(lib, 130, 8, 8, 0)["supported"] == 0
     assert _tc3_layout(lib, 16, 16, 240, 1)["supported"] == 0
+
+
+def test_matrix_digit_images_reproduce_the_matrix(lib):
+    """The four base-512 digits of a matrix row (row scaled by the largest entry of the whole row
+    into [128, 256)) reproduce every entry to 2^-35 of the row maximum (the last digit rounds
+    at 2^-27 of a first digit below 256); each weighted digit q is an integer of magnitude
+    <= 256 times 2^-9q (exact in bf16); padding is zero; a K-chunk is the same digits as the
+    matching columns of the whole image, with the same row scales."""
+    rng = np.random.default_rng(7)
+    nout, nk = 40, 37
+    C = rng.standard_normal((nout, nk)) * 10.0 ** rng.uniform(-3, 3, size=(nout, 1))
+    C[5] = 0.0
+    Cc = np.ascontiguousarray(C)
+    dp = ctypes.POINTER(ctypes.c_double)
+    fp = ctypes.POINTER(ctypes.c_float)
+    lib.exx_debug_matrix_digits.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int, ctypes.c_int, fp, fp]
+
+    def image(WN, Kp, n0, k0):
+        d = np.zeros((4, WN, Kp), np.float32)
+        sc = np.zeros(WN, np.float32)
+        assert lib.exx_debug_matrix_digits(nout, nk, Cc.ctypes.data_as(dp), WN, Kp, n0, k0,
+                                           d.ctypes.data_as(fp), sc.ctypes.data_as(fp)) == 0
+        return d.astype(np.float64), sc.astype(np.float64)
+
+    d, sc = image(48, 48, 0, 0)
+    recon = d.sum(axis=0) * sc[:, None]
+    for n in range(nout):
+        rmax = np.max(np.abs(C[n]))
+        assert np.max(np.abs(recon[n, :nk] - C[n])) <= 2.0 ** -35 * rmax + 1e-300, n
+    for q in range(4):
+        w = d[q] * 2.0 ** (9 * q)
+        assert np.all(w == np.round(w)) and np.max(np.abs(w)) <= 256
+    assert np.all(d[:, nout:, :] == 0) and np.all(d[:, :, nk:] == 0)
+    assert np.all(d[:, 5, :] == 0)
+    dc, scc = image(48, 16, 0, 16)        # the K-chunk of contraction indices 16..31
+    assert np.array_equal(dc, d[:, :, 16:32]) and np.array_equal(scc, sc)
+    dl, _ = image(48, 16, 0, 32)          # the last chunk: indices 32..36, zeros after
+    assert np.array_equal(dl[:, :, :nk - 32], d[:, :, 32:nk]) and np.all(dl[:, :, nk - 32:] == 0)
+    db, scb = image(16, 48, 16, 0)        # an output block: rows 16..31
+    assert np.array_equal(db, d[:, 16:32, :]) and np.array_equal(scb, sc[16:32])
