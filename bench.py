@@ -422,6 +422,18 @@ def run_batch48(args):
         bufs.append((psi, torch.from_numpy(s.f).to(dev), torch.empty_like(psi)))
     bargs = [(psi[:s.n_occ], f, psi, out) for (psi, f, out), s in zip(bufs, systems)]
     unique = sum(s.unique_pairs() for s in systems)
+    # every system's settings from the library's autotuner, on its own grid and data (untimed)
+    tuning = None
+    if not args.no_tune:
+        import collections
+        t0 = time.perf_counter()
+        picks = collections.Counter()
+        for p, (po, f, pi, out) in zip(plans, bargs):
+            t = p.autotune(po, f, pi, out=out)
+            picks[f"pairs {t['pairs_per_batch']}, block {t['block_orbitals']}, z {t['z_block']}/{t['z_buffers']}, "
+                  f"staging {t['staging']}, pipeline {t['pipeline']}"] += 1
+        tuning = {"systems_tuned": len(plans), "seconds": time.perf_counter() - t0,
+                  "choices": dict(picks.most_common())}
     side = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -486,6 +498,7 @@ def run_batch48(args):
         "per_system_loop": {"ms_per_step": t_loop / K, "value": u.item() * K / (t_loop / 1e3)},
         "graph_vs_loop_speedup": t_loop / t_graph,
         "graph_equals_loop_bitwise": identical,
+        "autotune": tuning,
         "clocks": clk,
     }
     # per-kernel times: one more step with CUDA events around every launch (timing issues
